@@ -1,0 +1,164 @@
+/*
+ * mdc.h -- C ABI of the GB300 multi-dimensional convolution (MDC) library.
+ *
+ * The library applies the MDC operator of Ravasi & Vasconcelos (arXiv 2011.11120)
+ * and solves the Marchenko redatuming system built on it, on one NVIDIA GB300
+ * (sm_103a).  Every operation runs in hand-written CUDA kernels; there is no CPU
+ * fallback.  Plain pointers and sizes only: no C++ or framework types cross it.
+ *
+ * Conventions shared by every call
+ *   - Time-domain arrays are real float32, row-major [nt][n_space][nv] (nv fastest).
+ *   - The kernel G is complex64 interleaved (re, im), row-major [nfmax][nr][ns]
+ *     (s fastest): G[k][r][s] = K(w_k, x_r, x_s), w_k = 2 pi k / (nt dt).
+ *   - "Device pointer" means memory the caller allocated on the current CUDA device;
+ *     the caller keeps ownership.  The handle owns its copy of G and its scratch.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are stream-ordered and asynchronous unless documented as blocking.
+ *   - Every call returns an mdc_status; no exception or abort crosses the ABI.
+ *     A negative status leaves the handle usable unless it is MDC_ERR_CUDA, which
+ *     reports a CUDA error (the context may then be unusable; see mdc_last_cuda_error).
+ *   - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef MDC_GB300_H
+#define MDC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdc_plan* mdc_handle;
+
+typedef enum {
+    MDC_OK = 0,
+    MDC_ERR_ARG = -1,       /* invalid argument (null pointer, size out of range, ...) */
+    MDC_ERR_OOM = -2,       /* device allocation failed */
+    MDC_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    MDC_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
+    MDC_ERR_NUMERIC = -5,   /* non-finite value met in a solver recurrence */
+    MDC_ERR_BUDGET = -6,    /* request exceeds the configured memory budget */
+    MDC_ERR_STATE = -7      /* call not valid in the handle's current state */
+} mdc_status;
+
+/* Storage format of the library-owned kernel copy (Section "Implementing the batch
+ * matrix multiplication operator": the kernel streamed once per pass dominates cost). */
+typedef enum {
+    MDC_C64 = 0,    /* complex float32 (the paper's complex64 kernel, Table 1) */
+    MDC_C16F = 1,   /* complex float16, one float32 scale per (frequency, row) */
+    MDC_CBF16 = 2,  /* complex bfloat16, one float32 scale per (frequency, row) */
+    MDC_CE4M3 = 3   /* complex FP8 E4M3, one float32 scale per (frequency, row) */
+} mdc_storage;
+
+/* mdc_forward / mdc_adjoint flags */
+#define MDC_CONJ_KERNEL 0x1u  /* use the conjugated kernel: R* (correlation) in Eq. 5 */
+
+/* Kernel classes for the timing counters (mdc_timing_read). */
+typedef enum {
+    MDC_KC_RFFT = 0,        /* F and I_wmax of Eq. 3 (plus window and time reversal) */
+    MDC_KC_PRODUCT_FWD = 1, /* K-hat of Eq. 3: per-frequency G(w) X(w) */
+    MDC_KC_PRODUCT_ADJ = 2, /* K-hat^H of Eq. 3: per-frequency G(w)^H Y(w) */
+    MDC_KC_IRFFT = 3,       /* I_wmax^H and F^H of Eq. 3 (plus fused epilogues) */
+    MDC_KC_SOLVER = 4,      /* LSQR scalar recurrences and vector updates */
+    MDC_KC_COUNT = 5
+} mdc_kernel_class;
+
+/*
+ * mdc_create -- build an MDC operator C = F^H I^H K-hat I F (Eq. 3) for kernel G.
+ *
+ *   G        device pointer, complex64 interleaved [nfmax][nr][ns]: the first nfmax
+ *            frequencies of the kernel (Eq. 2, truncated spectrum).  Read only; it is
+ *            copied (and for reduced storage quantised) into a library-owned, padded
+ *            layout, so the caller may free G when the call returns.
+ *   nfmax    number of kept frequencies, 1 <= nfmax <= nt/2 + 1.
+ *   nr, ns   output (receiver/row) and integration (source/column) sizes, >= 1.
+ *   nt       number of time samples: a power of two in [64, 4096].
+ *   dt, dr   time step and areal integration weight; the operator is scaled by dt*dr
+ *            (the integration step multiplied into the kernel, Theory section).
+ *   storage  an mdc_storage value.
+ *   stream   stream for the copy kernels.
+ * Blocking: allocates device memory and synchronises `stream` before returning.
+ * Errors: MDC_ERR_ARG for bad sizes or a null pointer, MDC_ERR_OOM if the copy does
+ * not fit; *out is set to NULL on failure.
+ */
+int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
+               double dt, double dr, int storage, void* stream);
+
+/*
+ * mdc_forward -- y = C x (Eq. 3, left), or y = R* x with MDC_CONJ_KERNEL (Eq. 5).
+ *   x  device float32 [nt][ns][nv] (input function f, integration axis ns).
+ *   y  device float32 [nt][nr][nv] (output function g), fully overwritten.
+ *   nv number of virtual points (columns), >= 1.
+ * Stream-ordered.  Grows the handle's scratch on first use of a larger nv (which
+ * allocates, so call mdc_reserve first when capturing into a CUDA graph).
+ */
+int mdc_forward(mdc_handle h, const float* x, float* y, int nv, unsigned flags, void* stream);
+
+/*
+ * mdc_adjoint -- x = C^H y (Eq. 3, right), or x = (R*)^H y with MDC_CONJ_KERNEL.
+ *   y  device float32 [nt][nr][nv];  x  device float32 [nt][ns][nv], overwritten.
+ * The same kernel buffer is read transposed; no second copy of G exists.
+ */
+int mdc_adjoint(mdc_handle h, const float* y, float* x, int nv, unsigned flags, void* stream);
+
+/* mdc_reserve -- size the handle's scratch for up to nv_max columns per pass (blocking). */
+int mdc_reserve(mdc_handle h, int nv_max);
+
+/*
+ * marchenko_lsqr -- solve the Marchenko system of Eq. 5 by LSQR and evaluate Eq. 6.
+ *
+ *   d = M f,  M = [[I, -Theta R], [-Theta R*, I]],  d = [Theta R f_d+ ; 0],
+ *   f = [f- ; f_m+],  then  g- = R f+ - f-,  g+* = f+ - R* f-,  f+ = f_d+ + f_m+.
+ *
+ *   R        handle whose kernel is the reflection response (requires nr == ns).
+ *   window   device int32 [ns][nv]: Theta cut-offs; Theta[t][s][v] = 1 iff
+ *            |tau(t)| < window[s][v], tau(t) = t for t < nt/2 and t - nt otherwise.
+ *   fd_plus  device float32 [nt][ns][nv]: initial (direct) focusing function f_d+.
+ *   nv       number of focusing points solved together as one system (one set of
+ *            LSQR scalars for all nv columns).
+ *   niter    maximum LSQR iterations (>= 1); tol > 0 also stops when the residual
+ *            estimate falls to tol * ||d||, tol <= 0 runs exactly niter iterations.
+ *   f_minus, f_mplus   device float32 [nt][ns][nv] outputs (the solution).
+ *   g_minus, g_plus    device float32 [nt][ns][nv] outputs or NULL (skips Eq. 6);
+ *            g_plus receives g+, the time reversal of the second row of Eq. 6.
+ *   resid    host double[niter + 1] or NULL: ||d||, then the LSQR residual estimate
+ *            after each iteration (unused tail entries set to -1).
+ *   iters_done host int or NULL: iterations actually performed.
+ * Blocking: synchronises `stream` before returning (host outputs).  Allocates its
+ * work vectors (5 block vectors of 2*nt*ns*nv floats) for the duration of the call.
+ * Errors: MDC_ERR_ARG (nr != ns, bad sizes, null required pointer), MDC_ERR_OOM,
+ * MDC_ERR_NUMERIC (a non-finite alpha or beta).
+ */
+int marchenko_lsqr(mdc_handle R, const int* window, const float* fd_plus, int nv, int niter,
+                   double tol, float* f_minus, float* f_mplus, float* g_minus, float* g_plus,
+                   double* resid, int* iters_done, void* stream);
+
+/* mdc_destroy -- free the handle and everything it owns (synchronises the device). */
+int mdc_destroy(mdc_handle h);
+
+/* mdc_strerror -- static text for a status code. */
+const char* mdc_strerror(int status);
+
+/* mdc_last_cuda_error -- the cudaError_t value behind the last MDC_ERR_CUDA (per thread). */
+int mdc_last_cuda_error(void);
+
+/* mdc_kernel_bytes -- bytes the library-owned kernel copy of a given shape occupies
+ * (padding and per-row scales included).  Host-only; no device needed. */
+int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage);
+
+/*
+ * Instrumentation.  mdc_timing(h, 1) makes the handle bracket every kernel launch
+ * with CUDA events on the launching stream; mdc_timing_read(h, cls, &ms, &n) then
+ * synchronises and returns the summed device time and launch count of one kernel
+ * class since the last mdc_timing(h, 1).  mdc_launch_count returns the number of
+ * kernels the handle has launched since creation (timing on or off).
+ */
+int mdc_timing(mdc_handle h, int enable);
+int mdc_timing_read(mdc_handle h, int kernel_class, double* total_ms, int64_t* launches);
+int64_t mdc_launch_count(mdc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDC_GB300_H */

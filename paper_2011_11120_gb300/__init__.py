@@ -1,0 +1,203 @@
+"""GB300 multi-dimensional convolution (MDC) and Marchenko-LSQR redatuming.
+
+Thin ctypes binding over the C ABI of ``include/mdc.h`` (``libmdc_gb300.so``).
+Functions keep the ABI's names and only marshal arguments: torch CUDA tensors
+become device pointers, the current torch stream becomes the ``stream``
+argument.  Every operation runs in the library's CUDA kernels; if the library
+is missing this module raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdc_gb300.so")
+
+MDC_OK = 0
+MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3 = 0, 1, 2, 3
+STORAGE = {"c64": MDC_C64, "c16f": MDC_C16F, "cbf16": MDC_CBF16, "ce4m3": MDC_CE4M3}
+MDC_CONJ_KERNEL = 0x1
+KC_RFFT, KC_PRODUCT_FWD, KC_PRODUCT_ADJ, KC_IRFFT, KC_SOLVER = range(5)
+KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj": KC_PRODUCT_ADJ,
+                  "irfft": KC_IRFFT, "solver": KC_SOLVER}
+
+# exported symbol -> (restype, argtypes)
+_vp, _i, _d, _u, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_int64
+SIGNATURES = {
+    "mdc_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i, _i, _d, _d, _i, _vp]),
+    "mdc_forward": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
+    "mdc_adjoint": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
+    "mdc_reserve": (_i, [_vp, _i]),
+    "marchenko_lsqr": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp,
+                            ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
+    "mdc_destroy": (_i, [_vp]),
+    "mdc_strerror": (ctypes.c_char_p, [_i]),
+    "mdc_last_cuda_error": (_i, []),
+    "mdc_kernel_bytes": (_i64, [_i, _i, _i, _i]),
+    "mdc_timing": (_i, [_vp, _i]),
+    "mdc_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
+    "mdc_launch_count": (_i64, [_vp]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2011_11120_gb300.build` (the MDC path has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class MDCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().mdc_strerror(status).decode()
+        if status == -3:
+            msg += f" (cudaError {lib().mdc_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{status}]")
+        self.status = status
+
+
+def _check(status: int, where: str) -> None:
+    if status != MDC_OK:
+        raise MDCError(status, where)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ ABI-named calls
+def mdc_create(G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None) -> ctypes.c_void_p:
+    """Build an MDC handle from a complex64 CUDA tensor G[nfmax, nr, ns] (copied)."""
+    if G.dtype != torch.complex64 or G.dim() != 3:
+        raise ValueError("G must be complex64 [nfmax, nr, ns]")
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    h = ctypes.c_void_p()
+    nf, nr, ns = G.shape
+    _check(lib().mdc_create(ctypes.byref(h), _ptr(G, name="G"), nf, nr, ns, nt, dt, dr, st, _stream(stream)),
+           "mdc_create")
+    return h
+
+
+def mdc_forward(h, x: torch.Tensor, y: torch.Tensor, nv: int, flags: int = 0, stream=None) -> None:
+    _check(lib().mdc_forward(h, _ptr(x, torch.float32, "x"), _ptr(y, torch.float32, "y"), nv, flags,
+                             _stream(stream)), "mdc_forward")
+
+
+def mdc_adjoint(h, y: torch.Tensor, x: torch.Tensor, nv: int, flags: int = 0, stream=None) -> None:
+    _check(lib().mdc_adjoint(h, _ptr(y, torch.float32, "y"), _ptr(x, torch.float32, "x"), nv, flags,
+                             _stream(stream)), "mdc_adjoint")
+
+
+def mdc_reserve(h, nv_max: int) -> None:
+    _check(lib().mdc_reserve(h, nv_max), "mdc_reserve")
+
+
+def marchenko_lsqr(h, window: torch.Tensor, fd_plus: torch.Tensor, nv: int, niter: int, tol: float,
+                   f_minus: torch.Tensor, f_mplus: torch.Tensor, g_minus=None, g_plus=None, stream=None):
+    """Solve Eq. 5 by LSQR and evaluate Eq. 6; returns (resid list, iterations done)."""
+    resid = (ctypes.c_double * (niter + 1))()
+    it = ctypes.c_int(0)
+    st = lib().marchenko_lsqr(h, _ptr(window, torch.int32, "window"), _ptr(fd_plus, torch.float32, "fd_plus"),
+                              nv, niter, tol, _ptr(f_minus, torch.float32, "f_minus"),
+                              _ptr(f_mplus, torch.float32, "f_mplus"), _ptr(g_minus, torch.float32, "g_minus"),
+                              _ptr(g_plus, torch.float32, "g_plus"), resid, ctypes.byref(it), _stream(stream))
+    _check(st, "marchenko_lsqr")
+    return [resid[i] for i in range(niter + 1)], it.value
+
+
+def mdc_destroy(h) -> None:
+    _check(lib().mdc_destroy(h), "mdc_destroy")
+
+
+def mdc_kernel_bytes(nfmax: int, nr: int, ns: int, storage="c64") -> int:
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    return int(lib().mdc_kernel_bytes(nfmax, nr, ns, st))
+
+
+def mdc_timing(h, enable: bool) -> None:
+    _check(lib().mdc_timing(h, 1 if enable else 0), "mdc_timing")
+
+
+def mdc_timing_read(h, kernel_class) -> tuple:
+    cls = KERNEL_CLASSES[kernel_class] if isinstance(kernel_class, str) else int(kernel_class)
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(lib().mdc_timing_read(h, cls, ctypes.byref(ms), ctypes.byref(n)), "mdc_timing_read")
+    return ms.value, n.value
+
+
+def mdc_launch_count(h) -> int:
+    return int(lib().mdc_launch_count(h))
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class MDC:
+    """Owning wrapper: ``MDC(G, nt, dt, dr)``, ``.forward(x)``, ``.adjoint(y)``, ``.marchenko(...)``."""
+
+    def __init__(self, G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None):
+        self.nf, self.nr, self.ns = G.shape
+        self.nt, self.dt, self.dr = nt, dt, dr
+        self.h = mdc_create(G, nt, dt, dr, storage, stream)
+
+    def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, conj=False, stream=None):
+        nv = x.shape[2]
+        if out is None:
+            out = torch.empty((self.nt, self.nr, nv), dtype=torch.float32, device=x.device)
+        mdc_forward(self.h, x, out, nv, MDC_CONJ_KERNEL if conj else 0, stream)
+        return out
+
+    def adjoint(self, y: torch.Tensor, out: Optional[torch.Tensor] = None, conj=False, stream=None):
+        nv = y.shape[2]
+        if out is None:
+            out = torch.empty((self.nt, self.ns, nv), dtype=torch.float32, device=y.device)
+        mdc_adjoint(self.h, y, out, nv, MDC_CONJ_KERNEL if conj else 0, stream)
+        return out
+
+    def marchenko(self, window: torch.Tensor, fd_plus: torch.Tensor, niter: int, tol: float = 0.0,
+                  greens: bool = True, stream=None):
+        nv = fd_plus.shape[2]
+        mk = lambda: torch.empty_like(fd_plus)  # noqa: E731
+        fm, fmp = mk(), mk()
+        gm, gp = (mk(), mk()) if greens else (None, None)
+        resid, iters = marchenko_lsqr(self.h, window, fd_plus, nv, niter, tol, fm, fmp, gm, gp, stream)
+        return {"f_minus": fm, "f_mplus": fmp, "g_minus": gm, "g_plus": gp, "resid": resid, "iters": iters}
+
+    def close(self):
+        if self.h is not None:
+            mdc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

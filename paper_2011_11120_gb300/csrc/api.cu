@@ -1,0 +1,237 @@
+// C ABI: plan construction, MDC forward/adjoint (Eq. 3), instrumentation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace mdc {
+
+static thread_local int g_last_cuda_error = 0;
+void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
+LaunchScope::LaunchScope(mdc_plan* p_, cudaStream_t s_, int cls_) : p(p_), s(s_), cls(cls_) {
+    p->launch_count++;
+    p->timing.launches[cls]++;
+    if (p->timing.on && p->timing.used < p->timing.pool.size()) {
+        ev = &p->timing.pool[p->timing.used];
+        p->timing.used_class[p->timing.used] = cls;
+        p->timing.recorded[cls]++;
+        p->timing.used++;
+        cudaEventRecord(ev->a, s);
+    }
+}
+LaunchScope::~LaunchScope() {
+    if (ev) cudaEventRecord(ev->b, s);
+}
+
+int ensure_scratch(mdc_plan* p, int ncols);
+
+}  // namespace mdc
+
+using namespace mdc;
+
+#define MDC_CUDA_TRY(expr)                              \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) {                        \
+            set_cuda_error(_e);                         \
+            return _e == cudaErrorMemoryAllocation ? MDC_ERR_OOM : MDC_ERR_CUDA; \
+        }                                               \
+    } while (0)
+
+static bool valid_nt(int nt) { return nt >= 64 && nt <= 4096 && (nt & (nt - 1)) == 0; }
+
+extern "C" int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage) {
+    if (nfmax < 1 || nr < 1 || ns < 1) return -1;
+    const int64_t ldg = round_up(ns, G_PITCH_ALIGN);
+    const int64_t n = (int64_t)nfmax * nr * ldg;
+    switch (storage) {
+        case MDC_C64: return n * 8;
+        case MDC_C16F:
+        case MDC_CBF16: return n * 4 + (int64_t)nfmax * nr * 4;
+        case MDC_CE4M3: return n * 2 + (int64_t)nfmax * nr * 4;
+        default: return -1;
+    }
+}
+
+extern "C" const char* mdc_strerror(int status) {
+    switch (status) {
+        case MDC_OK: return "ok";
+        case MDC_ERR_ARG: return "invalid argument";
+        case MDC_ERR_OOM: return "device allocation failed";
+        case MDC_ERR_CUDA: return "CUDA runtime error";
+        case MDC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MDC_ERR_NUMERIC: return "non-finite value in solver recurrence";
+        case MDC_ERR_BUDGET: return "request exceeds memory budget";
+        case MDC_ERR_STATE: return "call not valid in current state";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int mdc_last_cuda_error(void) { return g_last_cuda_error; }
+
+static void free_plan(mdc_plan* p) {
+    if (!p) return;
+    cudaFree(p->G);
+    cudaFree(p->gscale);
+    cudaFree(p->tw);
+    cudaFree(p->specA);
+    cudaFree(p->specB);
+    for (auto& e : p->timing.pool) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    delete p;
+}
+
+extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
+                          double dt, double dr, int storage, void* stream) {
+    if (!out) return MDC_ERR_ARG;
+    *out = nullptr;
+    if (!G || nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
+    if (!(dt > 0.0) || !(dr > 0.0) || !std::isfinite(dt) || !std::isfinite(dr)) return MDC_ERR_ARG;
+    if (storage != MDC_C64) return MDC_ERR_ARG;   // reduced storage: see mdc_create_lowp
+    if ((int64_t)nr * nfmax > (int64_t)1 << 31) return MDC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mdc_plan* p = new (std::nothrow) mdc_plan();
+    if (!p) return MDC_ERR_OOM;
+    p->nf = nfmax; p->nr = nr; p->ns = ns; p->nt = nt; p->logn = ilog2(nt);
+    p->dt = dt; p->dr = dr; p->storage = storage;
+    p->ldg = round_up(ns, G_PITCH_ALIGN);
+    const size_t rowbytes = (size_t)p->ldg * sizeof(float2);
+    cudaError_t e = cudaMalloc(&p->G, rowbytes * nr * nfmax);
+    if (e == cudaSuccess) e = cudaMemcpy2DAsync(p->G, rowbytes, G, (size_t)ns * sizeof(float2),
+                                                (size_t)ns * sizeof(float2), (size_t)nr * nfmax,
+                                                cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && p->ldg > ns)
+        e = cudaMemset2DAsync((char*)p->G + (size_t)ns * sizeof(float2), rowbytes, 0,
+                              (size_t)(p->ldg - ns) * sizeof(float2), (size_t)nr * nfmax, s);
+    if (e == cudaSuccess) {
+        std::vector<float2> tw(nt / 2);
+        for (int j = 0; j < nt / 2; ++j) {
+            const double ang = -2.0 * M_PI * (double)j / (double)nt;
+            tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        e = cudaMalloc(&p->tw, sizeof(float2) * (nt / 2));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->tw, tw.data(), sizeof(float2) * (nt / 2),
+                                                  cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        free_plan(p);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? MDC_ERR_OOM : MDC_ERR_CUDA;
+    }
+    *out = p;
+    return MDC_OK;
+}
+
+int mdc::ensure_scratch(mdc_plan* p, int ncols) {
+    if (ncols <= p->nv_cap) return MDC_OK;
+    const size_t n = (size_t)p->nf * (size_t)(p->nr > p->ns ? p->nr : p->ns) * ncols;
+    float2 *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, n * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&b, n * sizeof(float2));
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        cudaGetLastError();
+        set_cuda_error(e);
+        return MDC_ERR_OOM;
+    }
+    cudaFree(p->specA);
+    cudaFree(p->specB);
+    p->specA = a;
+    p->specB = b;
+    p->nv_cap = ncols;
+    return MDC_OK;
+}
+
+extern "C" int mdc_reserve(mdc_handle h, int nv_max) {
+    if (!h || nv_max < 1) return MDC_ERR_ARG;
+    return ensure_scratch(h, nv_max);
+}
+
+// One MDC pass: rFFT of `in` (S_in spatial points), per-frequency product, irFFT to `out`.
+static int mdc_pass(mdc_plan* p, bool adjoint, const float* in, float* outp, int nv, unsigned flags,
+                    cudaStream_t s) {
+    if (!in || !outp || nv < 1) return MDC_ERR_ARG;
+    int st = ensure_scratch(p, nv);
+    if (st != MDC_OK) return st;
+    const int S_in = adjoint ? p->nr : p->ns;
+    const int S_out = adjoint ? p->ns : p->nr;
+    const int conj = (flags & MDC_CONJ_KERNEL) ? 1 : 0;
+    RfftArgs ra{};
+    ra.x = in; ra.x2 = nullptr; ra.C = S_in * nv; ra.S = S_in; ra.nv = nv;
+    ra.nt = p->nt; ra.logn = p->logn; ra.nf = p->nf; ra.cut = nullptr; ra.scale = C1(1.f);
+    ra.conj = conj; ra.X = p->specA; ra.ldv = nv; ra.voff = 0; ra.tw = p->tw; ra.active = nullptr;
+    launch_rfft(p, ra, s);
+    launch_product(p, adjoint, p->specA, nv, 0, p->specB, nv, 0, nv, s, nullptr);
+    IrfftArgs ia{};
+    ia.Y = p->specB; ia.ldv = nv; ia.voff = 0; ia.C = S_out * nv; ia.S = S_out; ia.nv = nv;
+    ia.nt = p->nt; ia.logn = p->logn; ia.nf = p->nf; ia.conj_in = conj;
+    ia.scale = (float)(p->dt * p->dr / (double)p->nt);
+    ia.out = outp; ia.a_mdc = C1(1.f); ia.a_base = C1(0.f); ia.a_prev = C1(0.f);
+    ia.base = nullptr; ia.cut = nullptr; ia.reverse_out = 0; ia.colsum = nullptr; ia.tw = p->tw;
+    ia.active = nullptr;
+    launch_irfft(p, ia, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(e); return MDC_ERR_CUDA; }
+    return MDC_OK;
+}
+
+extern "C" int mdc_forward(mdc_handle h, const float* x, float* y, int nv, unsigned flags, void* stream) {
+    if (!h || (flags & ~MDC_CONJ_KERNEL)) return MDC_ERR_ARG;
+    return mdc_pass(h, false, x, y, nv, flags, (cudaStream_t)stream);
+}
+
+extern "C" int mdc_adjoint(mdc_handle h, const float* y, float* x, int nv, unsigned flags, void* stream) {
+    if (!h || (flags & ~MDC_CONJ_KERNEL)) return MDC_ERR_ARG;
+    return mdc_pass(h, true, y, x, nv, flags, (cudaStream_t)stream);
+}
+
+extern "C" int mdc_destroy(mdc_handle h) {
+    if (!h) return MDC_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_plan(h);
+    return MDC_OK;
+}
+
+extern "C" int mdc_timing(mdc_handle h, int enable) {
+    if (!h) return MDC_ERR_ARG;
+    TimingState& t = h->timing;
+    if (enable) {
+        if (t.pool.empty()) {
+            t.pool.resize(16384);
+            t.used_class.resize(t.pool.size());
+            for (auto& e : t.pool) {
+                MDC_CUDA_TRY(cudaEventCreate(&e.a));
+                MDC_CUDA_TRY(cudaEventCreate(&e.b));
+            }
+        }
+        t.used = 0;
+        for (int i = 0; i < MDC_KC_COUNT; ++i) t.launches[i] = t.recorded[i] = 0;
+    }
+    t.on = enable != 0;
+    return MDC_OK;
+}
+
+extern "C" int mdc_timing_read(mdc_handle h, int cls, double* total_ms, int64_t* launches) {
+    if (!h || cls < 0 || cls >= MDC_KC_COUNT) return MDC_ERR_ARG;
+    TimingState& t = h->timing;
+    double tot = 0.0;
+    for (size_t i = 0; i < t.used; ++i) {
+        if (t.used_class[i] != cls) continue;
+        MDC_CUDA_TRY(cudaEventSynchronize(t.pool[i].b));
+        float ms = 0.f;
+        MDC_CUDA_TRY(cudaEventElapsedTime(&ms, t.pool[i].a, t.pool[i].b));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = t.recorded[cls];
+    return MDC_OK;
+}
+
+extern "C" int64_t mdc_launch_count(mdc_handle h) { return h ? h->launch_count : -1; }

@@ -1,0 +1,120 @@
+// Internal definitions shared by the MDC library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/mdc.h"
+
+namespace mdc {
+
+// ------------------------------------------------------------------ small helpers
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// A scalar coefficient used by fused epilogues: value = h * (*d) when d is set, else h.
+struct Coef {
+    float h;
+    const double* d;
+};
+__device__ inline float coef(Coef c) { return c.d ? (float)((double)c.h * (*c.d)) : c.h; }
+inline Coef C1(float v) { return Coef{v, nullptr}; }
+inline Coef CD(float v, const double* d) { return Coef{v, d}; }
+
+// Pad of the kernel's row pitch (complex elements) so every row starts 512-byte aligned
+// in complex64 storage and whole 16-byte vectors never straddle a row end.
+constexpr int G_PITCH_ALIGN = 64;
+
+// ------------------------------------------------------------------ plan
+struct EventPair { cudaEvent_t a, b; };
+
+struct TimingState {
+    bool on = false;
+    std::vector<EventPair> pool;
+    std::vector<int> used_class;   // class of each used pair
+    size_t used = 0;
+    int64_t launches[MDC_KC_COUNT] = {0, 0, 0, 0, 0};
+    int64_t recorded[MDC_KC_COUNT] = {0, 0, 0, 0, 0};
+};
+
+}  // namespace mdc
+
+struct mdc_plan {
+    int nf, nr, ns, nt, logn;
+    double dt, dr;
+    int storage;
+    int64_t ldg;                // row pitch of the kernel copy, in complex elements
+    void* G = nullptr;          // library-owned kernel [nf][nr][ldg] in `storage` format
+    float* gscale = nullptr;    // [nf][nr] per-row scales (reduced storage), else null
+    float2* tw = nullptr;       // [nt/2] e^{-2 pi i j/nt}, from host float64
+    // scratch spectra, sized for nv_cap columns
+    int nv_cap = 0;
+    float2* specA = nullptr;    // [nf][max(nr,ns)][nv_cap]
+    float2* specB = nullptr;
+    int64_t launch_count = 0;
+    mdc::TimingState timing;
+};
+
+namespace mdc {
+
+// ------------------------------------------------------------------ launch bookkeeping
+struct LaunchScope {
+    mdc_plan* p; cudaStream_t s; int cls; EventPair* ev = nullptr;
+    LaunchScope(mdc_plan* p_, cudaStream_t s_, int cls_);
+    ~LaunchScope();
+};
+
+// ------------------------------------------------------------------ kernels (launchers)
+struct RfftArgs {
+    const float* x;        // [nt][C]
+    const float* x2;       // optional second input added to x (same layout), or null
+    int C, S, nv;          // C = S * nv real columns
+    int nt, logn, nf;
+    const int* cut;        // Theta cut-offs [C] applied to the input, or null
+    Coef scale;            // multiplies the input
+    int conj;              // conjugate the output spectrum (time reversal of the input)
+    float2* X;             // [nf][S][ldv]
+    int ldv, voff;
+    const float2* tw;
+    const int* active;     // if non-null and *active == 0 the kernel does nothing
+};
+struct IrfftArgs {
+    const float2* Y;       // [nf][S][ldv]
+    int ldv, voff;
+    int C, S, nv, nt, logn, nf;
+    int conj_in;           // conjugate the input spectrum before the inverse transform
+    float scale;           // multiplies the inverse transform (1/nt and dt*dr folded in)
+    float* out;            // [nt][C]
+    // epilogue: out = a_mdc * Theta * ifft + a_base * base + a_prev * out_old
+    Coef a_mdc, a_base, a_prev;
+    const float* base;
+    const int* cut;        // Theta on the transform term, or null
+    int reverse_out;       // write at (-t) mod nt
+    double* colsum;        // per-column sum of squares of out, or null
+    const float2* tw;
+    const int* active;
+};
+void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
+void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
+
+// Per-frequency products on the library layout.
+//   forward: Y[k][r][voff_o + j] = sum_s G[k][r][s] X[k][s][voff_i + j], j < ncol
+//   adjoint: X[k][s][voff_o + j] = sum_r conj(G[k][r][s]) Y[k][r][voff_i + j]
+void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
+                    float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
+                    const int* active);
+
+void set_cuda_error(cudaError_t e);
+
+}  // namespace mdc

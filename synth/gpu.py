@@ -1,0 +1,55 @@
+"""Generate the synthetic hyperbolic-event kernel directly on the GPU.
+
+Large kernels (tens of GB) cannot be evaluated on the host in reasonable time,
+so the workload library ``libsynth_gen.so`` evaluates the same formula as
+``synth.kernel`` on the device (phase reduced in float64, float32 output).
+The event parameters come from ``synth.draw``; the float64 table
+``scale * W(f_k)`` is computed here.  This is workload generation only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+import synth
+
+_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsynth_gen.so")
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise RuntimeError(f"{_LIB} missing: run `python -m paper_2011_11120_gb300.build`")
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.synth_kernel_c64.restype = ctypes.c_int
+        L.synth_kernel_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def kernel_on_device(cfg: synth.Config, d: synth.Draw = None, device="cuda", out=None) -> torch.Tensor:
+    """complex64 G[nf, nr, ns] on the device, same formula and draws as ``synth.kernel``."""
+    if d is None:
+        d = synth.draw(cfg)
+    L = _load()
+    if out is None:
+        out = torch.empty((cfg.nf, cfg.nr, cfg.ns), dtype=torch.complex64, device=device)
+    f = cfg.freqs
+    ws = np.ascontiguousarray(synth.ricker_spectrum(f) * d.scale, dtype=np.float64)
+    t0 = np.ascontiguousarray(d.t0, np.float64)
+    vel = np.ascontiguousarray(d.vel, np.float64)
+    amp = np.ascontiguousarray(d.amp, np.float64)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = L.synth_kernel_c64(ctypes.c_void_p(out.data_ptr()), cfg.nf, cfg.n_side, synth.GRID_DX,
+                            1.0 / (cfg.nt * cfg.dt), len(t0), dp(t0), dp(vel), dp(amp), dp(ws), stream)
+    if st != 0:
+        raise RuntimeError(f"synth_kernel_c64 failed ({st})")
+    return out

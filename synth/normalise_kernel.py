@@ -34,6 +34,8 @@ def sigma_max(Gk: np.ndarray, iters: int = 40, seed: int = 0) -> float:
     for _ in range(iters):
         w = Gk.conj().T @ (Gk @ v)
         s = np.linalg.norm(w)
+        if s == 0.0:
+            return 0.0
         v = w / s
     return float(np.sqrt(s))
 

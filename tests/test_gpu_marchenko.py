@@ -1,0 +1,101 @@
+"""GPU parity: Marchenko LSQR (Eq. 5) and Green's functions (Eq. 6) against the FP64 oracle.
+
+The kernel is normalised so that ||R||_2 = 0.5 (the redatuming workload's
+reading), which keeps M well conditioned; float32 vectors with float64 LSQR
+scalars then track the float64 oracle to relative L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import marchenko as omar
+from oracle import solvers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def problem(n_side, nt, nf, nv_grid, z, n_events=5, seed_number=95):
+    cfg = synth.Config(seed_number, "redatum-test", n_side, nt, 0.004, nf, n_events, nv_grid * nv_grid, z,
+                       point_grid=nv_grid)
+    d = synth.draw(cfg)
+    G = synth.kernel(cfg, d)
+    smax = max(np.linalg.norm(G[k], 2) for k in range(cfg.nf))
+    G *= 0.5 / (cfg.dt * cfg.dr * smax)
+    cut = synth.window_cutoffs(cfg, d)
+    fd = synth.direct_focusing(cfg, d)
+    return cfg, G, cut, fd
+
+
+def oracle_solve(cfg, G, cut, fd, niter, tol=0.0):
+    op = omar.Marchenko(G, cfg.dt, cfg.dr, cut, cfg.nt)
+    d = op.data(fd)
+    res = solvers.lsqr(op.matvec, op.rmatvec, d, niter=niter, tol=tol)
+    gm, gps, gp = op.greens(res.x[0], res.x[1], fd)
+    return res, gm, gp
+
+
+@pytest.mark.parametrize("n_side,nt,nf,nvg,z,niter", [
+    (3, 64, 20, 1, 120.0, 6),       # nv = 1: 2 columns per pass (GEMV)
+    (5, 128, 40, 2, 200.0, 10),     # nv = 4: 8 columns per pass (GEMM)
+    (21, 512, 150, 2, 800.0, 20),   # redatuming shapes at reduced aperture
+])
+def test_marchenko_lsqr_matches_oracle(n_side, nt, nf, nvg, z, niter):
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(n_side, nt, nf, nvg, z)
+    res, gm, gp = oracle_solve(cfg, G, cut, fd, niter)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    out = op.marchenko(torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda(), niter)
+    op.close()
+    assert out["iters"] == res.iters == niter
+    assert rel(out["f_minus"].cpu().numpy(), res.x[0]) <= TOL
+    assert rel(out["f_mplus"].cpu().numpy(), res.x[1]) <= TOL
+    assert rel(out["g_minus"].cpu().numpy(), gm) <= TOL
+    assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL
+    assert np.allclose(out["resid"], res.resid, rtol=TOL, atol=0)
+
+
+def test_marchenko_tolerance_stop_matches_oracle():
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(5, 128, 40, 2, 200.0)
+    res, _, _ = oracle_solve(cfg, G, cut, fd, niter=50, tol=1e-4)
+    assert 1 < res.iters < 50
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    out = op.marchenko(torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda(), 50, tol=1e-4, greens=False)
+    op.close()
+    assert out["iters"] == res.iters
+    assert all(r == -1.0 for r in out["resid"][res.iters + 1:])
+    assert rel(out["f_minus"].cpu().numpy(), res.x[0]) <= TOL
+
+
+def test_marchenko_zero_window_gives_zero_solution():
+    """Theta = 0: d = 0, so x = 0 and Eq. 6 reduces to g- = R f_d+, g+ = P f_d+."""
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(3, 64, 20, 1, 120.0)
+    cut0 = np.zeros_like(cut)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    out = op.marchenko(torch.from_numpy(cut0).cuda(), torch.from_numpy(fd).cuda(), 5)
+    op.close()
+    assert out["iters"] == 0
+    assert float(out["f_minus"].abs().max()) == 0.0 and float(out["f_mplus"].abs().max()) == 0.0
+    ref = omar.Marchenko(G, cfg.dt, cfg.dr, cut0, cfg.nt)
+    _, _, gp = ref.greens(np.zeros_like(fd, np.float64), np.zeros_like(fd, np.float64), fd)
+    assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL
+    assert rel(out["g_minus"].cpu().numpy(), ref.R(fd)) <= TOL
+
+
+def test_marchenko_rejects_rectangular_kernel():
+    import paper_2011_11120_gb300 as m
+    G = torch.zeros((5, 3, 4), dtype=torch.complex64, device="cuda")
+    op = m.MDC(G, 64, 0.004, 1.0)
+    fd = torch.zeros((64, 4, 1), device="cuda")
+    with pytest.raises(m.MDCError):
+        op.marchenko(torch.zeros((4, 1), dtype=torch.int32, device="cuda"), fd, 3)
+    op.close()
