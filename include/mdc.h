@@ -106,6 +106,37 @@ int mdc_adjoint(mdc_handle h, const float* y, float* x, int nv, unsigned flags, 
 int mdc_reserve(mdc_handle h, int nv_max);
 
 /*
+ * mdc_forward_static_scratch -- y = C x (or R* x with MDC_CONJ_KERNEL) exactly as
+ * mdc_forward, but without allocating anything: the two frequency-domain work
+ * arrays live in one fixed device array compiled into the library instead of in
+ * memory the handle obtains with cudaMalloc.  The paper has no counterpart; this
+ * is a deployment variant of the forward pass.
+ *
+ * Who needs it: callers that cannot call cudaMalloc when they apply the operator:
+ * services whose device memory is entirely pre-reserved by their own pool allocator
+ * (a framework's caching allocator, a fixed per-tenant budget), so that a library
+ * allocation would fail or break their accounting; and latency-critical loops that
+ * cannot afford the device-wide synchronisation a cudaMalloc implies.  mdc_forward,
+ * by contrast, allocates on its first call with a larger nv.
+ *
+ * Limit: nfmax * max(nr, ns) * nv <= MDC_STATIC_SCRATCH_COMPLEX (2^21 complex
+ * values per work array; the fixed array is 32 MiB).  Larger requests return
+ * MDC_ERR_BUDGET and launch nothing.  Every device that loads the library holds
+ * the 32 MiB until the process exits.
+ * Set-up: the first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  Later calls do no set-up.
+ * Sharing: all calls on a device use the same array and it keeps the last call's
+ * contents; every call overwrites all of it that it reads, so nothing needs
+ * clearing.  Calls whose execution overlaps on the GPU (different streams without
+ * ordering between them) race on the array and give wrong results: order them.
+ * Arguments, layout, ownership and errors are otherwise those of mdc_forward.
+ */
+#define MDC_STATIC_SCRATCH_COMPLEX (1 << 21)
+int mdc_forward_static_scratch(mdc_handle h, const float* x, float* y, int nv, unsigned flags,
+                               void* stream);
+
+/*
  * marchenko_lsqr -- solve the Marchenko system of Eq. 5 by LSQR and evaluate Eq. 6.
  *
  *   d = M f,  M = [[I, -Theta R], [-Theta R*, I]],  d = [Theta R f_d+ ; 0],

@@ -32,6 +32,7 @@ SIGNATURES = {
     "mdc_forward": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_adjoint": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_reserve": (_i, [_vp, _i]),
+    "mdc_forward_static_scratch": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "marchenko_lsqr": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp,
                             ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
     "mdc_destroy": (_i, [_vp]),
@@ -115,6 +116,13 @@ def mdc_forward(h, x: torch.Tensor, y: torch.Tensor, nv: int, flags: int = 0, st
 def mdc_adjoint(h, y: torch.Tensor, x: torch.Tensor, nv: int, flags: int = 0, stream=None) -> None:
     _check(lib().mdc_adjoint(h, _ptr(y, torch.float32, "y"), _ptr(x, torch.float32, "x"), nv, flags,
                              _stream(stream)), "mdc_adjoint")
+
+
+def mdc_forward_static_scratch(h, x: torch.Tensor, y: torch.Tensor, nv: int, flags: int = 0,
+                               stream=None) -> None:
+    """mdc_forward without any device allocation (fixed 32 MiB library work array)."""
+    _check(lib().mdc_forward_static_scratch(h, _ptr(x, torch.float32, "x"), _ptr(y, torch.float32, "y"), nv,
+                                            flags, _stream(stream)), "mdc_forward_static_scratch")
 
 
 def mdc_reserve(h, nv_max: int) -> None:
