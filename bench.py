@@ -153,6 +153,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = synth.config(args.config, nv=args.nv)
+    if args.nf:
+        cfg = cfg.with_(nf=args.nf)
     from oracle import mdc as omdc
     d = synth.draw(cfg)
     rows = 8
@@ -209,6 +211,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     cfg = synth.config(args.config, nv=args.nv)
+    if args.nf:
+        cfg = cfg.with_(nf=args.nf)
     nv = args.nv
     d = synth.draw(cfg)
     G = sgpu.kernel_on_device(cfg, d)
@@ -322,6 +326,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--nv", type=int, default=1)
     ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--nf", type=int, default=0, help="override nfmax (smaller profiling case)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
