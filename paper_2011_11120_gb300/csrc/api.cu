@@ -92,7 +92,7 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
     *out = nullptr;
     if (!G || nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
     if (!(dt > 0.0) || !(dr > 0.0) || !std::isfinite(dt) || !std::isfinite(dr)) return MDC_ERR_ARG;
-    if (storage != MDC_C64) return MDC_ERR_ARG;   // reduced storage: see mdc_create_lowp
+    if (storage < MDC_C64 || storage > MDC_CE4M3) return MDC_ERR_ARG;
     if ((int64_t)nr * nfmax > (int64_t)1 << 31) return MDC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     mdc_plan* p = new (std::nothrow) mdc_plan();
@@ -100,14 +100,22 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
     p->nf = nfmax; p->nr = nr; p->ns = ns; p->nt = nt; p->logn = ilog2(nt);
     p->dt = dt; p->dr = dr; p->storage = storage;
     p->ldg = round_up(ns, G_PITCH_ALIGN);
-    const size_t rowbytes = (size_t)p->ldg * sizeof(float2);
+    const size_t rowbytes = (size_t)p->ldg * storage_bytes(storage);
     cudaError_t e = cudaMalloc(&p->G, rowbytes * nr * nfmax);
-    if (e == cudaSuccess) e = cudaMemcpy2DAsync(p->G, rowbytes, G, (size_t)ns * sizeof(float2),
-                                                (size_t)ns * sizeof(float2), (size_t)nr * nfmax,
-                                                cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess && p->ldg > ns)
-        e = cudaMemset2DAsync((char*)p->G + (size_t)ns * sizeof(float2), rowbytes, 0,
-                              (size_t)(p->ldg - ns) * sizeof(float2), (size_t)nr * nfmax, s);
+    if (storage == MDC_C64) {
+        if (e == cudaSuccess) e = cudaMemcpy2DAsync(p->G, rowbytes, G, (size_t)ns * sizeof(float2),
+                                                    (size_t)ns * sizeof(float2), (size_t)nr * nfmax,
+                                                    cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && p->ldg > ns)
+            e = cudaMemset2DAsync((char*)p->G + (size_t)ns * sizeof(float2), rowbytes, 0,
+                                  (size_t)(p->ldg - ns) * sizeof(float2), (size_t)nr * nfmax, s);
+    } else {
+        if (e == cudaSuccess) e = cudaMalloc(&p->gscale, sizeof(float) * (size_t)nr * nfmax);
+        if (e == cudaSuccess) {
+            launch_quantize(p, static_cast<const float2*>(G), s);
+            e = cudaGetLastError();
+        }
+    }
     if (e == cudaSuccess) {
         std::vector<float2> tw(nt / 2);
         for (int j = 0; j < nt / 2; ++j) {

@@ -115,6 +115,14 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
                     float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
                     const int* active);
 
+// Quantise a complex64 kernel [nf][nr][ns] into the plan's reduced-storage copy and row scales.
+void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s);
+
+// Bytes of one stored complex value.
+inline int storage_bytes(int storage) {
+    return storage == MDC_C64 ? 8 : (storage == MDC_CE4M3 ? 2 : 4);
+}
+
 void set_cuda_error(cudaError_t e);
 
 }  // namespace mdc

@@ -16,12 +16,56 @@
 #include "common.cuh"
 
 namespace mdc {
+
+// Largest column count served by the GEMV kernels.
+int gemv_max_columns() { return 4; }
+
 namespace {
 
 constexpr int GEMV_THREADS = 256;
 constexpr int FWD_ROWS_PER_CTA = 64;
 
-__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+// Storage formats of the kernel copy: complex values per 16-byte vector and decoding.
+template <int FMT> struct Fmt;
+template <> struct Fmt<MDC_C64> { static constexpr int CPV = 2; };
+template <> struct Fmt<MDC_C16F> { static constexpr int CPV = 4; };
+template <> struct Fmt<MDC_CBF16> { static constexpr int CPV = 4; };
+template <> struct Fmt<MDC_CE4M3> { static constexpr int CPV = 8; };
+
+__device__ __forceinline__ float2 dec_h2(unsigned w) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 dec_b2(unsigned w) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+    return __bfloat1622float2(h);
+}
+__device__ __forceinline__ float2 dec_e4m3x2(unsigned short w) {
+    __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)w, __NV_E4M3);
+    return __half22float2(__half2(r));
+}
+
+// Decode one 16-byte vector into CPV complex values (in storage units; row scale applied elsewhere).
+template <int FMT>
+__device__ __forceinline__ void decode(const uint4& v, float2* c) {
+    if constexpr (FMT == MDC_C64) {
+        c[0] = make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
+        c[1] = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
+    } else if constexpr (FMT == MDC_C16F) {
+        c[0] = dec_h2(v.x); c[1] = dec_h2(v.y); c[2] = dec_h2(v.z); c[3] = dec_h2(v.w);
+    } else if constexpr (FMT == MDC_CBF16) {
+        c[0] = dec_b2(v.x); c[1] = dec_b2(v.y); c[2] = dec_b2(v.z); c[3] = dec_b2(v.w);
+    } else {
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            c[2 * q] = dec_e4m3x2((unsigned short)(w[q] & 0xffffu));
+            c[2 * q + 1] = dec_e4m3x2((unsigned short)(w[q] >> 16));
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.x = fmaf(a.x, b.x, acc.x);
@@ -37,6 +81,10 @@ __device__ __forceinline__ void cfma_conj(float2& acc, float2 a, float2 b) {
     acc.y = fmaf(-a.y, b.x, acc.y);
 }
 
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+
+// complex64 specialisations: one warp per row, X(w) interleaved in shared memory (C64 keeps
+// two complex values per vector, so lanes already read distinct words).
 template <int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_c64(
     const float4* __restrict__ G, int ldg, int nr, int ns,
@@ -167,22 +215,197 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
     }
 }
 
+// Forward GEMV.  X(w) is staged de-interleaved by vector lane position:
+// xs[(j * nvec + i) * NVC + v] = X[CPV * i + j][v], so the 32 lanes of a warp, which
+// hold vectors i..i+31, read consecutive shared-memory words for every j.
+template <int FMT, int NVC>
+__global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
+    const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
+    const float2* __restrict__ X, int ldi, int voff_i,
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active) {
+    constexpr int CPV = Fmt<FMT>::CPV;
+    if (active && *active == 0) return;
+    extern __shared__ __align__(16) float2 xs[];
+    const int k = blockIdx.y;
+    const int nvec = ldg / CPV;
+    const float2* Xk = X + (size_t)k * ns * ldi + voff_i;
+    for (int e = threadIdx.x; e < ldg * NVC; e += GEMV_THREADS) {
+        const int s = e / NVC, v = e - s * NVC;
+        const int i = s / CPV, j = s - i * CPV;
+        xs[(j * nvec + i) * NVC + v] = s < ns ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * FWD_ROWS_PER_CTA;
+    const int r1 = min(r0 + FWD_ROWS_PER_CTA, nr);
+    for (int r = r0 + warp; r < r1; r += GEMV_THREADS / 32) {
+        const uint4* g = G + ((size_t)k * nr + r) * nvec;
+        float2 acc[NVC];
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) acc[v] = make_float2(0.f, 0.f);
+        int i = lane;
+        for (; i + 96 < nvec; i += 128) {
+            uint4 gv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gv[u] = ld_stream(g + i + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float2 c[CPV];
+                decode<FMT>(gv[u], c);
+#pragma unroll
+                for (int j = 0; j < CPV; ++j)
+#pragma unroll
+                    for (int v = 0; v < NVC; ++v) cfma(acc[v], c[j], xs[(j * nvec + i + 32 * u) * NVC + v]);
+            }
+        }
+        for (; i < nvec; i += 32) {
+            float2 c[CPV];
+            decode<FMT>(ld_stream(g + i), c);
+#pragma unroll
+            for (int j = 0; j < CPV; ++j)
+#pragma unroll
+                for (int v = 0; v < NVC; ++v) cfma(acc[v], c[j], xs[(j * nvec + i) * NVC + v]);
+        }
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc[v].x += __shfl_xor_sync(0xffffffffu, acc[v].x, off);
+                acc[v].y += __shfl_xor_sync(0xffffffffu, acc[v].y, off);
+            }
+        }
+        if (lane == 0) {
+            const float sc = (FMT == MDC_C64) ? 1.f : gscale[(size_t)k * nr + r];
+            float2* y = Y + ((size_t)k * nr + r) * ldo + voff_o;
+#pragma unroll
+            for (int v = 0; v < NVC; ++v) y[v] = make_float2(acc[v].x * sc, acc[v].y * sc);
+        }
+    }
+}
+
+// Adjoint GEMV: a CTA owns TILE = 32 * CPV adjacent columns s of one frequency (one 512-byte
+// segment of every row); warp w walks rows r = w, w + 8, ...; the row scale is folded into Y.
+template <int FMT, int NVC>
+__global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
+    const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
+    const float2* __restrict__ Yin, int ldi, int voff_i,
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active) {
+    constexpr int CPV = Fmt<FMT>::CPV;
+    constexpr int TILE = 32 * CPV;
+    constexpr int W = GEMV_THREADS / 32;
+    if (active && *active == 0) return;
+    extern __shared__ __align__(16) float2 ys[];   // [nr][NVC], then reduction space
+    const int k = blockIdx.y;
+    const int s0 = blockIdx.x * TILE;
+    const float2* Yk = Yin + (size_t)k * nr * ldi + voff_i;
+    for (int e = threadIdx.x; e < nr * NVC; e += GEMV_THREADS) {
+        const int r = e / NVC, v = e - r * NVC;
+        float2 y = Yk[(size_t)r * ldi + v];
+        if (FMT != MDC_C64) {
+            const float sc = gscale[(size_t)k * nr + r];
+            y.x *= sc;
+            y.y *= sc;
+        }
+        ys[e] = y;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvec = ldg / CPV;
+    const bool live = s0 + CPV * lane < ldg;
+    const uint4* g = G + (size_t)k * nr * nvec + (s0 / CPV) + lane;
+    float2 acc[CPV][NVC];
+#pragma unroll
+    for (int j = 0; j < CPV; ++j)
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) acc[j][v] = make_float2(0.f, 0.f);
+    if (live) {
+        int r = warp;
+        for (; r + 3 * W < nr; r += 4 * W) {
+            uint4 gv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gv[u] = ld_stream(g + (size_t)(r + u * W) * nvec);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float2 c[CPV];
+                decode<FMT>(gv[u], c);
+#pragma unroll
+                for (int v = 0; v < NVC; ++v) {
+                    const float2 y = ys[(r + u * W) * NVC + v];
+#pragma unroll
+                    for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c[j], y);
+                }
+            }
+        }
+        for (; r < nr; r += W) {
+            float2 c[CPV];
+            decode<FMT>(ld_stream(g + (size_t)r * nvec), c);
+#pragma unroll
+            for (int v = 0; v < NVC; ++v) {
+                const float2 y = ys[r * NVC + v];
+#pragma unroll
+                for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c[j], y);
+            }
+        }
+    }
+    __syncthreads();
+    float2* red = ys;   // reuse: W * TILE * NVC float2 (the launcher sizes shared memory for it)
+#pragma unroll
+    for (int j = 0; j < CPV; ++j)
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) red[(warp * TILE + CPV * lane + j) * NVC + v] = acc[j][v];
+    __syncthreads();
+    for (int e = threadIdx.x; e < TILE * NVC; e += GEMV_THREADS) {
+        const int sl = e / NVC, v = e - sl * NVC;
+        const int s = s0 + sl;
+        float2 tot = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < W; ++w) tot = cadd(tot, red[(w * TILE + sl) * NVC + v]);
+        if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
+    }
+}
+
 // ------------------------------------------------------------------ SIMT complex GEMM
 constexpr int GBM = 64, GBN = 64, GBK = 8;
 
-template <bool ADJ>
+template <int FMT> struct Bytes;
+template <> struct Bytes<MDC_C64> { static constexpr int v = 8; };
+template <> struct Bytes<MDC_C16F> { static constexpr int v = 4; };
+template <> struct Bytes<MDC_CBF16> { static constexpr int v = 4; };
+template <> struct Bytes<MDC_CE4M3> { static constexpr int v = 2; };
+
+// Two consecutive complex values starting at (even) element e of a kernel row.
+template <int FMT>
+__device__ __forceinline__ void load2(const unsigned char* row, int e, float2& c0, float2& c1) {
+    if constexpr (FMT == MDC_C64) {
+        const float4 v = *reinterpret_cast<const float4*>(row + (size_t)e * 8);
+        c0 = make_float2(v.x, v.y);
+        c1 = make_float2(v.z, v.w);
+    } else if constexpr (FMT == MDC_C16F || FMT == MDC_CBF16) {
+        const uint2 v = *reinterpret_cast<const uint2*>(row + (size_t)e * 4);
+        if constexpr (FMT == MDC_C16F) { c0 = dec_h2(v.x); c1 = dec_h2(v.y); }
+        else { c0 = dec_b2(v.x); c1 = dec_b2(v.y); }
+    } else {
+        const unsigned v = *reinterpret_cast<const unsigned*>(row + (size_t)e * 2);
+        c0 = dec_e4m3x2((unsigned short)(v & 0xffffu));
+        c1 = dec_e4m3x2((unsigned short)(v >> 16));
+    }
+}
+
+template <int FMT, bool ADJ>
 __global__ void __launch_bounds__(256) cgemm_simt(
-    const float2* __restrict__ G, int ldg, int nr, int ns,
+    const unsigned char* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ B, int ldb, int voff_b,
     float2* __restrict__ Cm, int ldc, int voff_c, int N, const int* active) {
     if (active && *active == 0) return;
+    constexpr int BPC = Bytes<FMT>::v;
     const int M = ADJ ? ns : nr;
     const int K = ADJ ? nr : ns;
     const int k = blockIdx.z;
     const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
     __shared__ __align__(16) float2 As[GBK][GBM];
     __shared__ __align__(16) float2 Bs[GBK][GBN];
-    const float2* Gk = G + (size_t)k * nr * ldg;
+    const unsigned char* Gk = G + (size_t)k * nr * ldg * BPC;
+    const float* sck = gscale + (size_t)k * nr;
     const float2* Bk = B + (size_t)k * K * ldb + voff_b;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     float2 acc[4][4];
@@ -192,19 +415,23 @@ __global__ void __launch_bounds__(256) cgemm_simt(
         for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
     for (int kt = 0; kt < K; kt += GBK) {
-        // A tile -> As[kk][m]
         if (!ADJ) {
             const int m = tid >> 2, kq = (tid & 3) * 2;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m0 + m < M) v = *reinterpret_cast<const float4*>(Gk + (size_t)(m0 + m) * ldg + kt + kq);
-            As[kq][m] = make_float2(v.x, v.y);
-            As[kq + 1][m] = make_float2(v.z, v.w);
+            float2 c0 = make_float2(0.f, 0.f), c1 = c0;
+            if (m0 + m < M) load2<FMT>(Gk + (size_t)(m0 + m) * ldg * BPC, kt + kq, c0, c1);
+            As[kq][m] = c0;
+            As[kq + 1][m] = c1;
         } else {
             const int kk = tid >> 5, mq = (tid & 31) * 2;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (kt + kk < K) v = *reinterpret_cast<const float4*>(Gk + (size_t)(kt + kk) * ldg + m0 + mq);
-            As[kk][mq] = make_float2(v.x, -v.y);
-            As[kk][mq + 1] = make_float2(v.z, -v.w);
+            float2 c0 = make_float2(0.f, 0.f), c1 = c0;
+            if (kt + kk < K) {
+                load2<FMT>(Gk + (size_t)(kt + kk) * ldg * BPC, m0 + mq, c0, c1);
+                const float sc = (FMT == MDC_C64) ? 1.f : sck[kt + kk];
+                c0 = make_float2(c0.x * sc, -c0.y * sc);
+                c1 = make_float2(c1.x * sc, -c1.y * sc);
+            }
+            As[kk][mq] = c0;
+            As[kk][mq + 1] = c1;
         }
         {
             const int kk = tid >> 5, nq = (tid & 31) * 2;
@@ -236,62 +463,82 @@ __global__ void __launch_bounds__(256) cgemm_simt(
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
+        const float sc = (FMT == MDC_C64 || ADJ) ? 1.f : sck[m];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + 16 * j;
-            if (n < N) Cm[((size_t)k * M + m) * ldc + voff_c + n] = acc[i][j];
+            if (n < N)
+                Cm[((size_t)k * M + m) * ldc + voff_c + n] = make_float2(acc[i][j].x * sc, acc[i][j].y * sc);
         }
     }
 }
 
-template <int NVC>
+template <int FMT, int NVC>
 void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                      int voff_o, cudaStream_t s, const int* active) {
     const size_t smem = (size_t)p->ldg * NVC * sizeof(float2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemv_fwd_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(gemv_fwd<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr = true;
     }
     dim3 grid((p->nr + FWD_ROWS_PER_CTA - 1) / FWD_ROWS_PER_CTA, p->nf);
-    gemv_fwd_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
-        reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-        voff_o, active);
+    if constexpr (FMT == MDC_C64) {
+        static bool attr64 = false;
+        if (!attr64) {
+            cudaFuncSetAttribute(gemv_fwd_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            attr64 = true;
+        }
+        gemv_fwd_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
+            reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
+            voff_o, active);
+        return;
+    }
+    gemv_fwd<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
+        reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
+        ldo, voff_o, active);
 }
 
-template <int NVC>
+template <int FMT, int NVC>
 void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                      int voff_o, cudaStream_t s, const int* active) {
+    constexpr int TILE = 32 * Fmt<FMT>::CPV;
     size_t smem = (size_t)p->nr * NVC * sizeof(float2);
-    const size_t red = (size_t)(GEMV_THREADS / 32) * ADJ_TILE * NVC * sizeof(float2);
+    const size_t red = (size_t)(GEMV_THREADS / 32) * TILE * NVC * sizeof(float2);
     if (smem < red) smem = red;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemv_adj_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(gemv_adj<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr = true;
     }
-    dim3 grid((unsigned)(p->ldg / ADJ_TILE), p->nf);
-    gemv_adj_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
-        reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-        voff_o, active);
+    dim3 grid((unsigned)((p->ldg + TILE - 1) / TILE), p->nf);
+    if constexpr (FMT == MDC_C64) {
+        static bool attr64 = false;
+        if (!attr64) {
+            cudaFuncSetAttribute(gemv_adj_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+            attr64 = true;
+        }
+        gemv_adj_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
+            reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
+            voff_o, active);
+        return;
+    }
+    gemv_adj<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
+        reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
+        ldo, voff_o, active);
 }
 
-}  // namespace
-
-// Largest column count served by the GEMV kernels (shared memory holds ldg * NVC complex).
-int gemv_max_columns() { return 4; }
-
-void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
-                    float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
-                    const int* active) {
-    LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
-    // the GEMV stages one frequency's input block (ldg or nr rows x ncol) in shared memory
+template <int FMT>
+void product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
+                 int voff_o, int ncol, cudaStream_t s, const int* active) {
+    constexpr int TILE = 32 * Fmt<FMT>::CPV;
     const int64_t stage = (int64_t)(adjoint ? p->nr : p->ldg) * ncol * (int64_t)sizeof(float2);
-    if (ncol <= gemv_max_columns() && stage <= 200 * 1024) {
-#define MDC_GEMV_CASE(n)                                                                  \
-    case n:                                                                               \
-        if (adjoint) gemv_adj_launch<n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active); \
-        else gemv_fwd_launch<n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active);         \
+    const int64_t red = (int64_t)(GEMV_THREADS / 32) * TILE * ncol * (int64_t)sizeof(float2);
+    if (ncol <= gemv_max_columns() && stage <= 200 * 1024 && red <= 200 * 1024) {
+#define MDC_GEMV_CASE(n)                                                                       \
+    case n:                                                                                    \
+        if (adjoint) gemv_adj_launch<FMT, n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active); \
+        else gemv_fwd_launch<FMT, n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active);         \
         break;
         switch (ncol) {
             MDC_GEMV_CASE(1)
@@ -304,13 +551,79 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
     }
     const int M = adjoint ? p->ns : p->nr;
     dim3 grid((ncol + GBN - 1) / GBN, (M + GBM - 1) / GBM, p->nf);
-    const float2* G = reinterpret_cast<const float2*>(p->G);
+    const unsigned char* G = reinterpret_cast<const unsigned char*>(p->G);
     if (adjoint)
-        cgemm_simt<true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-                                              voff_o, ncol, active);
+        cgemm_simt<FMT, true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
+                                                   out, ldo, voff_o, ncol, active);
     else
-        cgemm_simt<false><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-                                               voff_o, ncol, active);
+        cgemm_simt<FMT, false><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
+                                                    out, ldo, voff_o, ncol, active);
+}
+
+}  // namespace
+
+void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
+                    float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
+                    const int* active) {
+    LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
+    switch (p->storage) {
+        case MDC_C64: product_fmt<MDC_C64>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+        case MDC_C16F: product_fmt<MDC_C16F>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+        case MDC_CBF16: product_fmt<MDC_CBF16>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+        default: product_fmt<MDC_CE4M3>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+    }
+}
+
+// ------------------------------------------------------------------ quantiser
+// One CTA per kernel row (k, r): scale = max_s max(|Re|, |Im|) / QMAX, q = RNE(G / scale),
+// saturating for E4M3.  QMAX = 32768 (FP16: keeps the row far from subnormals), 1 (BF16),
+// 448 (E4M3 largest finite).  Padding columns s >= ns are written as zeros.
+template <int FMT>
+__global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ G, int ns, int ldg,
+                                                     unsigned char* __restrict__ Q, float* __restrict__ scale) {
+    constexpr float QMAX = FMT == MDC_C16F ? 32768.f : (FMT == MDC_CBF16 ? 1.f : 448.f);
+    const size_t row = blockIdx.x;
+    const float2* g = G + row * ns;
+    float m = 0.f;
+    for (int s = threadIdx.x; s < ns; s += 256) {
+        const float2 v = g[s];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const float rowmax = red[0];
+    const float sc = rowmax > 0.f ? rowmax / QMAX : 0.f;
+    const float inv = rowmax > 0.f ? QMAX / rowmax : 0.f;
+    if (threadIdx.x == 0) scale[row] = sc;
+    for (int s = threadIdx.x; s < ldg; s += 256) {
+        float2 v = s < ns ? g[s] : make_float2(0.f, 0.f);
+        v.x *= inv;
+        v.y *= inv;
+        if constexpr (FMT == MDC_C16F) {
+            reinterpret_cast<__half2*>(Q)[row * ldg + s] = __floats2half2_rn(v.x, v.y);
+        } else if constexpr (FMT == MDC_CBF16) {
+            reinterpret_cast<__nv_bfloat162*>(Q)[row * ldg + s] = __floats2bfloat162_rn(v.x, v.y);
+        } else {
+            reinterpret_cast<__nv_fp8x2_storage_t*>(Q)[row * ldg + s] =
+                __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
+void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s) {
+    const unsigned rows = (unsigned)((int64_t)p->nf * p->nr);
+    unsigned char* Q = reinterpret_cast<unsigned char*>(p->G);
+    switch (p->storage) {
+        case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
+        case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
+        case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
+        default: break;
+    }
 }
 
 }  // namespace mdc
