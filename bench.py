@@ -37,8 +37,11 @@ METRIC = "MDC fwd+adj HBM GB/s vs peak; redatum solves/s and p99 at <=1e-3 vs FP
 UNIT = "GB/s"
 
 
-def algorithmic_bytes(cfg, nv):
-    kernel = cfg.nf * cfg.nr * cfg.ns * 8
+BYTES_PER_COMPLEX = {"c64": 8, "c16f": 4, "cbf16": 4, "ce4m3": 2}
+
+
+def algorithmic_bytes(cfg, nv, storage="c64"):
+    kernel = cfg.nf * cfg.nr * cfg.ns * BYTES_PER_COMPLEX[storage]
     traces = cfg.nt * (cfg.nr + cfg.ns) * nv * 4
     return 2 * (kernel + traces), kernel
 
@@ -191,11 +194,11 @@ def run_reference(args):
     return 0
 
 
-def config_block(cfg, nv):
+def config_block(cfg, nv, storage="c64"):
     return {"workload": f"MDC fwd+adj, nr=ns={cfg.nr} ({cfg.n_side}x{cfg.n_side}, 20 m), nt={cfg.nt}, "
-                        f"dt={cfg.dt}, nfmax={cfg.nf}, {cfg.n_events} hyperbolic events, complex64 kernel "
-                        f"{cfg.nf * cfg.nr * cfg.ns * 8 / 1e9:.2f} GB, nv={nv}",
-            "nr": cfg.nr, "ns": cfg.ns, "nt": cfg.nt, "nfmax": cfg.nf, "nv": nv, "storage": "c64",
+                        f"dt={cfg.dt}, nfmax={cfg.nf}, {cfg.n_events} hyperbolic events, {storage} kernel "
+                        f"{cfg.nf * cfg.nr * cfg.ns * BYTES_PER_COMPLEX[storage] / 1e9:.2f} GB, nv={nv}",
+            "nr": cfg.nr, "ns": cfg.ns, "nt": cfg.nt, "nfmax": cfg.nf, "nv": nv, "storage": storage,
             "l2": "inputs larger than L2 (kernel streamed every pass)"}
 
 
@@ -216,7 +219,7 @@ def run_ours(args):
     nv = args.nv
     d = synth.draw(cfg)
     G = sgpu.kernel_on_device(cfg, d)
-    op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr)
+    op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.storage)
     del G
     torch.cuda.empty_cache()
     mdc.mdc_reserve(op.h, nv)
@@ -234,7 +237,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    bytes_step, kernel_bytes = algorithmic_bytes(cfg, nv)
+    bytes_step, kernel_bytes = algorithmic_bytes(cfg, nv, args.storage)
 
     # ---- device-timed region
     sampler = ClockSampler(local)
@@ -261,6 +264,7 @@ def run_ours(args):
         t, n = mdc.mdc_timing_read(op.h, name)
         kern[name] = {"ms_total": t, "launches": n, "ms_avg": t / n if n else None}
     mdc.mdc_timing(op.h, False)
+    mdc.mdc_device_status(op.h)
 
     # ---- end-to-end: pinned host input -> device, fwd+adj, result -> pinned host, every step
     for _ in range(2):
@@ -299,10 +303,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(config_block(cfg, nv), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "config": dict(config_block(cfg, nv, args.storage), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
-                     "kernel": "per-frequency product (forward GEMV + adjoint GEMV, c64)",
+                     "kernel": f"per-frequency product (forward + adjoint, {args.storage}, {nv} column(s))",
                      "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
         "kernels": kern,
@@ -327,6 +331,7 @@ def main():
     ap.add_argument("--nv", type=int, default=1)
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--nf", type=int, default=0, help="override nfmax (smaller profiling case)")
+    ap.add_argument("--storage", default="c64", choices=["c64", "c16f", "cbf16", "ce4m3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

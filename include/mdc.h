@@ -186,6 +186,9 @@ int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage);
  * kernels the handle has launched since creation (timing on or off).
  */
 int mdc_timing(mdc_handle h, int enable);
+/* mdc_device_status -- synchronise `stream` and report MDC_ERR_TIMEOUT if a kernel of this
+ * handle gave up a bounded device-side wait since the last check (the flag is then cleared). */
+int mdc_device_status(mdc_handle h, void* stream);
 int mdc_timing_read(mdc_handle h, int kernel_class, double* total_ms, int64_t* launches);
 int64_t mdc_launch_count(mdc_handle h);
 

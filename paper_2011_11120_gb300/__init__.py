@@ -42,6 +42,7 @@ SIGNATURES = {
     "mdc_timing": (_i, [_vp, _i]),
     "mdc_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "mdc_launch_count": (_i64, [_vp]),
+    "mdc_device_status": (_i, [_vp, _vp]),
 }
 
 _lib = None
@@ -165,6 +166,11 @@ def mdc_timing_read(h, kernel_class) -> tuple:
 
 def mdc_launch_count(h) -> int:
     return int(lib().mdc_launch_count(h))
+
+
+def mdc_device_status(h, stream=None) -> None:
+    """Raise MDCError(MDC_ERR_TIMEOUT) if a bounded device wait of this handle gave up."""
+    _check(lib().mdc_device_status(h, _stream(stream)), "mdc_device_status")
 
 
 # ------------------------------------------------------------------ convenience wrapper

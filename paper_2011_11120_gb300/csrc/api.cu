@@ -79,6 +79,9 @@ static void free_plan(mdc_plan* p) {
     cudaFree(p->tw);
     cudaFree(p->specA);
     cudaFree(p->specB);
+    cudaFree(p->tcB);
+    cudaFree(p->tcSigma);
+    cudaFree(p->err_flag);
     for (auto& e : p->timing.pool) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -116,6 +119,8 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
             e = cudaGetLastError();
         }
     }
+    if (e == cudaSuccess) e = cudaMalloc(&p->err_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->err_flag, 0, sizeof(int), s);
     if (e == cudaSuccess) {
         std::vector<float2> tw(nt / 2);
         for (int j = 0; j < nt / 2; ++j) {
@@ -138,22 +143,41 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
 }
 
 int mdc::ensure_scratch(mdc_plan* p, int ncols) {
-    if (ncols <= p->nv_cap) return MDC_OK;
-    const size_t n = (size_t)p->nf * (size_t)(p->nr > p->ns ? p->nr : p->ns) * ncols;
-    float2 *a = nullptr, *b = nullptr;
-    cudaError_t e = cudaMalloc(&a, n * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&b, n * sizeof(float2));
-    if (e != cudaSuccess) {
-        cudaFree(a);
-        cudaGetLastError();
-        set_cuda_error(e);
-        return MDC_ERR_OOM;
+    if (ncols > p->nv_cap) {
+        const size_t n = (size_t)p->nf * (size_t)(p->nr > p->ns ? p->nr : p->ns) * ncols;
+        float2 *a = nullptr, *b = nullptr;
+        cudaError_t e = cudaMalloc(&a, n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&b, n * sizeof(float2));
+        if (e != cudaSuccess) {
+            cudaFree(a);
+            cudaGetLastError();
+            set_cuda_error(e);
+            return MDC_ERR_OOM;
+        }
+        cudaFree(p->specA);
+        cudaFree(p->specB);
+        p->specA = a;
+        p->specB = b;
+        p->nv_cap = ncols;
     }
-    cudaFree(p->specA);
-    cudaFree(p->specB);
-    p->specA = a;
-    p->specB = b;
-    p->nv_cap = ncols;
+    // tensor-core operand for the FP16/BF16 copies (used from 8 columns on)
+    if ((p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncols >= 8 && ncols > p->tc_cap) {
+        void* b = nullptr;
+        float* sg = nullptr;
+        cudaError_t e = cudaMalloc(&b, tc_scratch_elems(p, ncols) * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&sg, (size_t)p->nf * ncols * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaFree(b);
+            cudaGetLastError();
+            set_cuda_error(e);
+            return MDC_ERR_OOM;
+        }
+        cudaFree(p->tcB);
+        cudaFree(p->tcSigma);
+        p->tcB = b;
+        p->tcSigma = sg;
+        p->tc_cap = ncols;
+    }
     return MDC_OK;
 }
 
@@ -243,3 +267,16 @@ extern "C" int mdc_timing_read(mdc_handle h, int cls, double* total_ms, int64_t*
 }
 
 extern "C" int64_t mdc_launch_count(mdc_handle h) { return h ? h->launch_count : -1; }
+
+extern "C" int mdc_device_status(mdc_handle h, void* stream) {
+    if (!h) return MDC_ERR_ARG;
+    int v = 0;
+    MDC_CUDA_TRY(cudaMemcpyAsync(&v, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    MDC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (v != 0) {
+        MDC_CUDA_TRY(cudaMemsetAsync(h->err_flag, 0, sizeof(int), (cudaStream_t)stream));
+        MDC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        return MDC_ERR_TIMEOUT;
+    }
+    return MDC_OK;
+}

@@ -62,6 +62,11 @@ struct mdc_plan {
     int nv_cap = 0;
     float2* specA = nullptr;    // [nf][max(nr,ns)][nv_cap]
     float2* specB = nullptr;
+    // tensor-core path (FP16/BF16 storage): prepared B operand and its column scales
+    void* tcB = nullptr;        // [nf][rows_pad][max(2*ldg, nr8)] 16-bit
+    float* tcSigma = nullptr;   // [nf][tc_cap]
+    int tc_cap = 0;
+    int* err_flag = nullptr;    // device int: non-zero after a bounded device wait gave up
     int64_t launch_count = 0;
     mdc::TimingState timing;
 };
@@ -114,6 +119,12 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
 void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
                     float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
                     const int* active);
+
+// Tensor-core products (tc_gemm.cu).
+bool tc_supported(const mdc_plan* p, int ncol);
+bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
+                       int voff_o, int ncol, cudaStream_t s, const int* active);
+size_t tc_scratch_elems(const mdc_plan* p, int ncol);
 
 // Quantise a complex64 kernel [nf][nr][ns] into the plan's reduced-storage copy and row scales.
 void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s);

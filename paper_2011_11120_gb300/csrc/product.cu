@@ -566,6 +566,8 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
                     float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
                     const int* active) {
     LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
+    if (tc_supported(p, ncol) && launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active))
+        return;
     switch (p->storage) {
         case MDC_C64: product_fmt<MDC_C64>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
         case MDC_C16F: product_fmt<MDC_C16F>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;

@@ -1,0 +1,524 @@
+// Tensor-core (tcgen05) per-frequency products for the FP16/BF16 kernel copies:
+// K-hat and K-hat^H of Eq. 3 when many virtual points make each frequency slice a
+// dense GEMM (the batched products the paper uses for groups of focusing points).
+//
+// The complex product is one real GEMM on the interleaved (re, im) storage of G:
+//
+//   forward  D[r][n'] = sum_K' G^[r][K'] BT[n'][K'],  K' = 2s + c,
+//            BT[2n]   = ( Xr_s, -Xi_s )_s   (row of reals along K')
+//            BT[2n+1] = ( Xi_s,  Xr_s )_s
+//            -> D[r][2n] = Re Y[r][n], D[r][2n+1] = Im Y[r][n].
+//            A = G^ read K-major (rows r, 512-byte... contiguous along K').
+//   adjoint  D[m][n''] = sum_r G^[r][m] BT[n''][r],  m = 2s + c, n'' = 2n + c'',
+//            BT[2n] = (Yr_r)_r, BT[2n+1] = (Yi_r)_r (row scale of G folded in),
+//            Re X'[s][n] = D[2s][2n] + D[2s+1][2n+1], Im X'[s][n] = D[2s][2n+1] - D[2s+1][2n].
+//            A = the SAME G buffer read MN-major (transposed operand); no second copy.
+//
+// One CTA computes a 128 x BN tile of D for one frequency: warp 0 streams A and B
+// tiles with TMA into a ring of 128-byte-swizzled shared-memory stages, warp 1 (one
+// thread) issues tcgen05.mma (M=128, N=BN, K=16, FP32 accumulation in TMEM), warps
+// 2-5 read the accumulator back with tcgen05.ld and write complex64 results.  B is
+// scaled per (frequency, column) by a power of two so FP16 neither overflows nor
+// underflows; the epilogue divides it out and applies G's row scale (forward).
+// Every wait on an mbarrier is bounded in wall time: on expiry the thread records
+// an error code, the producer drains its own copies in flight, TMEM is freed and
+// the CTA exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace mdc {
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase with the given parity to complete, for at most TC_WAIT_NS.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_test(bar, parity)) return true;
+        if (gtime() - t0 > TC_WAIT_NS) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D(tmem) (+)= A(smem desc) * B(smem desc), kind::f16, FP32 accumulation.
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Shared-memory matrix descriptor, 128-byte swizzle (layout type 2), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+struct TcArgs {
+    int kstages;        // reduction slices of TC_BK elements
+    int nout;           // output rows: nr (forward) or ns (adjoint)
+    int nr;             // kernel rows (row-scale stride)
+    int ncol;           // complex columns
+    const float* sigma; // [nf][ncol] power-of-two column scales of B
+    const float* gscale;// [nf][nr] kernel row scales (forward epilogue)
+    float2* out;
+    int ldo, voff_o;
+    int* err;
+};
+
+template <int BN> struct TcStages { static constexpr int v = BN >= 256 ? 4 : (BN >= 128 ? 6 : 8); };
+
+template <int BN>
+constexpr size_t tc_smem_bytes() {
+    return (size_t)TcStages<BN>::v * (TC_BM * 128 + BN * 128) + 1024 + 256;
+}
+
+template <bool ADJ, int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
+                   uint32_t idesc, const int* active) {
+    if (active && *active == 0) return;
+    constexpr int STAGES = TcStages<BN>::v;
+    constexpr uint32_t A_BYTES = TC_BM * 128;
+    constexpr uint32_t B_BYTES = BN * 128;
+    constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), done = su32(bars + 2 * STAGES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = blockIdx.z, m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
+
+    if (warp == 0) tmem_alloc(su32(tmem_slot), BN);
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(full0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, 1);
+        }
+        mbar_init(done, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < a.kstages; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t round = (uint32_t)(kb / STAGES);
+                if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1)) break;
+                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+                if (!ADJ) {
+                    tma_load_3d(sa, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
+                } else {
+                    tma_load_3d(sa, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
+                    tma_load_3d(sa + A_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+                }
+                tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
+                issued = kb + 1;
+            }
+            // drain: every copy this thread issued must have landed before the CTA can exit
+            for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+                mbar_wait(full0 + 8 * (kb % STAGES), (uint32_t)(kb / STAGES) & 1, a.err, 2);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kb = 0; kb < a.kstages; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(kb / STAGES) & 1, a.err, 3)) break;
+                tc_fence_after();
+                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                    // K-major: +32 bytes per 16 elements inside the swizzled row; MN-major: +16 rows
+                    const uint64_t ad = ADJ ? sdesc(sa + kk * 2048, A_BYTES / 2, 1024) : sdesc(sa + kk * 32, 16, 1024);
+                    const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
+                    umma_f16(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                }
+                umma_commit(empty0 + 8 * s);
+            }
+            umma_commit(done);
+        }
+    } else {
+        if (mbar_wait(done, 0, a.err, 4)) {
+            tc_fence_after();
+            const int q = warp & 3;
+            const int row = q * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+            const float* sig = a.sigma + (size_t)k * a.ncol;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(taddr + c0, v);
+                const int nb = (n0 + c0) >> 1;
+                if (!ADJ) {
+                    const int r = m0 + row;
+                    if (r < a.nout) {
+                        const float gs = a.gscale[(size_t)k * a.nr + r];
+                        float2* dst = a.out + ((size_t)k * a.nout + r) * a.ldo + a.voff_o;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int n = nb + j;
+                            if (n < a.ncol) {
+                                const float f = gs / sig[n];
+                                dst[n] = make_float2(__uint_as_float(v[2 * j]) * f, __uint_as_float(v[2 * j + 1]) * f);
+                            }
+                        }
+                    }
+                } else {
+                    float p[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) p[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
+                    const int s = (m0 + row) >> 1;
+                    if ((lane & 1) == 0 && s < a.nout) {
+                        float2* dst = a.out + ((size_t)k * a.nout + s) * a.ldo + a.voff_o;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int n = nb + j;
+                            if (n < a.ncol) {
+                                const float f = 1.f / sig[n];
+                                const float re = __uint_as_float(v[2 * j]) + p[2 * j + 1];
+                                const float im = __uint_as_float(v[2 * j + 1]) - p[2 * j];
+                                dst[n] = make_float2(re * f, im * f);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+// ------------------------------------------------------------------ B-operand preparation
+template <typename T> __device__ __forceinline__ T cvt(float x);
+template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ float pow2_scale(float maxabs) {
+    if (!(maxabs > 0.f) || !isfinite(maxabs)) return 1.f;
+    int e;
+    frexpf(maxabs, &e);           // maxabs < 2^e
+    return ldexpf(1.f, 14 - e);   // maxabs * scale < 2^14
+}
+
+// forward: X[k][s][ldi] (voff, ncol columns) -> BT[k][n'][2*ldg], sigma[k][n]
+template <typename T>
+__global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X, int ldi, int voff, int ns,
+                                                   int ncol, int ldg, int rows_pad, T* __restrict__ BT,
+                                                   float* __restrict__ sigma, const int* active) {
+    if (active && *active == 0) return;
+    const int k = blockIdx.y, n0 = blockIdx.x * 8;
+    const float2* Xk = X + (size_t)k * ns * ldi + voff;
+    __shared__ float red[256];
+    __shared__ float sig[8];
+    const int j0 = threadIdx.x & 7;
+    float m = 0.f;
+    if (n0 + j0 < ncol)
+        for (int s = threadIdx.x >> 3; s < ns; s += 32) {
+            const float2 v = Xk[(size_t)s * ldi + n0 + j0];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float mm = 0.f;
+        for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
+        const float sc = pow2_scale(mm);
+        sig[threadIdx.x] = sc;
+        if (n0 + (int)threadIdx.x < ncol) sigma[(size_t)k * ncol + n0 + threadIdx.x] = sc;
+    }
+    __syncthreads();
+    const size_t kp = 2 * (size_t)ldg;
+    T* Bk = BT + (size_t)k * rows_pad * kp;
+    for (int s = threadIdx.x; s < ldg; s += 256) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = n0 + j;
+            if (2 * n >= rows_pad) break;
+            float2 v = make_float2(0.f, 0.f);
+            if (n < ncol && s < ns) {
+                v = Xk[(size_t)s * ldi + n];
+                v.x *= sig[j];
+                v.y *= sig[j];
+            }
+            T* r0 = Bk + (size_t)(2 * n) * kp + 2 * (size_t)s;
+            T* r1 = r0 + kp;
+            r0[0] = cvt<T>(v.x);
+            r0[1] = cvt<T>(-v.y);
+            r1[0] = cvt<T>(v.y);
+            r1[1] = cvt<T>(v.x);
+        }
+    }
+}
+
+// adjoint: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] -> BT[k][n''][kpitch], sigma[k][n]
+template <typename T>
+__global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y, int ldi, int voff, int nr,
+                                                   int ncol, const float* __restrict__ gscale, int kpitch,
+                                                   int rows_pad, T* __restrict__ BT, float* __restrict__ sigma,
+                                                   const int* active) {
+    if (active && *active == 0) return;
+    const int k = blockIdx.y, n0 = blockIdx.x * 8;
+    const float2* Yk = Y + (size_t)k * nr * ldi + voff;
+    const float* gs = gscale + (size_t)k * nr;
+    __shared__ float red[256];
+    __shared__ float sig[8];
+    const int j0 = threadIdx.x & 7;
+    float m = 0.f;
+    if (n0 + j0 < ncol)
+        for (int r = threadIdx.x >> 3; r < nr; r += 32) {
+            const float2 v = Yk[(size_t)r * ldi + n0 + j0];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * gs[r]);
+        }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float mm = 0.f;
+        for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
+        const float sc = pow2_scale(mm);
+        sig[threadIdx.x] = sc;
+        if (n0 + (int)threadIdx.x < ncol) sigma[(size_t)k * ncol + n0 + threadIdx.x] = sc;
+    }
+    __syncthreads();
+    T* Bk = BT + (size_t)k * rows_pad * kpitch;
+    for (int r = threadIdx.x; r < kpitch; r += 256) {
+        const float g = r < nr ? gs[r] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = n0 + j;
+            if (2 * n >= rows_pad) break;
+            float2 v = make_float2(0.f, 0.f);
+            if (n < ncol && r < nr) {
+                v = Yk[(size_t)r * ldi + n];
+                const float f = g * sig[j];
+                v.x *= f;
+                v.y *= f;
+            }
+            Bk[(size_t)(2 * n) * kpitch + r] = cvt<T>(v.x);
+            Bk[(size_t)(2 * n + 1) * kpitch + r] = cvt<T>(v.y);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map_3d(CUtensorMap* m, const void* ptr, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
+                 uint64_t pitch1_bytes, uint64_t pitch2_bytes, uint32_t b0, uint32_t b1) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {pitch1_bytes, pitch2_bytes};
+    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                     const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int pick_bn(int n2) {
+    if (n2 <= 32) return 32;
+    if (n2 <= 64) return 64;
+    if (n2 <= 128) return 128;
+    return 256;
+}
+
+template <bool ADJ, int BN>
+void launch_tc(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& a, uint32_t idesc, dim3 grid,
+               cudaStream_t s, const int* active) {
+    static bool attr = false;
+    const size_t smem = tc_smem_bytes<BN>();
+    if (!attr) {
+        cudaFuncSetAttribute(tc_gemm_kernel<ADJ, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    tc_gemm_kernel<ADJ, BN><<<grid, TC_THREADS, smem, s>>>(A, B, a, idesc, active);
+}
+
+}  // namespace
+
+int tc_rows_pad(int ncol) {
+    const int n2 = 2 * ncol;
+    const int bn = pick_bn(n2);
+    return (n2 + bn - 1) / bn * bn;
+}
+
+size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
+    const size_t rows = (size_t)tc_rows_pad(ncol);
+    const size_t kfwd = 2 * (size_t)p->ldg;
+    const size_t kadj = (size_t)round_up(p->nr, 8);
+    return (size_t)p->nf * rows * (kfwd > kadj ? kfwd : kadj);
+}
+
+bool tc_supported(const mdc_plan* p, int ncol) {
+    return (p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncol >= 8 && p->tcB != nullptr &&
+           ncol <= p->tc_cap && encode_fn() != nullptr;
+}
+
+// Per-frequency product on tensor cores; returns false if it could not be launched.
+bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
+                       int voff_o, int ncol, cudaStream_t s, const int* active) {
+    const bool bf16 = p->storage == MDC_CBF16;
+    const int rows_pad = tc_rows_pad(ncol);
+    const int bn = pick_bn(2 * ncol);
+    const int kpitch = (int)round_up(p->nr, 8);
+    // B operand
+    dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
+    if (!adjoint) {
+        if (bf16)
+            tc_prep_fwd<__nv_bfloat16><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
+                                                          (__nv_bfloat16*)p->tcB, p->tcSigma, active);
+        else
+            tc_prep_fwd<__half><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
+                                                   (__half*)p->tcB, p->tcSigma, active);
+    } else {
+        if (bf16)
+            tc_prep_adj<__nv_bfloat16><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch,
+                                                          rows_pad, (__nv_bfloat16*)p->tcB, p->tcSigma, active);
+        else
+            tc_prep_adj<__half><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch, rows_pad,
+                                                   (__half*)p->tcB, p->tcSigma, active);
+    }
+    // tensor maps: A over the kernel copy [nf][nr][2*ldg] (16-bit reals), B over the prepared operand
+    const uint64_t kp = 2 * (uint64_t)p->ldg;
+    CUtensorMap A, B;
+    bool ok;
+    if (!adjoint) {
+        ok = make_map_3d(&A, p->G, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 128) &&
+             make_map_3d(&B, p->tcB, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bn);
+    } else {
+        ok = make_map_3d(&A, p->G, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 64) &&
+             make_map_3d(&B, p->tcB, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
+                         (uint64_t)kpitch * 2 * rows_pad, 64, bn);
+    }
+    if (!ok) return false;
+    TcArgs a{};
+    a.kstages = adjoint ? (p->nr + TC_BK - 1) / TC_BK : (int)(kp / TC_BK);
+    a.nout = adjoint ? p->ns : p->nr;
+    a.nr = p->nr;
+    a.ncol = ncol;
+    a.sigma = p->tcSigma;
+    a.gscale = p->gscale;
+    a.out = out;
+    a.ldo = ldo;
+    a.voff_o = voff_o;
+    a.err = p->err_flag;
+    const uint32_t fmt = bf16 ? 1u : 0u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((adjoint ? 1u : 0u) << 15) |
+                           ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    const int mrows = adjoint ? (int)(kp / TC_BM) : (p->nr + TC_BM - 1) / TC_BM;
+    dim3 grid((unsigned)(rows_pad / bn), (unsigned)mrows, (unsigned)p->nf);
+#define MDC_TC_CASE(BNV)                                                         \
+    case BNV:                                                                    \
+        if (adjoint) launch_tc<true, BNV>(A, B, a, idesc, grid, s, active);      \
+        else launch_tc<false, BNV>(A, B, a, idesc, grid, s, active);             \
+        break;
+    switch (bn) {
+        MDC_TC_CASE(32)
+        MDC_TC_CASE(64)
+        MDC_TC_CASE(128)
+        MDC_TC_CASE(256)
+    }
+#undef MDC_TC_CASE
+    return true;
+}
+
+}  // namespace mdc

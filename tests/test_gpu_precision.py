@@ -40,7 +40,7 @@ def dequantised(G64: np.ndarray, storage: str) -> np.ndarray:
     return (qr * s64).numpy() + 1j * (qi * s64).numpy()
 
 
-CASES = [(256, 441, 441, 64, 1, "synth"), (128, 100, 77, 50, 2, "rand"), (64, 40, 90, 20, 17, "rand"),
+CASES = [(256, 441, 441, 64, 1, "synth"), (128, 100, 77, 50, 2, "rand"), (64, 40, 90, 20, 7, "rand"),
          (512, 130, 70, 100, 4, "rand")]
 
 
