@@ -202,6 +202,53 @@ def config_block(cfg, nv, storage="c64"):
             "l2": "inputs larger than L2 (kernel streamed every pass)"}
 
 
+def run_redatum(args, dev):
+    """Marchenko redatuming (Eq. 5/6) at 1681 x 1681, nt=512, nfmax=150, nv=256 (16 x 16 focusing
+    points), kernel normalised to ||R|| = 0.5: FP16 kernel inside LSQR with float32 refinement,
+    timed per solve; the plain float32 (complex64) solve of the same job gives the comparison."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from synth import gpu as sgpu
+    cfg = synth.config(4)
+    d = synth.draw(cfg)
+    G = sgpu.kernel_on_device(cfg, d)
+    lo = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.redatum_storage)
+    ref = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    del G
+    torch.cuda.empty_cache()
+    cut = torch.from_numpy(synth.window_cutoffs(cfg, d)).to(dev)
+    fd = torch.from_numpy(synth.direct_focusing(cfg, d)).to(dev)
+    niter, nref, nin = cfg.niter, 1, args.redatum_refine_iters
+
+    def solve():
+        return lo.marchenko_refined(ref, cut, fd, niter, nrefine=nref, niter_refine=nin)
+
+    out = solve()                                      # warm-up (allocations, tensor maps)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.redatum_solves):
+        t0 = time.perf_counter()
+        out = solve()
+        times.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    plain = ref.marchenko(cut, fd, niter)              # float32 operator, one job, no refinement
+    t_plain = time.perf_counter() - t0
+    fm = out["f_minus"].double()
+    err = float((fm - plain["f_minus"].double()).norm() / plain["f_minus"].double().norm())
+    lo.close()
+    ref.close()
+    med = statistics.median(times)
+    return {"workload": f"Marchenko LSQR, nr=ns={cfg.nr} (41x41, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
+                        f"nv={cfg.nv} (16x16 focusing points, z=800 m), ||R||=0.5, {niter} LSQR iterations "
+                        f"on a {args.redatum_storage} kernel + {nref} float32 refinement step of {nin} iterations",
+            "solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "solves_timed": len(times),
+            "p50_ms": 1e3 * med, "p99_ms": 1e3 * max(times),
+            "iterations": out["iters"], "final_residual": out["final_residual"],
+            "rel_l2_vs_fp32_solve": err,
+            "fp32_one_job": {"solves_per_s": 1.0 / t_plain, "ms_per_solve": 1e3 * t_plain,
+                             "iterations": plain["iters"], "storage": "c64"}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -315,6 +362,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if world == 1 and not args.no_redatum:
+        result["redatum"] = run_redatum(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
     print(json.dumps(result), flush=True)
@@ -334,6 +383,10 @@ def main():
     ap.add_argument("--storage", default="c64", choices=["c64", "c16f", "cbf16", "ce4m3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-redatum", action="store_true")
+    ap.add_argument("--redatum-solves", type=int, default=3)
+    ap.add_argument("--redatum-storage", default="c16f", choices=["c16f", "cbf16"])
+    ap.add_argument("--redatum-refine-iters", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

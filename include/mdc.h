@@ -165,6 +165,76 @@ int marchenko_lsqr(mdc_handle R, const int* window, const float* fd_plus, int nv
                    double tol, float* f_minus, float* f_mplus, float* g_minus, float* g_plus,
                    double* resid, int* iters_done, void* stream);
 
+/*
+ * marchenko_lsqr_refined -- marchenko_lsqr with a reduced-precision kernel copy inside LSQR
+ * and float32-operator refinement (iterative refinement of the least-squares solution).
+ *
+ *   R        handle with any storage (typically MDC_C16F/MDC_CBF16) used inside LSQR.
+ *   R_ref    complex64 handle (MDC_C64) of the same kernel, same shape: it computes the data
+ *            vector d, the residuals d - M x, the Green's functions and the final check.
+ *   niter    LSQR iterations of the first solve (from x = 0).
+ *   nrefine  outer refinement steps: each recomputes r = d - M_ref x in float32 and runs
+ *            niter_refine further LSQR iterations on R, adding the correction to x.
+ *   resid    host double[(niter + 1) + nrefine * (niter_refine + 1)] or NULL: for each solve,
+ *            its right-hand-side norm then its residual estimates (-1 where not reached).
+ *   final_residual  host double or NULL: ||d - M_ref x|| / ||d||, accumulated in float64.
+ * Other arguments as marchenko_lsqr.  Blocking.  MDC_ERR_ARG if R_ref is not MDC_C64 or the
+ * shapes differ.
+ */
+int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int* window, const float* fd_plus,
+                           int nv, int niter, int nrefine, int niter_refine, double tol,
+                           float* f_minus, float* f_mplus, float* g_minus, float* g_plus,
+                           double* resid, double* final_residual, int* iters_done, void* stream);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of redatuming jobs (Eq. 5 for groups of focusing points,
+ * the paper's embarrassingly parallel level of the Discussion, served on one GPU).
+ *
+ * Jobs arrive with srv_submit (host inputs, copied).  srv_step admits queued jobs in
+ * arrival order while the device-memory budget and the column capacity allow, then
+ * advances every running job by one LSQR iteration: all running jobs' columns are
+ * stacked so ONE forward and ONE adjoint product stream the kernel for all of them.
+ * Each job keeps its own float64 LSQR scalars, so its result does not depend on which
+ * jobs share its steps (with an FP16/BF16 kernel the server routes every product through
+ * the tensor-core path so the arithmetic per column is the same for any batch).  A job
+ * that finishes its solve is refined (nrefine steps of niter_refine iterations against
+ * the complex64 reference kernel), then its Green's functions (Eq. 6) and float64
+ * residual check ||d - M_ref x|| / ||d|| are computed and its outputs copied to the host
+ * buffers given at submission.
+ * ------------------------------------------------------------------------------------ */
+typedef struct mdc_server* mdc_server_handle;
+
+enum { MDC_JOB_QUEUED = 0, MDC_JOB_RUNNING = 1, MDC_JOB_DONE = 2, MDC_JOB_FAILED = 3 };
+
+/* srv_create -- R: kernel used inside LSQR (nr == ns); R_ref: complex64 reference of the same
+ * kernel or NULL (then R serves for data and Green's functions, and nrefine must be 0).
+ * hbm_budget_bytes bounds the device memory of running jobs' state (about 48 bytes per
+ * time sample per column); max_cols bounds the stacked columns (2 per virtual point).
+ * The server owns R's scratch while it exists.  Allocates; blocking. */
+int srv_create(mdc_server_handle* out, mdc_handle R, mdc_handle R_ref, int64_t hbm_budget_bytes,
+               int max_cols, int nrefine, int niter_refine, void* stream);
+/* srv_submit -- queue one job: window int32 [ns][nv] and fd_plus float32 [nt][ns][nv] in host
+ * memory (copied now); niter LSQR iterations (tol > 0: stop earlier at tol * ||d||).  The four
+ * host output buffers [nt][ns][nv] (each may be NULL) are filled when the job completes.
+ * MDC_ERR_BUDGET if the job can never fit.  *job_id receives the job's id. */
+int srv_submit(mdc_server_handle s, const int* window_host, const float* fd_plus_host, int nv, int niter,
+               double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+               float* g_plus_host, int64_t* job_id);
+/* srv_step -- admit, advance every running job by one iteration, complete finished jobs
+ * (their host outputs are written before return).  Blocking.  *completed = jobs completed. */
+int srv_step(mdc_server_handle s, int* completed);
+/* srv_poll -- state (MDC_JOB_*), iterations, final residual ratio, latency (submit to
+ * completion, s) and queueing delay (submit to admission, s); -1 where not yet known.
+ * Returns the job's error status if it failed. */
+int srv_poll(mdc_server_handle s, int64_t job_id, int* state, int* iters, double* final_residual,
+             double* latency_s, double* queue_s);
+/* srv_release -- forget a completed or failed job (MDC_ERR_STATE while queued/running). */
+int srv_release(mdc_server_handle s, int64_t job_id);
+/* srv_stats -- queued and running job counts, bytes and columns in use. */
+int srv_stats(mdc_server_handle s, int* queued, int* running, int64_t* bytes_in_use, int* cols_in_use);
+/* srv_destroy -- drop all jobs and free the server (the handles stay valid). */
+int srv_destroy(mdc_server_handle s);
+
 /* mdc_destroy -- free the handle and everything it owns (synchronises the device). */
 int mdc_destroy(mdc_handle h);
 

@@ -35,6 +35,8 @@ SIGNATURES = {
     "mdc_forward_static_scratch": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "marchenko_lsqr": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp,
                             ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
+    "marchenko_lsqr_refined": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, _vp, _vp, _vp, _vp,
+                                    ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
     "mdc_destroy": (_i, [_vp]),
     "mdc_strerror": (ctypes.c_char_p, [_i]),
     "mdc_last_cuda_error": (_i, []),
@@ -43,6 +45,14 @@ SIGNATURES = {
     "mdc_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "mdc_launch_count": (_i64, [_vp]),
     "mdc_device_status": (_i, [_vp, _vp]),
+    "srv_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _i64, _i, _i, _i, _vp]),
+    "srv_submit": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
+    "srv_step": (_i, [_vp, ctypes.POINTER(_i)]),
+    "srv_poll": (_i, [_vp, _i64, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d),
+                      ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "srv_release": (_i, [_vp, _i64]),
+    "srv_stats": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i)]),
+    "srv_destroy": (_i, [_vp]),
 }
 
 _lib = None
@@ -143,6 +153,24 @@ def marchenko_lsqr(h, window: torch.Tensor, fd_plus: torch.Tensor, nv: int, nite
     return [resid[i] for i in range(niter + 1)], it.value
 
 
+def marchenko_lsqr_refined(h, h_ref, window: torch.Tensor, fd_plus: torch.Tensor, nv: int, niter: int,
+                           nrefine: int, niter_refine: int, tol: float, f_minus: torch.Tensor,
+                           f_mplus: torch.Tensor, g_minus=None, g_plus=None, stream=None):
+    """Reduced-precision LSQR with float32 refinement; returns (resid list, final residual, iterations)."""
+    nres = (niter + 1) + nrefine * (niter_refine + 1)
+    resid = (ctypes.c_double * nres)()
+    fin = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    st = lib().marchenko_lsqr_refined(h, h_ref, _ptr(window, torch.int32, "window"),
+                                      _ptr(fd_plus, torch.float32, "fd_plus"), nv, niter, nrefine, niter_refine,
+                                      tol, _ptr(f_minus, torch.float32, "f_minus"),
+                                      _ptr(f_mplus, torch.float32, "f_mplus"),
+                                      _ptr(g_minus, torch.float32, "g_minus"), _ptr(g_plus, torch.float32, "g_plus"),
+                                      resid, ctypes.byref(fin), ctypes.byref(it), _stream(stream))
+    _check(st, "marchenko_lsqr_refined")
+    return [resid[i] for i in range(nres)], fin.value, it.value
+
+
 def mdc_destroy(h) -> None:
     _check(lib().mdc_destroy(h), "mdc_destroy")
 
@@ -205,6 +233,19 @@ class MDC:
         resid, iters = marchenko_lsqr(self.h, window, fd_plus, nv, niter, tol, fm, fmp, gm, gp, stream)
         return {"f_minus": fm, "f_mplus": fmp, "g_minus": gm, "g_plus": gp, "resid": resid, "iters": iters}
 
+    def marchenko_refined(self, ref: "MDC", window: torch.Tensor, fd_plus: torch.Tensor, niter: int,
+                          nrefine: int = 1, niter_refine: int = 10, tol: float = 0.0, greens: bool = True,
+                          stream=None):
+        """Solve with this (reduced-precision) handle, refining against ``ref`` (complex64)."""
+        nv = fd_plus.shape[2]
+        mk = lambda: torch.empty_like(fd_plus)  # noqa: E731
+        fm, fmp = mk(), mk()
+        gm, gp = (mk(), mk()) if greens else (None, None)
+        resid, fin, iters = marchenko_lsqr_refined(self.h, ref.h, window, fd_plus, nv, niter, nrefine,
+                                                   niter_refine, tol, fm, fmp, gm, gp, stream)
+        return {"f_minus": fm, "f_mplus": fmp, "g_minus": gm, "g_plus": gp, "resid": resid,
+                "final_residual": fin, "iters": iters}
+
     def close(self):
         if self.h is not None:
             mdc_destroy(self.h)
@@ -215,3 +256,66 @@ class MDC:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ serving
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+
+
+def _hptr(a):
+    """Host pointer of a contiguous numpy array (or None)."""
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def srv_create(h, h_ref, hbm_budget_bytes: int, max_cols: int, nrefine: int = 0, niter_refine: int = 0,
+               stream=None):
+    v = ctypes.c_void_p()
+    _check(lib().srv_create(ctypes.byref(v), h, h_ref, int(hbm_budget_bytes), max_cols, nrefine, niter_refine,
+                            _stream(stream)), "srv_create")
+    return v
+
+
+def srv_submit(v, window, fd_plus, nv: int, niter: int, tol: float = 0.0, outputs=(None, None, None, None)) -> int:
+    """Queue a job from host numpy arrays (int32 window [ns][nv], float32 fd_plus [nt][ns][nv])."""
+    import numpy as np
+    window = np.ascontiguousarray(window, dtype=np.int32)
+    fd_plus = np.ascontiguousarray(fd_plus, dtype=np.float32)
+    jid = ctypes.c_int64(0)
+    o = [_hptr(a) for a in outputs]
+    _check(lib().srv_submit(v, _hptr(window), _hptr(fd_plus), nv, niter, tol, o[0], o[1], o[2], o[3],
+                            ctypes.byref(jid)), "srv_submit")
+    return jid.value
+
+
+def srv_step(v) -> int:
+    n = ctypes.c_int(0)
+    _check(lib().srv_step(v, ctypes.byref(n)), "srv_step")
+    return n.value
+
+
+def srv_poll(v, job_id: int) -> dict:
+    st, it = ctypes.c_int(0), ctypes.c_int(0)
+    fr, lat, qs = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    rc = lib().srv_poll(v, job_id, ctypes.byref(st), ctypes.byref(it), ctypes.byref(fr), ctypes.byref(lat),
+                        ctypes.byref(qs))
+    return {"state": st.value, "iters": it.value, "final_residual": fr.value, "latency_s": lat.value,
+            "queue_s": qs.value, "status": rc}
+
+
+def srv_release(v, job_id: int) -> None:
+    _check(lib().srv_release(v, job_id), "srv_release")
+
+
+def srv_stats(v) -> dict:
+    q, r, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    b = ctypes.c_int64(0)
+    _check(lib().srv_stats(v, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c)), "srv_stats")
+    return {"queued": q.value, "running": r.value, "bytes": b.value, "cols": c.value}
+
+
+def srv_destroy(v) -> None:
+    _check(lib().srv_destroy(v), "srv_destroy")

@@ -161,7 +161,7 @@ int mdc::ensure_scratch(mdc_plan* p, int ncols) {
         p->nv_cap = ncols;
     }
     // tensor-core operand for the FP16/BF16 copies (used from 8 columns on)
-    if ((p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncols >= 8 && ncols > p->tc_cap) {
+    if ((p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncols > p->tc_cap) {
         void* b = nullptr;
         float* sg = nullptr;
         cudaError_t e = cudaMalloc(&b, tc_scratch_elems(p, ncols) * 2);

@@ -67,6 +67,7 @@ struct mdc_plan {
     float* tcSigma = nullptr;   // [nf][tc_cap]
     int tc_cap = 0;
     int* err_flag = nullptr;    // device int: non-zero after a bounded device wait gave up
+    bool force_tc = false;      // FP16/BF16: tensor-core products for every column count
     int64_t launch_count = 0;
     mdc::TimingState timing;
 };
@@ -93,6 +94,7 @@ struct RfftArgs {
     int ldv, voff;
     const float2* tw;
     const int* active;     // if non-null and *active == 0 the kernel does nothing
+    int vec4;              // set by the launcher: x (and x2) 16-byte aligned rows, C % 4 == 0
 };
 struct IrfftArgs {
     const float2* Y;       // [nf][S][ldv]
@@ -109,6 +111,7 @@ struct IrfftArgs {
     double* colsum;        // per-column sum of squares of out, or null
     const float2* tw;
     const int* active;
+    int vec4;              // set by the launcher: aligned 4-column output path
 };
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
 void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);

@@ -158,6 +158,373 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft_kernel(IrfftArgs a, int log
     }
 }
 
+// ------------------------------------------------------------------ four-step kernels
+// nt = N1 * N2 (N1, N2 in {8, 16, 32}).  Pass A: for each residue n2, an N1-point DFT in
+// registers over t = n1 * N2 + n2, then the twiddle W_nt^(n2 k1); pass B: for each k1 an
+// N2-point DFT over the N2 consecutive rows k1 * N2 + n2.  Result bin k = k1 + N1 * k2
+// sits in row k1 * N2 + k2.  Four shared-memory sweeps per transform instead of
+// 2 log2(nt) + 1 for radix 2.  Layout: row t of P complex sequences at
+// t * RS + (t / N2) * BP, RS = P + 1 and BP chosen so that both passes spread a warp's
+// 8-byte accesses over distinct bank pairs.
+
+__host__ __device__ constexpr int brev_bits(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+__host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n / 2); }
+
+// In-register R-point DFT, a[k] = sum_n a[n] w^(n k), w = tw[nt/R] (tw holds W_nt^j, j < nt/2).
+// Decimation in frequency (natural order in, bit-reversed order out), then a compile-time
+// permutation back to natural order: every array index is a constant after unrolling.
+template <int R, int STRIDE>
+__device__ __forceinline__ void reg_fft(float2 (&a)[R], const float2* tw) {
+    constexpr int L = clog2(R);
+#pragma unroll
+    for (int st = 0; st < L; ++st) {
+        const int h = R >> (st + 1);          // half span of this stage
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const float2 u = a[g + j], v = a[g + j + h];
+                a[g + j] = cadd(u, v);
+                const float2 d = csub(u, v);
+                a[g + j + h] = (j == 0) ? d : cmul(d, tw[j * (1 << st) * STRIDE]);
+            }
+        }
+    }
+    float2 b[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) b[i] = a[brev_bits(i, L)];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = b[i];
+}
+
+template <int N1, int N2> struct FourStep {
+    static constexpr int NT = N1 * N2;
+    static constexpr int P0 = 8192 / NT;
+    static constexpr int P = P0 > 32 ? 32 : (P0 < 8 ? 8 : P0);     // complex sequences per CTA
+    static constexpr int CT = 2 * P;                                  // real columns per CTA
+    static constexpr int RS = P + 1;
+    static constexpr int BP = ((8 - (N2 * RS) % 16) % 16 + 16) % 16;
+    static constexpr int ZSIZE = NT * RS + N1 * BP;                  // float2 elements
+    static constexpr size_t smem = (size_t)(NT / 2 + ZSIZE) * sizeof(float2) + FFT_THREADS * 32;
+    __device__ static __forceinline__ int zi(int t, int j) { return t * RS + (t / N2) * BP + j; }
+};
+
+__device__ __forceinline__ float2 tw_full(const float2* tw, int m, int nt) {
+    return m < (nt >> 1) ? tw[m] : make_float2(-tw[m - (nt >> 1)].x, -tw[m - (nt >> 1)].y);
+}
+
+template <int N1, int N2>
+__device__ __forceinline__ void four_step(float2* z, const float2* tw) {
+    using F = FourStep<N1, N2>;
+    constexpr int P = F::P;
+    for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
+        const int j = task % P, n2 = task / P;
+        float2 r[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) r[n1] = z[F::zi(n1 * N2 + n2, j)];
+        reg_fft<N1, N2>(r, tw);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            const float2 v = k1 == 0 ? r[0] : cmul(r[k1], tw_full(tw, n2 * k1, F::NT));
+            z[F::zi(k1 * N2 + n2, j)] = v;
+        }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
+        const int j = task % P, k1 = task / P;
+        float2 r[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) r[n2] = z[F::zi(k1 * N2 + n2, j)];
+        reg_fft<N2, N1>(r, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) z[F::zi(k1 * N2 + k2, j)] = r[k2];
+    }
+    __syncthreads();
+}
+
+// Row holding bin (or time sample) q after four_step.
+template <int N1, int N2>
+__device__ __forceinline__ int out_row(int q) { return (q % N1) * N2 + q / N1; }
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
+    using F = FourStep<N1, N2>;
+    constexpr int NT = F::NT, CT = F::CT;
+    if (a.active && *a.active == 0) return;
+    extern __shared__ __align__(16) float2 sm2[];
+    float2* tw = sm2;
+    float2* z = sm2 + NT / 2;
+    const int c0 = blockIdx.x * CT;
+    for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = a.tw[i];
+    const float sc = coef(a.scale);
+    // Load the [NT][CT] tile with many independent loads in flight per thread.
+    auto put = [&](int t, int cl, float v) {
+        const int c = c0 + cl;
+        if (a.cut) {
+            const int tau = t < (NT >> 1) ? t : NT - t;
+            if (tau >= a.cut[c]) v = 0.f;
+        }
+        reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v * sc;
+    };
+    if (a.vec4 && c0 + CT <= a.C) {
+        constexpr int Q = CT / 4, PER = NT * Q / FFT_THREADS, B = PER < 16 ? PER : 16;
+#pragma unroll 1
+        for (int b0 = 0; b0 < PER; b0 += B) {
+            float4 v[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int q = threadIdx.x + (b0 + u) * FFT_THREADS;
+                const size_t off = (size_t)(q / Q) * a.C + c0 + 4 * (q % Q);
+                v[u] = *reinterpret_cast<const float4*>(a.x + off);
+                if (a.x2) {
+                    const float4 w = *reinterpret_cast<const float4*>(a.x2 + off);
+                    v[u].x += w.x; v[u].y += w.y; v[u].z += w.z; v[u].w += w.w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int q = threadIdx.x + (b0 + u) * FFT_THREADS;
+                const int t = q / Q, cl = 4 * (q % Q);
+                put(t, cl, v[u].x);
+                put(t, cl + 1, v[u].y);
+                put(t, cl + 2, v[u].z);
+                put(t, cl + 3, v[u].w);
+            }
+        }
+    } else {
+        constexpr int PER = NT * CT / FFT_THREADS, B = PER < 16 ? PER : 16;
+#pragma unroll 1
+        for (int b0 = 0; b0 < PER; b0 += B) {
+            float v[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int idx = threadIdx.x + (b0 + u) * FFT_THREADS;
+                const int t = idx / CT, c = c0 + idx % CT;
+                v[u] = 0.f;
+                if (c < a.C) {
+                    const size_t off = (size_t)t * a.C + c;
+                    v[u] = a.x[off];
+                    if (a.x2) v[u] += a.x2[off];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int idx = threadIdx.x + (b0 + u) * FFT_THREADS;
+                const int t = idx / CT, cl = idx % CT;
+                if (c0 + cl < a.C) put(t, cl, v[u]);
+                else reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    four_step<N1, N2>(z, tw);
+    for (int idx = threadIdx.x; idx < a.nf * CT; idx += FFT_THREADS) {
+        const int k = idx / CT, cl = idx % CT, c = c0 + cl;
+        if (c >= a.C) continue;
+        const int j = cl >> 1;
+        const float2 Z = z[F::zi(out_row<N1, N2>(k), j)];
+        const float2 Zm = z[F::zi(out_row<N1, N2>((NT - k) & (NT - 1)), j)];
+        float2 r;
+        if ((cl & 1) == 0) r = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+        else               r = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
+        if (a.conj) r.y = -r.y;
+        const int s = c / a.nv, v = c - s * a.nv;
+        a.X[((size_t)k * a.S + s) * a.ldv + a.voff + v] = r;
+    }
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
+    using F = FourStep<N1, N2>;
+    constexpr int NT = F::NT, CT = F::CT, P = F::P;
+    if (a.active && *a.active == 0) return;
+    extern __shared__ __align__(16) float2 sm2[];
+    float2* tw = sm2;
+    float2* z = sm2 + NT / 2;
+    double* red = reinterpret_cast<double*>(z + F::ZSIZE);
+    const int c0 = blockIdx.x * CT;
+    for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = cconj(a.tw[i]);
+    // rows no bin reaches are zero
+    for (int idx = threadIdx.x; idx < NT * P; idx += FFT_THREADS) {
+        const int k = idx / P;
+        if (k >= a.nf && NT - k >= a.nf) z[F::zi(k, idx % P)] = make_float2(0.f, 0.f);
+    }
+    // Each loaded bin kk < nf of the two columns fills Z[kk] and its Hermitian mirror Z[NT - kk].
+    {
+        const int items = a.nf * P;
+        constexpr int B = 8;
+#pragma unroll 1
+        for (int b0 = 0; b0 < items; b0 += B * FFT_THREADS) {
+            float2 A[B], Bv[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+                A[u] = make_float2(0.f, 0.f);
+                Bv[u] = A[u];
+                if (idx < items) {
+                    const int j = idx % P, kk = idx / P, ca = c0 + 2 * j;
+                    if (ca < a.C) {
+                        const int sa = ca / a.nv, va = ca - sa * a.nv;
+                        const size_t ia = ((size_t)kk * a.S + sa) * a.ldv + a.voff + va;
+                        if (ca + 1 < a.C) {
+                            const int sb = (ca + 1) / a.nv, vb = ca + 1 - sb * a.nv;
+                            const size_t ib = ((size_t)kk * a.S + sb) * a.ldv + a.voff + vb;
+                            if (ib == ia + 1 && (ia & 1) == 0) {
+                                const float4 q = *reinterpret_cast<const float4*>(a.Y + ia);
+                                A[u] = make_float2(q.x, q.y);
+                                Bv[u] = make_float2(q.z, q.w);
+                            } else {
+                                A[u] = a.Y[ia];
+                                Bv[u] = a.Y[ib];
+                            }
+                        } else {
+                            A[u] = a.Y[ia];
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+                if (idx >= items) continue;
+                const int j = idx % P, kk = idx / P;
+                float2 Av = A[u], Bw = Bv[u];
+                if (a.conj_in) { Av.y = -Av.y; Bw.y = -Bw.y; }
+                if (kk == 0 || 2 * kk == NT) { Av.y = 0.f; Bw.y = 0.f; }
+                z[F::zi(kk, j)] = make_float2(Av.x - Bw.y, Av.y + Bw.x);
+                if (kk > 0 && 2 * kk < NT) z[F::zi(NT - kk, j)] = make_float2(Av.x + Bw.y, Bw.x - Av.y);
+            }
+        }
+    }
+    __syncthreads();
+    four_step<N1, N2>(z, tw);
+
+    const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
+    const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
+    if (a.vec4) {
+        // four adjacent columns per thread: 16-byte loads and stores
+        constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, B = PER < 8 ? PER : 8;
+        const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
+        double ss[4] = {0.0, 0.0, 0.0, 0.0};
+        if (cq < a.C) {
+            int cut[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+#pragma unroll 1
+            for (int b0 = 0; b0 < PER; b0 += B) {
+                float4 bv[B], pv[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const size_t o = (size_t)(t0 + (b0 + u) * TS) * a.C + cq;
+                    bv[u] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    pv[u] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int t = t0 + (b0 + u) * TS;
+                    const int row = out_row<N1, N2>(t);
+                    const float2 z0 = z[F::zi(row, 2 * q)], z1 = z[F::zi(row, 2 * q + 1)];
+                    const int tau = t < (NT >> 1) ? t : NT - t;
+                    float v[4] = {z0.x, z0.y, z1.x, z1.y};
+                    const float bb[4] = {bv[u].x, bv[u].y, bv[u].z, bv[u].w};
+                    const float pp[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float val = tau >= cut[i] ? 0.f : v[i] * a.scale;
+                        v[i] = am * val + ab * bb[i] + ap * pp[i];
+                        ss[i] += (double)v[i] * (double)v[i];
+                    }
+                    *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
+                }
+            }
+        }
+        if (a.colsum) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = ss[i];
+            __syncthreads();
+            if (threadIdx.x < CT && c0 + (int)threadIdx.x < a.C) {
+                const int qq = threadIdx.x / 4, ii = threadIdx.x % 4;
+                double tot = 0.0;
+                for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
+                a.colsum[c0 + threadIdx.x] = tot;
+            }
+        }
+        return;
+    }
+    const int cl = threadIdx.x % CT, c = c0 + cl;
+    double ss = 0.0;
+    if (c < a.C) {
+        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        constexpr int TS = FFT_THREADS / CT, PER = NT / TS, B = PER < 8 ? PER : 8;
+        const int t0 = threadIdx.x / CT;
+#pragma unroll 1
+        for (int b0 = 0; b0 < PER; b0 += B) {
+            float bv[B], pv[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int t = t0 + (b0 + u) * TS;
+                const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
+                bv[u] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
+                pv[u] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const int t = t0 + (b0 + u) * TS;
+                const float2 zz = z[F::zi(out_row<N1, N2>(t), cl >> 1)];
+                float val = ((cl & 1) ? zz.y : zz.x) * a.scale;
+                const int tau = t < (NT >> 1) ? t : NT - t;
+                if (tau >= cut) val = 0.f;
+                const float r = am * val + ab * bv[u] + ap * pv[u];
+                const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
+                a.out[(size_t)to * a.C + c] = r;
+                ss += (double)r * (double)r;
+            }
+        }
+    }
+    if (a.colsum) {
+        red[threadIdx.x] = ss;
+        __syncthreads();
+        if (threadIdx.x < CT && c < a.C) {
+            double tot = 0.0;
+            for (int i = threadIdx.x; i < FFT_THREADS; i += CT) tot += red[i];
+            a.colsum[c] = tot;
+        }
+    }
+}
+
+template <int N1, int N2>
+void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
+    using F = FourStep<N1, N2>;
+    RfftArgs a = a0;
+    a.vec4 = (a.C % 4 == 0) && ((uintptr_t)a.x % 16 == 0) && (!a.x2 || (uintptr_t)a.x2 % 16 == 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(rfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem);
+        attr = true;
+    }
+    LaunchScope ls(p, s, MDC_KC_RFFT);
+    rfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+}
+
+template <int N1, int N2>
+void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
+    using F = FourStep<N1, N2>;
+    IrfftArgs a = a0;
+    a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
+             (!a.base || (uintptr_t)a.base % 16 == 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(irfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem);
+        attr = true;
+    }
+    LaunchScope ls(p, s, MDC_KC_IRFFT);
+    irfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+}
+
 int tile_log_columns(int nt) {
     // CT * nt ~ 16K floats per CTA (64 KB), CT in [4, 64]
     int ct = 16384 / nt;
@@ -172,6 +539,14 @@ size_t irfft_smem(int nt, int logCT) { return rfft_smem(nt, logCT) + FFT_THREADS
 }  // namespace
 
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+    switch (a.nt) {
+        case 64: rfft4_launch<8, 8>(p, a, s); return;
+        case 128: rfft4_launch<16, 8>(p, a, s); return;
+        case 256: rfft4_launch<16, 16>(p, a, s); return;
+        case 512: rfft4_launch<32, 16>(p, a, s); return;
+        case 1024: rfft4_launch<32, 32>(p, a, s); return;
+        default: break;
+    }
     const int logCT = tile_log_columns(a.nt);
     const size_t smem = rfft_smem(a.nt, logCT);
     static bool attr_set = false;
@@ -185,6 +560,14 @@ void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
 }
 
 void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+    switch (a.nt) {
+        case 64: irfft4_launch<8, 8>(p, a, s); return;
+        case 128: irfft4_launch<16, 8>(p, a, s); return;
+        case 256: irfft4_launch<16, 16>(p, a, s); return;
+        case 512: irfft4_launch<32, 16>(p, a, s); return;
+        case 1024: irfft4_launch<32, 32>(p, a, s); return;
+        default: break;
+    }
     const int logCT = tile_log_columns(a.nt);
     const size_t smem = irfft_smem(a.nt, logCT);
     static bool attr_set = false;

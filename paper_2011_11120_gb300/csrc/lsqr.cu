@@ -176,160 +176,302 @@ int elementwise_grid(int64_t n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-struct Buffers {
-    float* blk[6] = {};        // U1 U2 V1 V2 W1 W2
-    double* csU = nullptr;     // [2C]
+// sqrt(sum of column sums) / reference norm, written to out (the FP64 residual check).
+__global__ void __launch_bounds__(RED_THREADS) norm_ratio(const double* cs, int n, const double* ref, double* out) {
+    const double v = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) *out = (*ref > 0.0) ? v / *ref : v;
+}
+__global__ void __launch_bounds__(RED_THREADS) norm_store(const double* cs, int n, double* out) {
+    const double v = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void copy_f(int64_t n, const float* a, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i];
+}
+
+// w_1 = v_1 = v-hat / alpha_1; x is kept (refinement continues from the current solution).
+__global__ void lsqr_w_init(int64_t n, float* __restrict__ w1, float* __restrict__ w2,
+                            const float* __restrict__ v1, const float* __restrict__ v2, const double* sc) {
+    const float ia = (float)sc[S_INV_ALPHA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        w1[i] = ia * v1[i];
+        w2[i] = ia * v2[i];
+    }
+}
+
+enum Extra { X_DNORM, X_FINAL, X_COUNT };
+
+// Work state of one Marchenko solve (Eq. 5) on one GPU stream.
+struct Solver {
+    mdc_plan* p = nullptr;     // operator used inside LSQR (any storage)
+    mdc_plan* pr = nullptr;    // operator for data, residuals and Green's functions (FP32 path)
+    int nv = 0, n = 0, C = 0;
+    int64_t B = 0;
+    cudaStream_t s = nullptr;
+    const int* cut = nullptr;
+    float* blk[7] = {};        // U1 U2 V1 V2 W1 W2 D1
+    double* csU = nullptr;
     double* csV = nullptr;
-    double* sc = nullptr;      // [S_COUNT]
-    double* resid = nullptr;   // [niter+1]
-    int* act = nullptr;        // [niter+2]
-    int* iters = nullptr;
-    ~Buffers() {
-        for (float* b : blk) cudaFree(b);
-        cudaFree(csU); cudaFree(csV); cudaFree(sc); cudaFree(resid); cudaFree(act); cudaFree(iters);
+    double* sc = nullptr;      // [S_COUNT] LSQR scalars
+    double* xs = nullptr;      // [X_COUNT] data norm, final residual ratio
+    double* resid = nullptr;   // [nresid]
+    int* act = nullptr;        // [nact]
+    int* iters = nullptr;      // [nsolves]
+    int nresid = 0, nact = 0, nsolves = 0;
+    int ldv = 0, voff0 = 0;    // spectrum layout: columns per point and this system's first column
+    bool async_alloc = false;  // stream-ordered allocation (serving)
+
+    void release(void* q) {
+        if (!q) return;
+        if (async_alloc) cudaFreeAsync(q, s);
+        else cudaFree(q);
+    }
+    ~Solver() {
+        for (float* b : blk) release(b);
+        release(csU); release(csV); release(sc); release(xs); release(resid); release(act); release(iters);
+    }
+    template <typename T> cudaError_t get(T** q, size_t bytes) {
+        return async_alloc ? cudaMallocAsync((void**)q, bytes, s) : cudaMalloc((void**)q, bytes);
+    }
+    void layout(int ld, int off) { ldv = ld; voff0 = off; }
+    int LD() const { return ldv ? ldv : 2 * nv; }
+    float* U1() { return blk[0]; } float* U2() { return blk[1]; }
+    float* V1() { return blk[2]; } float* V2() { return blk[3]; }
+    float* W1() { return blk[4]; } float* W2() { return blk[5]; }
+    float* D1() { return blk[6]; }
+
+    int alloc(bool keep_data) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < (keep_data ? 7 : 6) && e == cudaSuccess; ++i) e = get(&blk[i], B * sizeof(float));
+        if (e == cudaSuccess) e = get(&csU, 2 * (size_t)C * sizeof(double));
+        if (e == cudaSuccess) e = get(&csV, 2 * (size_t)C * sizeof(double));
+        if (e == cudaSuccess) e = get(&sc, S_COUNT * sizeof(double));
+        if (e == cudaSuccess) e = get(&xs, X_COUNT * sizeof(double));
+        if (e == cudaSuccess) e = get(&resid, nresid * sizeof(double));
+        if (e == cudaSuccess) e = get(&act, nact * sizeof(int));
+        if (e == cudaSuccess) e = get(&iters, nsolves * sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_cuda_error(e);
+            return MDC_ERR_OOM;
+        }
+        cudaMemsetAsync(xs, 0, X_COUNT * sizeof(double), s);
+        cudaMemsetAsync(act, 0, nact * sizeof(int), s);
+        cudaMemsetAsync(iters, 0, nsolves * sizeof(int), s);
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        fill_d<<<1, 256, 0, s>>>(resid, nresid, -1.0);
+        return MDC_OK;
+    }
+
+    void rfft(mdc_plan* q, const float* x, const float* x2, const int* cutp, Coef scale, int conj, int voff,
+              const int* active) {
+        RfftArgs a{};
+        a.x = x; a.x2 = x2; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt; a.logn = q->logn; a.nf = q->nf;
+        a.cut = cutp; a.scale = scale; a.conj = conj; a.X = q->specA; a.ldv = LD(); a.voff = voff0 + voff;
+        a.tw = q->tw; a.active = active;
+        launch_rfft(q, a, s);
+    }
+    void irfft(mdc_plan* q, int voff, int conj_in, float* out, Coef a_mdc, const int* cutp, const float* base,
+               Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active) {
+        IrfftArgs a{};
+        a.Y = q->specB; a.ldv = LD(); a.voff = voff0 + voff; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt;
+        a.logn = q->logn; a.nf = q->nf; a.conj_in = conj_in; a.scale = (float)(q->dt * q->dr / (double)q->nt);
+        a.out = out; a.a_mdc = a_mdc; a.a_base = a_base; a.a_prev = a_prev; a.base = base; a.cut = cutp;
+        a.reverse_out = reverse; a.colsum = colsum; a.tw = q->tw; a.active = active;
+        launch_irfft(q, a, s);
+    }
+
+    // u-hat = d = [Theta R f_d+ ; 0] (kernel pr), column sums into csU; D1 keeps d for refinement.
+    void data_pass(const float* fd) {
+        const Coef zero = C1(0.f);
+        rfft(pr, fd, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
+        launch_product(pr, false, pr->specA, LD(), voff0, pr->specB, LD(), voff0, nv, s, nullptr);
+        irfft(pr, 0, 0, U1(), C1(1.f), cut, nullptr, zero, zero, csU, 0, nullptr);
+        cudaMemsetAsync(U2(), 0, B * sizeof(float), s);
+        cudaMemsetAsync(csU + C, 0, C * sizeof(double), s);
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            norm_store<<<1, RED_THREADS, 0, s>>>(csU, 2 * C, xs + X_DNORM);
+        }
+        if (D1()) {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            copy_f<<<elementwise_grid(B), 256, 0, s>>>(B, U1(), D1());
+        }
+    }
+
+    // u-hat = d - M x with the kernel pr:  [D1 - x1 + Theta R x2 ; -x2 + Theta R* x1], sums into csU.
+    void residual_pass(const float* x1, const float* x2) {
+        rfft(pr, x2, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
+        rfft(pr, x1, nullptr, nullptr, C1(1.f), 1, nv, nullptr);
+        launch_product(pr, false, pr->specA, LD(), voff0, pr->specB, LD(), voff0, 2 * nv, s, nullptr);
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            copy_f<<<elementwise_grid(B), 256, 0, s>>>(B, D1(), U1());
+        }
+        irfft(pr, 0, 0, U1(), C1(1.f), cut, x1, C1(-1.f), C1(1.f), csU, 0, nullptr);
+        irfft(pr, nv, 1, U2(), C1(1.f), cut, x2, C1(-1.f), C1(0.f), csU + C, 0, nullptr);
+    }
+
+    // M^H u with u = u-hat / beta:  v-hat <- [a - (R*)^H Theta b ; b - R^H Theta a] + vprev * v-hat
+    void apply_MH(const int* active, Coef vprev) {
+        rfft(p, U1(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, active);
+        rfft(p, U2(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, active);
+        launch_product(p, true, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, active);
+        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, active);
+        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, active);
+    }
+
+    // LSQR start on u-hat (holding the right-hand side and its column sums): beta_1, then
+    // alpha_1 v_1 = M^H u_1, w_1 = v_1; x is zeroed or kept (refinement accumulates into it).
+    void lsqr_init(float* x1, float* x2, bool zero_x, int* act0, double* resid0) {
+        const Coef zero = C1(0.f);
+        const int eg = elementwise_grid(B);
+        cudaMemsetAsync(sc, 0, S_COUNT * sizeof(double), s);
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, 2 * C, resid0, act0 + 1);
+        }
+        apply_MH(act0 + 1, zero);
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(sc, csV, 2 * C, act0 + 1);
+        }
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        if (zero_x) lsqr_xw_init<<<eg, 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc);
+        else lsqr_w_init<<<eg, 256, 0, s>>>(B, W1(), W2(), V1(), V2(), sc);
+    }
+    // One LSQR iteration in four phases around the forward and adjoint products (so several
+    // systems can share one product over their stacked columns).
+    //   u-hat <- M v - alpha u:  M [a; b] = [a - Theta R b ; b - Theta R* a]
+    void iter_fwd_pre(const int* a) {
+        rfft(p, V2(), nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 0, 0, a);
+        rfft(p, V1(), nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 1, nv, a);
+    }
+    void iter_fwd_post(const int* a) {
+        irfft(p, 0, 0, U1(), C1(-1.f), cut, V1(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU, 0, a);
+        irfft(p, nv, 1, U2(), C1(-1.f), cut, V2(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU + C, 0, a);
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, 2 * C, a);
+    }
+    //   v-hat <- M^H u - beta v
+    void iter_adj_pre(const int* a) {
+        rfft(p, U1(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, a);
+        rfft(p, U2(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, a);
+    }
+    void iter_adj_post(int it, int niter, double tol, int* act0, double* resid0, int* itp, float* x1, float* x2) {
+        const int* a = act0 + it;
+        const Coef vprev = CD(1.f, sc + S_V_PREV);
+        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, a);
+        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, a);
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, csV, 2 * C, a, act0 + it + 1, resid0, itp, it, niter,
+                                                        tol);
+        }
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        lsqr_xw<<<elementwise_grid(B), 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc, a);
+    }
+
+    // LSQR on u-hat (already holding the right-hand side and its column sums); x accumulates.
+    // act0: niter + 2 flags, resid0: niter + 1 entries, itp: iteration counter of this solve.
+    void lsqr(float* x1, float* x2, int niter, double tol, bool zero_x, int* act0, double* resid0, int* itp) {
+        lsqr_init(x1, x2, zero_x, act0, resid0);
+        for (int it = 1; it <= niter; ++it) {
+            const int* a = act0 + it;
+            iter_fwd_pre(a);
+            launch_product(p, false, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, a);
+            iter_fwd_post(a);
+            iter_adj_pre(a);
+            launch_product(p, true, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, a);
+            iter_adj_post(it, niter, tol, act0, resid0, itp, x1, x2);
+        }
+    }
+
+    // Eq. 6: g- = R f+ - f-,  g+* = f+ - R* f-,  f+ = f_d+ + f_m+ ; g+ = time reversal of g+*
+    void greens(const float* fd, const float* fm, const float* fmp, float* gm, float* gp) {
+        const Coef zero = C1(0.f);
+        float* fplus = W1();
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            vec_add<<<elementwise_grid(B), 256, 0, s>>>(B, fd, fmp, fplus);
+        }
+        rfft(pr, fplus, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
+        rfft(pr, fm, nullptr, nullptr, C1(1.f), 1, nv, nullptr);
+        launch_product(pr, false, pr->specA, LD(), voff0, pr->specB, LD(), voff0, 2 * nv, s, nullptr);
+        if (gm) irfft(pr, 0, 0, gm, C1(1.f), nullptr, fm, C1(-1.f), zero, nullptr, 0, nullptr);
+        if (gp) irfft(pr, nv, 1, gp, C1(-1.f), nullptr, fplus, C1(1.f), zero, nullptr, 1, nullptr);
     }
 };
 
 }  // namespace
 
-int run_marchenko_lsqr(mdc_plan* p, const int* cut, const float* fd, int nv, int niter, double tol,
-                       float* fm, float* fmp, float* gm, float* gp, double* resid_h, int* iters_h,
-                       cudaStream_t s) {
-    const int n = p->ns;
-    const int C = n * nv;
-    const int64_t B = (int64_t)p->nt * C;
+// Solve Eq. 5 with LSQR on kernel p; with a reference kernel pr != p, refine: each outer step
+// recomputes u-hat = d - M_pr x in float32 and runs niter_ref further LSQR iterations on p
+// from the current x (the correction accumulates into x).
+int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, int nv, int niter, int nref,
+                  int niter_ref, double tol, float* fm, float* fmp, float* gm, float* gp, double* resid_h,
+                  double* final_h, int* iters_h, cudaStream_t s) {
+    Solver S;
+    S.p = p;
+    S.pr = pr;
+    S.nv = nv;
+    S.n = p->ns;
+    S.C = p->ns * nv;
+    S.B = (int64_t)p->nt * S.C;
+    S.s = s;
+    S.cut = cut;
+    S.nsolves = 1 + nref;
+    S.nresid = (niter + 1) + nref * (niter_ref + 1);
+    S.nact = (niter + 2) + nref * (niter_ref + 2);
     int st = ensure_scratch(p, 2 * nv);
+    if (st == MDC_OK && pr != p) st = ensure_scratch(pr, 2 * nv);
     if (st != MDC_OK) return st;
-    Buffers b;
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&b.blk[i], B * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&b.csU, 2 * C * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b.csV, 2 * C * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b.sc, S_COUNT * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b.resid, (niter + 1) * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b.act, (niter + 2) * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&b.iters, sizeof(int));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        set_cuda_error(e);
-        return MDC_ERR_OOM;
-    }
-    float *U1 = b.blk[0], *U2 = b.blk[1], *V1 = b.blk[2], *V2 = b.blk[3], *W1 = b.blk[4], *W2 = b.blk[5];
-    const double* sc = b.sc;
-    const int eg = elementwise_grid(B);
+    const bool refine = nref > 0;
+    st = S.alloc(refine || final_h != nullptr);
+    if (st != MDC_OK) return st;
 
-    cudaMemsetAsync(b.sc, 0, S_COUNT * sizeof(double), s);
-    cudaMemsetAsync(b.act, 0, (niter + 2) * sizeof(int), s);
-    cudaMemsetAsync(b.iters, 0, sizeof(int), s);
-    {
+    S.data_pass(fd);
+    S.lsqr(fm, fmp, niter, tol, true, S.act, S.resid, S.iters);
+    int aoff = niter + 2, roff = niter + 1;
+    for (int o = 0; o < nref; ++o) {
+        S.residual_pass(fm, fmp);
+        S.lsqr(fm, fmp, niter_ref, tol, false, S.act + aoff, S.resid + roff, S.iters + 1 + o);
+        aoff += niter_ref + 2;
+        roff += niter_ref + 1;
+    }
+    if (final_h) {
+        S.residual_pass(fm, fmp);
         LaunchScope ls(p, s, MDC_KC_SOLVER);
-        fill_d<<<1, 256, 0, s>>>(b.resid, niter + 1, -1.0);
+        norm_ratio<<<1, RED_THREADS, 0, s>>>(S.csU, 2 * S.C, S.xs + X_DNORM, S.xs + X_FINAL);
     }
+    if (gm || gp) S.greens(fd, fm, fmp, gm, gp);
 
-    const float irscale = (float)(p->dt * p->dr / (double)p->nt);
-    auto rfft = [&](const float* x, const float* x2, const int* cutp, Coef scale, int conj, int voff,
-                    const int* active) {
-        RfftArgs a{};
-        a.x = x; a.x2 = x2; a.C = C; a.S = n; a.nv = nv; a.nt = p->nt; a.logn = p->logn; a.nf = p->nf;
-        a.cut = cutp; a.scale = scale; a.conj = conj; a.X = p->specA; a.ldv = 2 * nv; a.voff = voff;
-        a.tw = p->tw; a.active = active;
-        launch_rfft(p, a, s);
-    };
-    auto irfft = [&](int voff, int conj_in, float* out, Coef a_mdc, const int* cutp, const float* base,
-                     Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active) {
-        IrfftArgs a{};
-        a.Y = p->specB; a.ldv = 2 * nv; a.voff = voff; a.C = C; a.S = n; a.nv = nv; a.nt = p->nt;
-        a.logn = p->logn; a.nf = p->nf; a.conj_in = conj_in; a.scale = irscale; a.out = out;
-        a.a_mdc = a_mdc; a.a_base = a_base; a.a_prev = a_prev; a.base = base; a.cut = cutp;
-        a.reverse_out = reverse; a.colsum = colsum; a.tw = p->tw; a.active = active;
-        launch_irfft(p, a, s);
-    };
-    const Coef zero = C1(0.f);
-
-    // d = [Theta R f_d+ ; 0] -> u-hat, beta_1
-    rfft(fd, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
-    launch_product(p, false, p->specA, 2 * nv, 0, p->specB, 2 * nv, 0, nv, s, nullptr);
-    irfft(0, 0, U1, C1(1.f), cut, nullptr, zero, zero, b.csU, 0, nullptr);
-    cudaMemsetAsync(U2, 0, B * sizeof(float), s);
-    cudaMemsetAsync(b.csU + C, 0, C * sizeof(double), s);
-    {
-        LaunchScope ls(p, s, MDC_KC_SOLVER);
-        lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(b.sc, b.csU, 2 * C, b.resid, b.act + 1);
-    }
-    // alpha_1 v_1 = M^H u_1 :  M^H [a; b] = [a - (R*)^H Theta b ; b - R^H Theta a]
-    auto apply_MH = [&](const int* active, Coef vprev) {
-        rfft(U1, nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, active);
-        rfft(U2, nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, active);
-        launch_product(p, true, p->specA, 2 * nv, 0, p->specB, 2 * nv, 0, 2 * nv, s, active);
-        irfft(nv, 1, V1, C1(-1.f), nullptr, U1, CD(1.f, sc + S_INV_BETA), vprev, b.csV, 0, active);
-        irfft(0, 0, V2, C1(-1.f), nullptr, U2, CD(1.f, sc + S_INV_BETA), vprev, b.csV + C, 0, active);
-    };
-    apply_MH(b.act + 1, zero);
-    {
-        LaunchScope ls(p, s, MDC_KC_SOLVER);
-        lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(b.sc, b.csV, 2 * C, b.act + 1);
-    }
-    {
-        LaunchScope ls(p, s, MDC_KC_SOLVER);
-        lsqr_xw_init<<<eg, 256, 0, s>>>(B, fm, fmp, W1, W2, V1, V2, sc);
-    }
-
-    for (int it = 1; it <= niter; ++it) {
-        const int* act = b.act + it;
-        // u-hat <- M v - alpha u,  v = v-hat / alpha,  u = u-hat / beta
-        //   M [a; b] = [a - Theta R b ; b - Theta R* a]
-        rfft(V2, nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 0, 0, act);
-        rfft(V1, nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 1, nv, act);
-        launch_product(p, false, p->specA, 2 * nv, 0, p->specB, 2 * nv, 0, 2 * nv, s, act);
-        irfft(0, 0, U1, C1(-1.f), cut, V1, CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), b.csU, 0, act);
-        irfft(nv, 1, U2, C1(-1.f), cut, V2, CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), b.csU + C, 0,
-              act);
-        {
-            LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_beta<<<1, RED_THREADS, 0, s>>>(b.sc, b.csU, 2 * C, act);
-        }
-        // v-hat <- M^H u - beta v
-        apply_MH(act, CD(1.f, sc + S_V_PREV));
-        {
-            LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(b.sc, b.csV, 2 * C, act, b.act + it + 1, b.resid,
-                                                        b.iters, it, niter, tol);
-        }
-        {
-            LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_xw<<<eg, 256, 0, s>>>(B, fm, fmp, W1, W2, V1, V2, sc, act);
-        }
-    }
-
-    // Eq. 6: g- = R f+ - f-,  g+* = f+ - R* f-,  f+ = f_d+ + f_m+ ; g+ = time reversal of g+*
-    if (gm || gp) {
-        float* fplus = W1;   // w is no longer needed
-        {
-            LaunchScope ls(p, s, MDC_KC_SOLVER);
-            vec_add<<<eg, 256, 0, s>>>(B, fd, fmp, fplus);
-        }
-        rfft(fplus, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
-        rfft(fm, nullptr, nullptr, C1(1.f), 1, nv, nullptr);
-        launch_product(p, false, p->specA, 2 * nv, 0, p->specB, 2 * nv, 0, 2 * nv, s, nullptr);
-        if (gm) irfft(0, 0, gm, C1(1.f), nullptr, fm, C1(-1.f), zero, nullptr, 0, nullptr);
-        if (gp) irfft(nv, 1, gp, C1(-1.f), nullptr, fplus, C1(1.f), zero, nullptr, 1, nullptr);
-    }
-
-    std::vector<double> sch(S_COUNT);
-    std::vector<double> rh(niter + 1);
-    int ih = 0;
-    e = cudaMemcpyAsync(sch.data(), b.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rh.data(), b.resid, (niter + 1) * sizeof(double),
-                                              cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ih, b.iters, sizeof(int), cudaMemcpyDeviceToHost, s);
+    std::vector<double> sch(S_COUNT), rh(S.nresid), xh(X_COUNT);
+    std::vector<int> ih(S.nsolves);
+    cudaError_t e = cudaMemcpyAsync(sch.data(), S.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rh.data(), S.resid, S.nresid * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xh.data(), S.xs, X_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ih.data(), S.iters, S.nsolves * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_cuda_error(e);
         return MDC_ERR_CUDA;
     }
-    if (resid_h) for (int i = 0; i <= niter; ++i) resid_h[i] = rh[i];
-    if (iters_h) *iters_h = ih;
+    if (resid_h) for (int i = 0; i < S.nresid; ++i) resid_h[i] = rh[i];
+    if (final_h) *final_h = xh[X_FINAL];
+    if (iters_h) {
+        int tot = 0;
+        for (int v : ih) tot += v;
+        *iters_h = tot;
+    }
+    int err = 0;
+    cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) return MDC_ERR_TIMEOUT;
     return sch[S_STATUS] != 0.0 ? MDC_ERR_NUMERIC : MDC_OK;
 }
 
@@ -341,6 +483,399 @@ extern "C" int marchenko_lsqr(mdc_handle R, const int* window, const float* fd_p
     if (!R || !window || !fd_plus || !f_minus || !f_mplus || nv < 1 || niter < 1) return MDC_ERR_ARG;
     if (R->nr != R->ns) return MDC_ERR_ARG;
     if (!std::isfinite(tol)) return MDC_ERR_ARG;
-    return mdc::run_marchenko_lsqr(R, window, fd_plus, nv, niter, tol, f_minus, f_mplus, g_minus, g_plus,
-                                   resid, iters_done, (cudaStream_t)stream);
+    return mdc::run_marchenko(R, R, window, fd_plus, nv, niter, 0, 0, tol, f_minus, f_mplus, g_minus, g_plus,
+                              resid, nullptr, iters_done, (cudaStream_t)stream);
+}
+
+extern "C" int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int* window, const float* fd_plus,
+                                      int nv, int niter, int nrefine, int niter_refine, double tol, float* f_minus,
+                                      float* f_mplus, float* g_minus, float* g_plus, double* resid,
+                                      double* final_residual, int* iters_done, void* stream) {
+    if (!R || !R_ref || !window || !fd_plus || !f_minus || !f_mplus || nv < 1 || niter < 1) return MDC_ERR_ARG;
+    if (nrefine < 0 || (nrefine > 0 && niter_refine < 1)) return MDC_ERR_ARG;
+    if (R->nr != R->ns || R_ref->nr != R->nr || R_ref->ns != R->ns || R_ref->nt != R->nt ||
+        R_ref->nf != R->nf || R_ref->storage != MDC_C64)
+        return MDC_ERR_ARG;
+    if (!std::isfinite(tol)) return MDC_ERR_ARG;
+    return mdc::run_marchenko(R, R_ref, window, fd_plus, nv, niter, nrefine, niter_refine, tol, f_minus, f_mplus,
+                              g_minus, g_plus, resid, final_residual, iters_done, (cudaStream_t)stream);
+}
+
+// ======================================================================== serving
+// Continuous batching of redatuming jobs (Eq. 5 systems for groups of focusing points).
+// Each job keeps its own LSQR state (vectors and float64 scalars) resident on the device.
+// srv_step admits queued jobs while the HBM budget and the column capacity allow (their
+// data vector and LSQR start run as their own passes), then advances EVERY running job
+// by one LSQR iteration with their columns stacked side by side in one spectrum: one
+// forward and one adjoint product stream the kernel once for all jobs.  Jobs that finish
+// a solve move to refinement (float32 residual on the reference kernel) or complete
+// (Green's functions, results copied to the caller's host buffers).
+#include <chrono>
+#include <deque>
+#include <unordered_map>
+
+namespace mdc {
+namespace {
+
+enum JobState { JOB_QUEUED = 0, JOB_RUNNING = 1, JOB_DONE = 2, JOB_FAILED = 3 };
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServeJob {
+    int64_t id = 0;
+    int nv = 0, niter = 0;
+    double tol = 0.0;
+    std::vector<int> cut_h;
+    std::vector<float> fd_h;
+    float* out[4] = {};          // caller host buffers: f-, f_m+, g-, g+ (nullable)
+    int state = JOB_QUEUED, status = MDC_OK;
+    Solver* S = nullptr;
+    int* cut_d = nullptr;
+    float* fd_d = nullptr;
+    float* x[4] = {};            // device f-, f_m+, g-, g+
+    int solve = 0, it = 0, aoff = 0, roff = 0;
+    int iters = 0;
+    double final_resid = -1.0;
+    double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
+    int64_t bytes = 0;
+};
+
+}  // namespace
+}  // namespace mdc
+
+using mdc::ServeJob;
+
+struct mdc_server {
+    mdc_plan* p = nullptr;       // kernel used inside LSQR
+    mdc_plan* pr = nullptr;      // float32 reference kernel (data, residuals, Green's functions)
+    int64_t budget = 0, used = 0;
+    int max_cols = 0, cols = 0;
+    int nref = 0, niter_ref = 0;
+    cudaStream_t s = nullptr;
+    int64_t next_id = 1;
+    std::deque<ServeJob*> queue;
+    std::vector<ServeJob*> running;
+    std::unordered_map<int64_t, ServeJob*> jobs;
+    int* flags_h = nullptr;      // pinned
+    int flags_cap = 0;
+};
+
+namespace mdc {
+namespace {
+
+int64_t job_bytes(const mdc_plan* p, int nv) {
+    const int64_t C = (int64_t)p->ns * nv, B = (int64_t)p->nt * C;
+    return 12 * B * 4 + 4 * C * 8 + C * 4 + (1 << 20);
+}
+
+void free_job_device(mdc_server* v, ServeJob* j) {
+    delete j->S;
+    j->S = nullptr;
+    cudaFreeAsync(j->cut_d, v->s);
+    cudaFreeAsync(j->fd_d, v->s);
+    for (float*& q : j->x) {
+        if (q) cudaFreeAsync(q, v->s);
+        q = nullptr;
+    }
+    j->cut_d = nullptr;
+    j->fd_d = nullptr;
+}
+
+int start_job(mdc_server* v, ServeJob* j) {
+    mdc_plan* p = v->p;
+    const int64_t C = (int64_t)p->ns * j->nv, B = (int64_t)p->nt * C;
+    cudaError_t e = cudaMallocAsync((void**)&j->cut_d, C * sizeof(int), v->s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&j->fd_d, B * sizeof(float), v->s);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMallocAsync((void**)&j->x[i], B * sizeof(float), v->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->cut_d, j->cut_h.data(), C * sizeof(int), cudaMemcpyHostToDevice, v->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->fd_d, j->fd_h.data(), B * sizeof(float), cudaMemcpyHostToDevice, v->s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_cuda_error(e);
+        free_job_device(v, j);
+        return MDC_ERR_OOM;
+    }
+    Solver* S = new Solver();
+    S->p = p;
+    S->pr = v->pr;
+    S->nv = j->nv;
+    S->n = p->ns;
+    S->C = (int)C;
+    S->B = B;
+    S->s = v->s;
+    S->cut = j->cut_d;
+    S->async_alloc = true;
+    S->nsolves = 1 + v->nref;
+    S->nresid = (j->niter + 1) + v->nref * (v->niter_ref + 1);
+    S->nact = (j->niter + 2) + v->nref * (v->niter_ref + 2);
+    j->S = S;
+    int st = S->alloc(true);
+    if (st != MDC_OK) {
+        free_job_device(v, j);
+        return st;
+    }
+    S->layout(0, 0);
+    S->data_pass(j->fd_d);
+    S->lsqr_init(j->x[0], j->x[1], true, S->act, S->resid);
+    j->solve = 0;
+    j->it = 0;
+    j->aoff = 0;
+    j->roff = 0;
+    return MDC_OK;
+}
+
+// Complete a finished job: float32 residual check, Green's functions, results to the host.
+void finish_job(mdc_server* v, ServeJob* j) {
+    Solver* S = j->S;
+    S->layout(0, 0);
+    S->residual_pass(j->x[0], j->x[1]);
+    {
+        LaunchScope ls(v->p, v->s, MDC_KC_SOLVER);
+        norm_ratio<<<1, RED_THREADS, 0, v->s>>>(S->csU, 2 * S->C, S->xs + X_DNORM, S->xs + X_FINAL);
+    }
+    S->greens(j->fd_d, j->x[0], j->x[1], j->x[2], j->x[3]);
+    const size_t bytes = (size_t)S->B * sizeof(float);
+    for (int i = 0; i < 4; ++i)
+        if (j->out[i]) cudaMemcpyAsync(j->out[i], j->x[i], bytes, cudaMemcpyDeviceToHost, v->s);
+}
+
+}  // namespace
+}  // namespace mdc
+
+using namespace mdc;
+
+extern "C" int srv_create(mdc_server** out, mdc_handle R, mdc_handle R_ref, int64_t hbm_budget_bytes, int max_cols,
+                          int nrefine, int niter_refine, void* stream) {
+    if (!out) return MDC_ERR_ARG;
+    *out = nullptr;
+    if (!R || hbm_budget_bytes <= 0 || max_cols < 2 || R->nr != R->ns || nrefine < 0) return MDC_ERR_ARG;
+    if (R_ref && (R_ref->storage != MDC_C64 || R_ref->nr != R->nr || R_ref->ns != R->ns || R_ref->nt != R->nt ||
+                  R_ref->nf != R->nf))
+        return MDC_ERR_ARG;
+    if (nrefine > 0 && (!R_ref || niter_refine < 1)) return MDC_ERR_ARG;
+    mdc_server* v = new (std::nothrow) mdc_server();
+    if (!v) return MDC_ERR_OOM;
+    v->p = R;
+    v->pr = R_ref ? R_ref : R;
+    v->budget = hbm_budget_bytes;
+    v->max_cols = max_cols;
+    v->nref = nrefine;
+    v->niter_ref = niter_refine;
+    v->s = (cudaStream_t)stream;
+    // one product path for every batch composition: a job's columns see the same arithmetic
+    // alone or in a mix
+    R->force_tc = (R->storage == MDC_C16F || R->storage == MDC_CBF16);
+    int st = ensure_scratch(R, max_cols);
+    if (st == MDC_OK && v->pr != R) st = ensure_scratch(v->pr, max_cols);
+    if (st != MDC_OK) {
+        delete v;
+        return st;
+    }
+    *out = v;
+    return MDC_OK;
+}
+
+extern "C" int srv_submit(mdc_server* v, const int* window_host, const float* fd_plus_host, int nv, int niter,
+                          double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+                          float* g_plus_host, int64_t* job_id) {
+    if (!v || !window_host || !fd_plus_host || nv < 1 || niter < 1 || !job_id || !std::isfinite(tol))
+        return MDC_ERR_ARG;
+    if (2 * nv > v->max_cols) return MDC_ERR_BUDGET;
+    if (job_bytes(v->p, nv) > v->budget) return MDC_ERR_BUDGET;
+    ServeJob* j = new (std::nothrow) ServeJob();
+    if (!j) return MDC_ERR_OOM;
+    const int64_t C = (int64_t)v->p->ns * nv, B = (int64_t)v->p->nt * C;
+    j->id = v->next_id++;
+    j->nv = nv;
+    j->niter = niter;
+    j->tol = tol;
+    j->cut_h.assign(window_host, window_host + C);
+    j->fd_h.assign(fd_plus_host, fd_plus_host + B);
+    j->out[0] = f_minus_host;
+    j->out[1] = f_mplus_host;
+    j->out[2] = g_minus_host;
+    j->out[3] = g_plus_host;
+    j->bytes = job_bytes(v->p, nv);
+    j->t_submit = now_s();
+    v->queue.push_back(j);
+    v->jobs[j->id] = j;
+    *job_id = j->id;
+    return MDC_OK;
+}
+
+extern "C" int srv_step(mdc_server* v, int* completed) {
+    if (!v) return MDC_ERR_ARG;
+    int ndone = 0;
+    // 1. admission, in arrival order, while memory and columns allow
+    while (!v->queue.empty()) {
+        ServeJob* j = v->queue.front();
+        if (v->used + j->bytes > v->budget || v->cols + 2 * j->nv > v->max_cols) break;
+        v->queue.pop_front();
+        j->t_start = now_s();
+        const int st = start_job(v, j);
+        if (st != MDC_OK) {
+            j->state = JOB_FAILED;
+            j->status = st;
+            j->t_done = now_s();
+            ++ndone;
+            continue;
+        }
+        j->state = JOB_RUNNING;
+        v->used += j->bytes;
+        v->cols += 2 * j->nv;
+        v->running.push_back(j);
+    }
+    // 2. one LSQR iteration for every running job, columns stacked in one spectrum
+    const int nrun = (int)v->running.size();
+    if (nrun > 0) {
+        int L = 0;
+        std::vector<int> off(nrun);
+        for (int i = 0; i < nrun; ++i) {
+            off[i] = L;
+            L += 2 * v->running[i]->nv;
+        }
+        std::vector<const int*> act(nrun);
+        for (int i = 0; i < nrun; ++i) {
+            ServeJob* j = v->running[i];
+            j->S->layout(L, off[i]);
+            act[i] = j->S->act + j->aoff + j->it + 1;
+            j->S->iter_fwd_pre(act[i]);
+        }
+        launch_product(v->p, false, v->p->specA, L, 0, v->p->specB, L, 0, L, v->s, nullptr);
+        for (int i = 0; i < nrun; ++i) v->running[i]->S->iter_fwd_post(act[i]);
+        for (int i = 0; i < nrun; ++i) v->running[i]->S->iter_adj_pre(act[i]);
+        launch_product(v->p, true, v->p->specA, L, 0, v->p->specB, L, 0, L, v->s, nullptr);
+        for (int i = 0; i < nrun; ++i) {
+            ServeJob* j = v->running[i];
+            const int niter = j->solve == 0 ? j->niter : v->niter_ref;
+            j->S->iter_adj_post(j->it + 1, niter, j->tol, j->S->act + j->aoff, j->S->resid + j->roff,
+                                j->S->iters + j->solve, j->x[0], j->x[1]);
+            j->it += 1;
+            j->S->layout(0, 0);
+        }
+        // 3. which jobs go on: read each job's continue flag for its next iteration
+        if (v->flags_cap < nrun) {
+            if (v->flags_h) cudaFreeHost(v->flags_h);
+            v->flags_cap = nrun * 2;
+            if (cudaMallocHost((void**)&v->flags_h, v->flags_cap * sizeof(int)) != cudaSuccess) {
+                v->flags_h = nullptr;
+                v->flags_cap = 0;
+                return MDC_ERR_OOM;
+            }
+        }
+        for (int i = 0; i < nrun; ++i) {
+            ServeJob* j = v->running[i];
+            cudaMemcpyAsync(v->flags_h + i, j->S->act + j->aoff + j->it + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                            v->s);
+        }
+        cudaError_t e = cudaStreamSynchronize(v->s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            return MDC_ERR_CUDA;
+        }
+        // 4. finished solves: refine or complete
+        std::vector<ServeJob*> keep, fin;
+        for (int i = 0; i < nrun; ++i) {
+            ServeJob* j = v->running[i];
+            if (v->flags_h[i]) {
+                keep.push_back(j);
+                continue;
+            }
+            if (j->solve < v->nref) {
+                const int niter = j->solve == 0 ? j->niter : v->niter_ref;
+                j->S->residual_pass(j->x[0], j->x[1]);
+                j->aoff += niter + 2;
+                j->roff += niter + 1;
+                j->solve += 1;
+                j->it = 0;
+                j->S->lsqr_init(j->x[0], j->x[1], false, j->S->act + j->aoff, j->S->resid + j->roff);
+                keep.push_back(j);
+            } else {
+                finish_job(v, j);
+                fin.push_back(j);
+            }
+        }
+        if (!fin.empty()) {
+            std::vector<std::vector<int>> its(fin.size());
+            std::vector<double> res(fin.size());
+            for (size_t q = 0; q < fin.size(); ++q) {
+                its[q].resize(fin[q]->S->nsolves);
+                cudaMemcpyAsync(its[q].data(), fin[q]->S->iters, its[q].size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                v->s);
+                cudaMemcpyAsync(&res[q], fin[q]->S->xs + X_FINAL, sizeof(double), cudaMemcpyDeviceToHost, v->s);
+            }
+            e = cudaStreamSynchronize(v->s);
+            if (e != cudaSuccess) {
+                set_cuda_error(e);
+                return MDC_ERR_CUDA;
+            }
+            for (size_t q = 0; q < fin.size(); ++q) {
+                ServeJob* j = fin[q];
+                int tot = 0;
+                for (int x : its[q]) tot += x;
+                j->iters = tot;
+                j->final_resid = res[q];
+                j->t_done = now_s();
+                j->state = JOB_DONE;
+                v->used -= j->bytes;
+                v->cols -= 2 * j->nv;
+                free_job_device(v, j);
+                ++ndone;
+            }
+        }
+        v->running.swap(keep);
+    }
+    if (completed) *completed = ndone;
+    return MDC_OK;
+}
+
+extern "C" int srv_poll(mdc_server* v, int64_t id, int* state, int* iters, double* final_residual,
+                        double* latency_s, double* queue_s) {
+    if (!v) return MDC_ERR_ARG;
+    auto it = v->jobs.find(id);
+    if (it == v->jobs.end()) return MDC_ERR_ARG;
+    ServeJob* j = it->second;
+    if (state) *state = j->state;
+    if (iters) *iters = j->iters;
+    if (final_residual) *final_residual = j->final_resid;
+    if (latency_s) *latency_s = j->state >= JOB_DONE ? j->t_done - j->t_submit : -1.0;
+    if (queue_s) *queue_s = j->state >= JOB_RUNNING ? j->t_start - j->t_submit : -1.0;
+    return j->state == JOB_FAILED ? j->status : MDC_OK;
+}
+
+extern "C" int srv_release(mdc_server* v, int64_t id) {
+    if (!v) return MDC_ERR_ARG;
+    auto it = v->jobs.find(id);
+    if (it == v->jobs.end()) return MDC_ERR_ARG;
+    if (it->second->state < JOB_DONE) return MDC_ERR_STATE;
+    delete it->second;
+    v->jobs.erase(it);
+    return MDC_OK;
+}
+
+extern "C" int srv_stats(mdc_server* v, int* queued, int* running, int64_t* bytes_in_use, int* cols_in_use) {
+    if (!v) return MDC_ERR_ARG;
+    if (queued) *queued = (int)v->queue.size();
+    if (running) *running = (int)v->running.size();
+    if (bytes_in_use) *bytes_in_use = v->used;
+    if (cols_in_use) *cols_in_use = v->cols;
+    return MDC_OK;
+}
+
+extern "C" int srv_destroy(mdc_server* v) {
+    if (!v) return MDC_ERR_ARG;
+    cudaStreamSynchronize(v->s);
+    for (auto& kv : v->jobs) {
+        if (kv.second->S) free_job_device(v, kv.second);
+        delete kv.second;
+    }
+    cudaStreamSynchronize(v->s);
+    if (v->flags_h) cudaFreeHost(v->flags_h);
+    v->p->force_tc = false;
+    delete v;
+    return MDC_OK;
 }

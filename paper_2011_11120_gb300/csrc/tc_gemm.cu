@@ -142,13 +142,21 @@ template <int BN> struct TcStages { static constexpr int v = BN >= 256 ? 4 : (BN
 
 template <int BN>
 constexpr size_t tc_smem_bytes() {
-    return (size_t)TcStages<BN>::v * (TC_BM * 128 + BN * 128) + 1024 + 256;
+    return (size_t)TcStages<BN>::v * (TC_BM * 128 + BN * 128) + 1024 + 512;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent CTA (one per SM): tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with the
+// column tile fastest, then the row tile, then the frequency.  The TMA/MMA stage ring runs
+// continuously across tiles and the accumulator is double-buffered in TMEM (2 x BN columns),
+// so the epilogue of one tile overlaps the main loop of the next.
 template <bool ADJ, int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
-                   uint32_t idesc, const int* active) {
+                   uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
     if (active && *active == 0) return;
     constexpr int STAGES = TcStages<BN>::v;
     constexpr uint32_t A_BYTES = TC_BM * 128;
@@ -159,71 +167,101 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-    const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), done = su32(bars + 2 * STAGES);
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
+    const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k = blockIdx.z, m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
 
-    if (warp == 0) tmem_alloc(su32(tmem_slot), BN);
+    if (warp == 0) tmem_alloc(su32(tmem_slot), 2 * BN);
     if (threadIdx.x == 32) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(full0 + 8 * i, 1);
             mbar_init(empty0 + 8 * i, 1);
         }
-        mbar_init(done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8 * i, 1);
+            mbar_init(acce0 + 8 * i, 128);
+        }
         fence_mbar_init();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int per_freq = n_tiles_n * n_tiles_m;
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kb = 0; kb < a.kstages; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t round = (uint32_t)(kb / STAGES);
-                if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1)) break;
-                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
-                mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-                if (!ADJ) {
-                    tma_load_3d(sa, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
-                } else {
-                    tma_load_3d(sa, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
-                    tma_load_3d(sa + A_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+            long g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                const int k = tile / per_freq, rem = tile - k * per_freq;
+                const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
+                for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    const uint32_t round = (uint32_t)(g / STAGES);
+                    if (g >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                    mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+                    if (!ADJ) {
+                        tma_load_3d(sa, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
+                    } else {
+                        tma_load_3d(sa, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
+                        tma_load_3d(sa + A_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+                    }
+                    tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
                 }
-                tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
-                issued = kb + 1;
             }
             // drain: every copy this thread issued must have landed before the CTA can exit
-            for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-                mbar_wait(full0 + 8 * (kb % STAGES), (uint32_t)(kb / STAGES) & 1, a.err, 2);
+            for (long q = g > STAGES ? g - STAGES : 0; q < g; ++q)
+                mbar_wait(full0 + 8 * (int)(q % STAGES), (uint32_t)(q / STAGES) & 1, a.err, 2);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int kb = 0; kb < a.kstages; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(full0 + 8 * s, (uint32_t)(kb / STAGES) & 1, a.err, 3)) break;
+            long g = 0;
+            int i = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) break;
                 tc_fence_after();
-                const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+                    const int s = (int)(g % STAGES);
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                    // K-major: +32 bytes per 16 elements inside the swizzled row; MN-major: +16 rows
-                    const uint64_t ad = ADJ ? sdesc(sa + kk * 2048, A_BYTES / 2, 1024) : sdesc(sa + kk * 32, 16, 1024);
-                    const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
-                    umma_f16(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        // K-major: +32 bytes per 16 elements inside the swizzled row; MN-major: +16 rows
+                        const uint64_t ad =
+                            ADJ ? sdesc(sa + kk * 2048, A_BYTES / 2, 1024) : sdesc(sa + kk * 32, 16, 1024);
+                        const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
+                        umma_f16(d, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(empty0 + 8 * s);
                 }
-                umma_commit(empty0 + 8 * s);
+                umma_commit(accf0 + 8 * buf);
             }
-            umma_commit(done);
         }
     } else {
-        if (mbar_wait(done, 0, a.err, 4)) {
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            const int buf = i & 1;
+            if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) break;
             tc_fence_after();
-            const int q = warp & 3;
-            const int row = q * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16);
+            const int k = tile / per_freq, rem = tile - k * per_freq;
+            const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
             const float* sig = a.sigma + (size_t)k * a.ncol;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -248,9 +286,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     float p[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) p[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
-                    const int s = (m0 + row) >> 1;
-                    if ((lane & 1) == 0 && s < a.nout) {
-                        float2* dst = a.out + ((size_t)k * a.nout + s) * a.ldo + a.voff_o;
+                    const int sidx = (m0 + row) >> 1;
+                    if ((lane & 1) == 0 && sidx < a.nout) {
+                        float2* dst = a.out + ((size_t)k * a.nout + sidx) * a.ldo + a.voff_o;
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const int n = nb + j;
@@ -264,13 +302,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             }
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * buf);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, BN);
+        tmem_dealloc(tmem, 2 * BN);
     }
 }
 
@@ -421,6 +461,17 @@ int pick_bn(int n2) {
     return 256;
 }
 
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
 template <bool ADJ, int BN>
 void launch_tc(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& a, uint32_t idesc, dim3 grid,
                cudaStream_t s, const int* active) {
@@ -430,7 +481,10 @@ void launch_tc(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& a, uint
         cudaFuncSetAttribute(tc_gemm_kernel<ADJ, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    tc_gemm_kernel<ADJ, BN><<<grid, TC_THREADS, smem, s>>>(A, B, a, idesc, active);
+    const int n_tiles = (int)(grid.x * grid.y * grid.z);
+    const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
+    tc_gemm_kernel<ADJ, BN><<<ctas, TC_THREADS, smem, s>>>(A, B, a, idesc, active, (int)grid.x, (int)grid.y,
+                                                           n_tiles);
 }
 
 }  // namespace
@@ -449,7 +503,7 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
 }
 
 bool tc_supported(const mdc_plan* p, int ncol) {
-    return (p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncol >= 8 && p->tcB != nullptr &&
+    return (p->storage == MDC_C16F || p->storage == MDC_CBF16) && (ncol >= 8 || p->force_tc) && p->tcB != nullptr &&
            ncol <= p->tc_cap && encode_fn() != nullptr;
 }
 

@@ -114,6 +114,10 @@ CONFIGS = {
     3: Config(3, "mdc-8281x8281-nt1024-nf160", 91, 1024, 0.004, 160, 20, 1, 600.0),
     4: Config(4, "marchenko-1681x1681-nt512-nf150-nv256", 41, 512, 0.004, 150, 20, 256, 800.0,
               point_grid=16, normalise=True, niter=20),
+    # serving: the 8281-trace kernel of config 3 (same draws), normalised like the redatuming
+    # kernel; virtual points, nv and iterations are drawn per job by the serving workload
+    5: Config(3, "serving-8281x8281-nt1024-nf160", 91, 1024, 0.004, 160, 20, 1, 800.0,
+              normalise=True, niter=20),
 }
 
 

@@ -99,3 +99,45 @@ def test_marchenko_rejects_rectangular_kernel():
     with pytest.raises(m.MDCError):
         op.marchenko(torch.zeros((4, 1), dtype=torch.int32, device="cuda"), fd, 3)
     op.close()
+
+
+@pytest.mark.parametrize("storage,tol_plain,tol_refined", [("c16f", 5e-3, 1e-4), ("cbf16", 3e-2, 1e-3)])
+def test_marchenko_reduced_precision_with_refinement(storage, tol_plain, tol_refined):
+    """FP16/BF16 kernel inside LSQR (tensor-core products at 2nv = 8 columns), float32 refinement.
+
+    Stated figures: without refinement the solution carries the operator's rounding amplified
+    by the conditioning (kappa <= 3 here); one refinement step brings it to the float32 level.
+    """
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(21, 512, 150, 2, 800.0)
+    niter = 20
+    res, gm, gp = oracle_solve(cfg, G, cut, fd, niter)
+    Gt = torch.from_numpy(G.astype(np.complex64)).cuda()
+    lo = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage=storage)
+    ref = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    cut_t, fd_t = torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda()
+    plain = lo.marchenko(cut_t, fd_t, niter, greens=False)
+    out = lo.marchenko_refined(ref, cut_t, fd_t, niter, nrefine=1, niter_refine=10)
+    lo.close()
+    ref.close()
+    e_plain = rel(plain["f_minus"].cpu().numpy(), res.x[0])
+    e_ref = max(rel(out["f_minus"].cpu().numpy(), res.x[0]), rel(out["f_mplus"].cpu().numpy(), res.x[1]))
+    e_g = max(rel(out["g_minus"].cpu().numpy(), gm), rel(out["g_plus"].cpu().numpy(), gp))
+    print(f"{storage}: plain {e_plain:.2e} refined {e_ref:.2e} greens {e_g:.2e} "
+          f"final residual {out['final_residual']:.2e} iters {out['iters']}")
+    assert e_plain <= tol_plain
+    assert e_ref <= tol_refined and e_g <= tol_refined
+    assert out["iters"] == niter + 10
+    assert 0.0 <= out["final_residual"] <= 1e-3
+
+
+def test_refined_rejects_reduced_reference():
+    import paper_2011_11120_gb300 as m
+    G = torch.zeros((5, 4, 4), dtype=torch.complex64, device="cuda")
+    a = m.MDC(G, 64, 0.004, 1.0, storage="c16f")
+    b = m.MDC(G, 64, 0.004, 1.0, storage="c16f")
+    fd = torch.zeros((64, 4, 1), device="cuda")
+    with pytest.raises(m.MDCError):
+        a.marchenko_refined(b, torch.zeros((4, 1), dtype=torch.int32, device="cuda"), fd, 3)
+    a.close()
+    b.close()

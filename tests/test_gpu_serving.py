@@ -1,0 +1,147 @@
+"""Continuous-batching server: results equal the single-job solver and the FP64 oracle,
+each job's result is the same alone and in a mix, admission follows the memory budget,
+and jobs arriving mid-flight join running ones."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import marchenko as omar
+from oracle import solvers
+from test_gpu_marchenko import problem, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def make_jobs(cfg, G, specs, seed=0):
+    """Jobs: (nv, niter, tol) with random focusing points at z = 200 m on the problem's grid."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for nv, niter, tol in specs:
+        c = cfg.with_(nv=nv, point_grid=0, z_point=200.0)
+        d = synth.draw(c)
+        d.points = rng.uniform(0, synth.GRID_DX * (cfg.n_side - 1), size=(nv, 2))
+        jobs.append({"nv": nv, "niter": niter, "tol": tol, "cut": synth.window_cutoffs(c, d),
+                     "fd": synth.direct_focusing(c, d)})
+    return jobs
+
+
+def outputs(cfg, nv):
+    return [np.zeros((cfg.nt, cfg.ns, nv), np.float32) for _ in range(4)]
+
+
+def run_server(m, lo, ref, cfg, jobs, schedule, budget=1 << 34, max_cols=64, nref=0, niter_ref=0):
+    """schedule: {step_index: [job indices submitted before that step]}; runs until all done."""
+    srv = m.srv_create(lo.h, ref.h if ref is not None else None, budget, max_cols, nref, niter_ref)
+    outs, ids, step = {}, {}, 0
+    try:
+        while True:
+            for i in schedule.get(step, []):
+                o = outputs(cfg, jobs[i]["nv"])
+                outs[i] = o
+                ids[i] = m.srv_submit(srv, jobs[i]["cut"], jobs[i]["fd"], jobs[i]["nv"], jobs[i]["niter"],
+                                      jobs[i]["tol"], o)
+            m.srv_step(srv)
+            step += 1
+            polls = {i: m.srv_poll(srv, ids[i]) for i in ids}
+            if len(ids) == sum(len(v) for v in schedule.values()) and all(
+                    p["state"] == m.JOB_DONE for p in polls.values()):
+                return outs, polls, step
+            assert step < 500
+    finally:
+        m.srv_destroy(srv)
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg, G, cut, fd = problem(11, 256, 60, 1, 200.0)
+    return cfg, G
+
+
+def test_server_matches_single_job_solver_and_oracle(small):
+    """complex64 kernel, no refinement: every job equals marchenko_lsqr and the FP64 oracle."""
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    jobs = make_jobs(cfg, G, [(3, 12, 0.0), (1, 8, 0.0), (5, 10, 1e-4), (2, 6, 0.0)], seed=1)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    outs, polls, _ = run_server(m, op, None, cfg, jobs, {0: [0, 1], 2: [2], 3: [3]})
+    for i, job in enumerate(jobs):
+        ref = omar.Marchenko(G, cfg.dt, cfg.dr, job["cut"], cfg.nt)
+        res = solvers.lsqr(ref.matvec, ref.rmatvec, ref.data(job["fd"]), niter=job["niter"], tol=job["tol"])
+        gm, _, gp = ref.greens(res.x[0], res.x[1], job["fd"])
+        assert polls[i]["iters"] == res.iters
+        assert rel(outs[i][0], res.x[0]) <= 1e-5 and rel(outs[i][1], res.x[1]) <= 1e-5
+        assert rel(outs[i][2], gm) <= 1e-5 and rel(outs[i][3], gp) <= 1e-5
+        single = op.marchenko(torch.from_numpy(job["cut"]).cuda(), torch.from_numpy(job["fd"]).cuda(),
+                              job["niter"], tol=job["tol"])
+        assert rel(outs[i][0], single["f_minus"].cpu().numpy()) <= 1e-6
+    op.close()
+
+
+def test_server_solo_equals_mix_fp16_with_refinement(small):
+    """FP16 kernel in LSQR + float32 refinement: a job's result alone equals its result in a mix."""
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    jobs = make_jobs(cfg, G, [(3, 12, 0.0), (4, 9, 0.0), (1, 14, 0.0), (6, 7, 0.0)], seed=2)
+    Gt = torch.from_numpy(G.astype(np.complex64)).cuda()
+    lo = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c16f")
+    ref = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    solo, _, _ = run_server(m, lo, ref, cfg, jobs, {0: [0]}, nref=1, niter_ref=5)
+    mix, polls, _ = run_server(m, lo, ref, cfg, jobs, {0: [1, 2], 1: [0], 4: [3]}, nref=1, niter_ref=5)
+    for k in range(4):
+        d = rel(mix[0][k], solo[0][k])
+        print(f"output {k}: solo vs mix rel L2 {d:.2e}")
+        assert d <= 1e-6
+    # accuracy of every mixed job against the converged FP64 solution
+    for i, job in enumerate(jobs):
+        o = omar.Marchenko(G, cfg.dt, cfg.dr, job["cut"], cfg.nt)
+        res = solvers.lsqr(o.matvec, o.rmatvec, o.data(job["fd"]), niter=200, tol=1e-13)
+        e = rel(mix[i][0], res.x[0])
+        print(f"job {i}: rel L2 vs converged FP64 {e:.2e}, final residual {polls[i]['final_residual']:.2e}")
+        assert e <= 1e-3
+        assert polls[i]["iters"] == job["niter"] + 5
+    lo.close()
+    ref.close()
+
+
+def test_server_admission_by_budget_and_mid_flight_arrivals(small):
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    jobs = make_jobs(cfg, G, [(2, 10, 0.0), (2, 10, 0.0), (2, 10, 0.0)], seed=3)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    per_job = 12 * cfg.nt * cfg.ns * 2 * 4 + 4 * cfg.ns * 2 * 8 + cfg.ns * 2 * 4 + (1 << 20)
+    srv = m.srv_create(op.h, None, int(1.5 * per_job), 64)      # room for one job at a time
+    try:
+        ids = [m.srv_submit(srv, j["cut"], j["fd"], j["nv"], j["niter"]) for j in jobs]
+        m.srv_step(srv)
+        st = m.srv_stats(srv)
+        assert st["running"] == 1 and st["queued"] == 2
+        steps = 1
+        while any(m.srv_poll(srv, i)["state"] != m.JOB_DONE for i in ids):
+            m.srv_step(srv)
+            steps += 1
+            assert m.srv_stats(srv)["running"] <= 1
+            assert steps < 100
+        assert steps >= 30          # three jobs of 10 iterations, one at a time
+        q = [m.srv_poll(srv, i)["queue_s"] for i in ids]
+        assert q[0] <= q[1] <= q[2]
+        with pytest.raises(m.MDCError):
+            big = make_jobs(cfg, G, [(40, 5, 0.0)], seed=4)[0]
+            m.srv_submit(srv, big["cut"], big["fd"], 40, 5)          # can never fit the budget
+    finally:
+        m.srv_destroy(srv)
+    # mid-flight arrival: the second job starts while the first is still running
+    srv = m.srv_create(op.h, None, 1 << 34, 64)
+    try:
+        a = m.srv_submit(srv, jobs[0]["cut"], jobs[0]["fd"], 2, 10)
+        for _ in range(3):
+            m.srv_step(srv)
+        b = m.srv_submit(srv, jobs[1]["cut"], jobs[1]["fd"], 2, 10)
+        m.srv_step(srv)
+        assert m.srv_poll(srv, a)["state"] == m.JOB_RUNNING and m.srv_poll(srv, b)["state"] == m.JOB_RUNNING
+        while m.srv_poll(srv, b)["state"] != m.JOB_DONE:
+            m.srv_step(srv)
+        assert m.srv_poll(srv, a)["latency_s"] < m.srv_poll(srv, b)["latency_s"] + 1.0
+    finally:
+        m.srv_destroy(srv)
+    op.close()
