@@ -113,6 +113,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over the process group (all ranks get it)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -249,6 +258,140 @@ def run_redatum(args, dev):
                              "iterations": plain["iters"], "storage": "c64"}}
 
 
+def serve_loop(mdc, srv, arrivals, pool, horizon, drain):
+    """Submit arrivals (t, nv, niter, tol, entry) as their time comes, step the server, and
+    collect completed jobs; returns (completed records, jobs still queued or running)."""
+    t0 = time.perf_counter()
+    ia, pending, done = 0, {}, []
+    while True:
+        now = time.perf_counter() - t0
+        while ia < len(arrivals) and arrivals[ia][0] <= now and now < horizon:
+            _, nv, niter, tol, e = arrivals[ia]
+            cut, fd = pool[e]
+            jid = mdc.srv_submit(srv, cut, fd, nv, niter, tol)
+            pending[jid] = (nv, niter, tol)
+            ia += 1
+        if now >= horizon and (not drain or not pending):
+            break
+        if not pending:
+            time.sleep(0.0005)
+            continue
+        mdc.srv_step(srv)
+        for jid in list(pending):
+            p = mdc.srv_poll(srv, jid)
+            if p["state"] >= mdc.JOB_DONE:
+                done.append(dict(p, nv=pending[jid][0], niter=pending[jid][1], tol=pending[jid][2]))
+                mdc.srv_release(srv, jid)
+                del pending[jid]
+    return done, len(pending), time.perf_counter() - t0
+
+
+def percentile(vals, q):
+    return float(np.percentile(np.asarray(vals), q)) if vals else None
+
+
+def run_serving(args, dev):
+    """Continuous batching of redatuming jobs on the resident FP16 kernel (Poisson arrivals,
+    nv ~ U{1..128}, niter ~ U{10..30}, half of the jobs with tolerance 1e-3)."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from synth import gpu as sgpu
+    cfg = synth.config(args.serving_config)
+    d = synth.draw(cfg.with_(nv=1, point_grid=0))
+    G = sgpu.kernel_on_device(cfg, d)
+    lo = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage="c16f")
+    del G
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(synth.SEED_BASE + 5)
+    extent = synth.GRID_DX * (cfg.n_side - 1)
+    pool = []
+    for _ in range(args.serving_pool):
+        pts = rng.uniform(0.0, extent, size=(128, 2))
+        cut, fd = sgpu.focusing_inputs_on_device(cfg.with_(z_point=800.0), pts, device=dev)
+        fd_h = torch.empty(fd.shape, dtype=torch.float32, pin_memory=True)
+        fd_h.copy_(fd)
+        pool.append((cut.cpu().numpy(), fd_h.numpy()))
+        del fd
+    torch.cuda.empty_cache()
+    per_point = 12 * cfg.nt * cfg.ns * 4 + 4 * cfg.ns * 8 + cfg.ns * 4
+    free = torch.cuda.mem_get_info()[0]
+    max_cols = int(min(2048, 2 * (0.8 * free) // per_point))
+    # scratch of the server: two spectra and the tensor-core operand for max_cols columns
+    scratch = 2 * cfg.nf * cfg.ns * max_cols * 8 + cfg.nf * max_cols * 2 * 2 * (cfg.ns + 64) * 2
+    budget = int(0.85 * (free - scratch))
+    max_cols = int(min(max_cols, 2 * budget // per_point))
+
+    def arrivals(rate, horizon, seed):
+        r = np.random.default_rng(seed)
+        t, out = 0.0, []
+        while True:
+            t += r.exponential(1.0 / rate)
+            if t >= horizon:
+                return out
+            nv = int(r.integers(1, 129))
+            niter = int(r.integers(10, 31))
+            tol = 1e-3 if r.random() < 0.5 else 0.0
+            out.append((t, nv, niter, tol, int(r.integers(0, len(pool)))))
+
+    res = {"workload": f"Poisson redatuming jobs on the {cfg.nr}x{cfg.ns}, nt={cfg.nt}, nfmax={cfg.nf} kernel "
+                       f"(FP16 copy resident, ||R||=0.5), nv ~ U{{1..128}} at z=800 m, niter ~ U{{10..30}}, "
+                       f"half with tol 1e-3; columns of all running jobs share one product per pass",
+           "hbm_budget_gb": budget / 1e9, "max_cols": max_cols}
+    # (i)+(ii): the offered load, fixed horizon, backlog stated
+    srv = mdc.srv_create(lo.h, None, budget, max_cols)
+    arr = arrivals(args.serving_rate, args.serving_horizon, 1)
+    done, backlog, el = serve_loop(mdc, srv, arr, pool, args.serving_horizon, False)
+    mdc.srv_destroy(srv)
+    lat = [j["latency_s"] for j in done]
+    cap = len(done) / el if el > 0 else 0.0
+    res["offered"] = {"rate_per_s": args.serving_rate, "horizon_s": args.serving_horizon, "submitted": len(arr),
+                      "completed": len(done), "backlog": backlog,
+                      "solves_per_s": cap, "virtual_points_per_s": sum(j["nv"] for j in done) / el,
+                      "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+                      "max_final_residual": max([j["final_residual"] for j in done], default=None)}
+    # (iii): 0.7 x the measured capacity, drained
+    rate3 = max(0.7 * cap, 0.05)
+    srv = mdc.srv_create(lo.h, None, budget, max_cols)
+    arr = arrivals(rate3, args.serving_horizon, 2)
+    done, backlog, el = serve_loop(mdc, srv, arr, pool, args.serving_horizon, True)
+    mdc.srv_destroy(srv)
+    lat = [j["latency_s"] for j in done]
+    res["at_0.7_capacity"] = {"rate_per_s": rate3, "submitted": len(arr), "completed": len(done),
+                              "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+                              "wall_s": el}
+    # one job alone through the server: the reference for the FP32 comparison below
+    nv0, niter0 = 64, 20
+    cut0, fd0 = pool[0]
+    out16 = [np.zeros((cfg.nt, cfg.ns, nv0), np.float32) for _ in range(4)]
+    srv = mdc.srv_create(lo.h, None, budget, max_cols)
+    jid = mdc.srv_submit(srv, cut0, fd0, nv0, niter0, 0.0, out16)
+    t0 = time.perf_counter()
+    while mdc.srv_poll(srv, jid)["state"] < mdc.JOB_DONE:
+        mdc.srv_step(srv)
+    t_alone = time.perf_counter() - t0
+    mdc.srv_destroy(srv)
+    lo.close()
+    # (iv): the plain float32 one-job-at-a-time solve (complex64 kernel, no batching)
+    G = sgpu.kernel_on_device(cfg, d)
+    op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    del G
+    torch.cuda.empty_cache()
+    cut_t = torch.from_numpy(np.ascontiguousarray(cut0[:, :nv0])).to(dev)
+    fd_t = torch.from_numpy(np.ascontiguousarray(fd0[:, :, :nv0])).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out32 = op.marchenko(cut_t, fd_t, niter0)
+    t32 = time.perf_counter() - t0
+    f32 = out32["f_minus"].double().cpu().numpy()
+    err = float(np.linalg.norm(out16[0] - f32) / np.linalg.norm(f32))
+    op.close()
+    res["one_job_fp16_alone"] = {"nv": nv0, "niter": niter0, "seconds": t_alone}
+    res["fp32_one_job_at_a_time"] = {"nv": nv0, "niter": niter0, "seconds": t32, "solves_per_s": 1.0 / t32,
+                                     "storage": "c64"}
+    res["rel_l2_fp16_vs_fp32"] = err
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -330,9 +473,7 @@ def run_ours(args):
     ms_e2e = f0.elapsed_time(f1)
 
     if world > 1:
-        t = torch.tensor([ms, ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = float(t[0]), float(t[1])
+        ms, ms_e2e = max_over_ranks([ms, ms_e2e], dev)
     op.close()
     if rank != 0:
         if world > 1:
@@ -364,6 +505,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_redatum:
         result["redatum"] = run_redatum(args, dev)
+    if world == 1 and not args.no_serving:
+        result["serving"] = run_serving(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
     print(json.dumps(result), flush=True)
@@ -384,6 +527,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-redatum", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-config", type=int, default=5)
+    ap.add_argument("--serving-rate", type=float, default=50.0)
+    ap.add_argument("--serving-horizon", type=float, default=20.0)
+    ap.add_argument("--serving-pool", type=int, default=2)
     ap.add_argument("--redatum-solves", type=int, default=3)
     ap.add_argument("--redatum-storage", default="c16f", choices=["c16f", "cbf16"])
     ap.add_argument("--redatum-refine-iters", type=int, default=5)

@@ -213,12 +213,15 @@ enum { MDC_JOB_QUEUED = 0, MDC_JOB_RUNNING = 1, MDC_JOB_DONE = 2, MDC_JOB_FAILED
  * The server owns R's scratch while it exists.  Allocates; blocking. */
 int srv_create(mdc_server_handle* out, mdc_handle R, mdc_handle R_ref, int64_t hbm_budget_bytes,
                int max_cols, int nrefine, int niter_refine, void* stream);
-/* srv_submit -- queue one job: window int32 [ns][nv] and fd_plus float32 [nt][ns][nv] in host
- * memory (copied now); niter LSQR iterations (tol > 0: stop earlier at tol * ||d||).  The four
- * host output buffers [nt][ns][nv] (each may be NULL) are filled when the job completes.
- * MDC_ERR_BUDGET if the job can never fit.  *job_id receives the job's id. */
-int srv_submit(mdc_server_handle s, const int* window_host, const float* fd_plus_host, int nv, int niter,
-               double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+/* srv_submit -- queue one job: window int32 [ns][ld] and fd_plus float32 [nt][ns][ld] in host
+ * memory, of which the first nv columns are the job's (ld >= nv; pinned memory copies fastest).
+ * The buffers are NOT copied at submission: they are read when the job is admitted, so the
+ * caller keeps them unchanged until the job completes.  niter LSQR iterations (tol > 0: stop
+ * earlier at tol * ||d||).  The four host output buffers [nt][ns][nv] (each may be NULL) are
+ * written when the job completes.  MDC_ERR_BUDGET if the job can never fit the budget or the
+ * column capacity.  *job_id receives the job's id. */
+int srv_submit(mdc_server_handle s, const int* window_host, const float* fd_plus_host, int nv, int ld,
+               int niter, double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
                float* g_plus_host, int64_t* job_id);
 /* srv_step -- admit, advance every running job by one iteration, complete finished jobs
  * (their host outputs are written before return).  Blocking.  *completed = jobs completed. */

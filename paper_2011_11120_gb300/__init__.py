@@ -46,7 +46,7 @@ SIGNATURES = {
     "mdc_launch_count": (_i64, [_vp]),
     "mdc_device_status": (_i, [_vp, _vp]),
     "srv_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _i64, _i, _i, _i, _vp]),
-    "srv_submit": (_i, [_vp, _vp, _vp, _i, _i, _d, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
+    "srv_submit": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
     "srv_step": (_i, [_vp, ctypes.POINTER(_i)]),
     "srv_poll": (_i, [_vp, _i64, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d),
                       ctypes.POINTER(_d), ctypes.POINTER(_d)]),
@@ -259,6 +259,8 @@ class MDC:
 
 
 # ------------------------------------------------------------------ serving
+import numpy as np  # noqa: E402
+
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
 
@@ -280,13 +282,17 @@ def srv_create(h, h_ref, hbm_budget_bytes: int, max_cols: int, nrefine: int = 0,
 
 
 def srv_submit(v, window, fd_plus, nv: int, niter: int, tol: float = 0.0, outputs=(None, None, None, None)) -> int:
-    """Queue a job from host numpy arrays (int32 window [ns][nv], float32 fd_plus [nt][ns][nv])."""
-    import numpy as np
-    window = np.ascontiguousarray(window, dtype=np.int32)
-    fd_plus = np.ascontiguousarray(fd_plus, dtype=np.float32)
+    """Queue a job from host numpy arrays: int32 window [ns][ld], float32 fd_plus [nt][ns][ld]
+    (first nv columns used).  The arrays are read at admission: keep them alive and unchanged
+    until the job completes."""
+    if window.dtype != np.int32 or fd_plus.dtype != np.float32:
+        raise ValueError("window must be int32 and fd_plus float32")
+    ld = window.shape[-1]
+    if fd_plus.shape[-1] != ld or nv > ld:
+        raise ValueError("window and fd_plus need the same last dimension >= nv")
     jid = ctypes.c_int64(0)
     o = [_hptr(a) for a in outputs]
-    _check(lib().srv_submit(v, _hptr(window), _hptr(fd_plus), nv, niter, tol, o[0], o[1], o[2], o[3],
+    _check(lib().srv_submit(v, _hptr(window), _hptr(fd_plus), nv, ld, niter, tol, o[0], o[1], o[2], o[3],
                             ctypes.byref(jid)), "srv_submit")
     return jid.value
 

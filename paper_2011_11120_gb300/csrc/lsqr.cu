@@ -527,9 +527,10 @@ struct ServeJob {
     int64_t id = 0;
     int nv = 0, niter = 0;
     double tol = 0.0;
-    std::vector<int> cut_h;
-    std::vector<float> fd_h;
-    float* out[4] = {};          // caller host buffers: f-, f_m+, g-, g+ (nullable)
+    const int* cut_h = nullptr;  // caller host inputs [ns][ld] and [nt][ns][ld] (first nv columns used)
+    const float* fd_h = nullptr;
+    int ld = 0;
+    float* out[4] = {};          // caller host buffers: f-, f_m+, g-, g+ (nullable), [nt][ns][nv]
     int state = JOB_QUEUED, status = MDC_OK;
     Solver* S = nullptr;
     int* cut_d = nullptr;
@@ -589,10 +590,13 @@ int start_job(mdc_server* v, ServeJob* j) {
     cudaError_t e = cudaMallocAsync((void**)&j->cut_d, C * sizeof(int), v->s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&j->fd_d, B * sizeof(float), v->s);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMallocAsync((void**)&j->x[i], B * sizeof(float), v->s);
+    const size_t w = (size_t)j->nv;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(j->cut_d, j->cut_h.data(), C * sizeof(int), cudaMemcpyHostToDevice, v->s);
+        e = cudaMemcpy2DAsync(j->cut_d, w * sizeof(int), j->cut_h, (size_t)j->ld * sizeof(int), w * sizeof(int),
+                              (size_t)p->ns, cudaMemcpyHostToDevice, v->s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(j->fd_d, j->fd_h.data(), B * sizeof(float), cudaMemcpyHostToDevice, v->s);
+        e = cudaMemcpy2DAsync(j->fd_d, w * sizeof(float), j->fd_h, (size_t)j->ld * sizeof(float), w * sizeof(float),
+                              (size_t)p->ns * p->nt, cudaMemcpyHostToDevice, v->s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_cuda_error(e);
@@ -679,22 +683,22 @@ extern "C" int srv_create(mdc_server** out, mdc_handle R, mdc_handle R_ref, int6
     return MDC_OK;
 }
 
-extern "C" int srv_submit(mdc_server* v, const int* window_host, const float* fd_plus_host, int nv, int niter,
-                          double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+extern "C" int srv_submit(mdc_server* v, const int* window_host, const float* fd_plus_host, int nv, int ld,
+                          int niter, double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
                           float* g_plus_host, int64_t* job_id) {
-    if (!v || !window_host || !fd_plus_host || nv < 1 || niter < 1 || !job_id || !std::isfinite(tol))
+    if (!v || !window_host || !fd_plus_host || nv < 1 || ld < nv || niter < 1 || !job_id || !std::isfinite(tol))
         return MDC_ERR_ARG;
     if (2 * nv > v->max_cols) return MDC_ERR_BUDGET;
     if (job_bytes(v->p, nv) > v->budget) return MDC_ERR_BUDGET;
     ServeJob* j = new (std::nothrow) ServeJob();
     if (!j) return MDC_ERR_OOM;
-    const int64_t C = (int64_t)v->p->ns * nv, B = (int64_t)v->p->nt * C;
     j->id = v->next_id++;
     j->nv = nv;
     j->niter = niter;
     j->tol = tol;
-    j->cut_h.assign(window_host, window_host + C);
-    j->fd_h.assign(fd_plus_host, fd_plus_host + B);
+    j->cut_h = window_host;
+    j->fd_h = fd_plus_host;
+    j->ld = ld;
     j->out[0] = f_minus_host;
     j->out[1] = f_mplus_host;
     j->out[2] = g_minus_host;
@@ -801,12 +805,13 @@ extern "C" int srv_step(mdc_server* v, int* completed) {
         }
         if (!fin.empty()) {
             std::vector<std::vector<int>> its(fin.size());
-            std::vector<double> res(fin.size());
+            std::vector<double> res(fin.size()), bad(fin.size());
             for (size_t q = 0; q < fin.size(); ++q) {
                 its[q].resize(fin[q]->S->nsolves);
                 cudaMemcpyAsync(its[q].data(), fin[q]->S->iters, its[q].size() * sizeof(int), cudaMemcpyDeviceToHost,
                                 v->s);
                 cudaMemcpyAsync(&res[q], fin[q]->S->xs + X_FINAL, sizeof(double), cudaMemcpyDeviceToHost, v->s);
+                cudaMemcpyAsync(&bad[q], fin[q]->S->sc + S_STATUS, sizeof(double), cudaMemcpyDeviceToHost, v->s);
             }
             e = cudaStreamSynchronize(v->s);
             if (e != cudaSuccess) {
@@ -820,7 +825,9 @@ extern "C" int srv_step(mdc_server* v, int* completed) {
                 j->iters = tot;
                 j->final_resid = res[q];
                 j->t_done = now_s();
-                j->state = JOB_DONE;
+                // a non-finite alpha or beta retires this job alone: its batch mates' columns never mix with it
+                j->state = (bad[q] != 0.0 || !std::isfinite(res[q])) ? JOB_FAILED : JOB_DONE;
+                if (j->state == JOB_FAILED) j->status = MDC_ERR_NUMERIC;
                 v->used -= j->bytes;
                 v->cols -= 2 * j->nv;
                 free_job_device(v, j);

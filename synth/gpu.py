@@ -53,3 +53,22 @@ def kernel_on_device(cfg: synth.Config, d: synth.Draw = None, device="cuda", out
     if st != 0:
         raise RuntimeError(f"synth_kernel_c64 failed ({st})")
     return out
+
+
+def focusing_inputs_on_device(cfg: synth.Config, points: np.ndarray, device="cuda", margin: int = 4):
+    """Window cut-offs int32 [ns][nv] and direct focusing function float32 [nt][ns][nv] for the
+    given focusing points (z = cfg.z_point), evaluated on the device with the formulas of
+    synth.window_cutoffs and synth.direct_focusing (float64 arithmetic, float32 output)."""
+    xy = torch.from_numpy(synth.grid_xy(cfg.n_side)).to(device)
+    pts = torch.from_numpy(np.asarray(points, np.float64)).to(device)
+    dd = ((xy[:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+    td = torch.sqrt(cfg.z_point * cfg.z_point + dd) / synth.POINT_SPEED            # [ns, nv]
+    cut = (torch.round(td / cfg.dt).to(torch.int64) - margin).to(torch.int32)
+    tau = torch.from_numpy(synth.signed_time_index(cfg.nt).astype(np.float64) * cfg.dt).to(device)
+    fd = torch.empty((cfg.nt, cfg.ns, pts.shape[0]), dtype=torch.float32, device=device)
+    a2 = (np.pi * synth.RICKER_FP) ** 2
+    for t0 in range(0, cfg.nt, 64):
+        arg = tau[t0:t0 + 64, None, None] + td[None]
+        q = a2 * arg * arg
+        fd[t0:t0 + 64] = ((1.0 - 2.0 * q) * torch.exp(-q)).to(torch.float32)
+    return cut, fd

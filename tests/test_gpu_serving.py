@@ -145,3 +145,32 @@ def test_server_admission_by_budget_and_mid_flight_arrivals(small):
     finally:
         m.srv_destroy(srv)
     op.close()
+
+
+def test_server_retires_a_non_finite_job_alone(small):
+    """A job whose data holds NaN fails with MDC_ERR_NUMERIC; its batch mates are unaffected."""
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    jobs = make_jobs(cfg, G, [(2, 8, 0.0), (3, 8, 0.0), (2, 8, 0.0)], seed=5)
+    bad = dict(jobs[1])
+    bad["fd"] = jobs[1]["fd"].copy()
+    bad["fd"][3, 5, 1] = np.nan
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    solo, _, _ = run_server(m, op, None, cfg, [jobs[0]], {0: [0]})
+    srv = m.srv_create(op.h, None, 1 << 34, 64)
+    try:
+        outs = [outputs(cfg, j["nv"]) for j in (jobs[0], bad, jobs[2])]
+        ids = [m.srv_submit(srv, j["cut"], j["fd"], j["nv"], j["niter"], 0.0, o)
+               for j, o in zip((jobs[0], bad, jobs[2]), outs)]
+        for _ in range(30):
+            m.srv_step(srv)
+            if all(m.srv_poll(srv, i)["state"] >= m.JOB_DONE for i in ids):
+                break
+        polls = [m.srv_poll(srv, i) for i in ids]
+        assert polls[1]["state"] == m.JOB_FAILED and polls[1]["status"] == -5
+        assert polls[0]["state"] == m.JOB_DONE and polls[2]["state"] == m.JOB_DONE
+        assert rel(outs[0][0], solo[0][0]) <= 1e-6
+        assert np.isfinite(outs[2][0]).all()
+    finally:
+        m.srv_destroy(srv)
+    op.close()
