@@ -37,7 +37,7 @@ METRIC = "MDC fwd+adj HBM GB/s vs peak; redatum solves/s and p99 at <=1e-3 vs FP
 UNIT = "GB/s"
 
 
-BYTES_PER_COMPLEX = {"c64": 8, "c16f": 4, "cbf16": 4, "ce4m3": 2}
+BYTES_PER_COMPLEX = {"c64": 8, "c16f": 4, "cbf16": 4, "ce4m3": 2, "c32s": 8}
 
 
 def algorithmic_bytes(cfg, nv, storage="c64"):
@@ -222,7 +222,8 @@ def run_redatum(args, dev):
     d = synth.draw(cfg)
     G = sgpu.kernel_on_device(cfg, d)
     lo = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.redatum_storage)
-    ref = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    ref = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.redatum_ref_storage)
+    plain_op = ref if args.redatum_ref_storage == "c64" else mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage="c64")
     del G
     torch.cuda.empty_cache()
     cut = torch.from_numpy(synth.window_cutoffs(cfg, d)).to(dev)
@@ -240,16 +241,18 @@ def run_redatum(args, dev):
         out = solve()
         times.append(time.perf_counter() - t0)
     t0 = time.perf_counter()
-    plain = ref.marchenko(cut, fd, niter)              # float32 operator, one job, no refinement
+    plain = plain_op.marchenko(cut, fd, niter)         # complex64 SIMT operator, one job, no refinement
     t_plain = time.perf_counter() - t0
     fm = out["f_minus"].double()
     err = float((fm - plain["f_minus"].double()).norm() / plain["f_minus"].double().norm())
     lo.close()
     ref.close()
+    plain_op.close()
     med = statistics.median(times)
     return {"workload": f"Marchenko LSQR, nr=ns={cfg.nr} (41x41, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
                         f"nv={cfg.nv} (16x16 focusing points, z=800 m), ||R||=0.5, {niter} LSQR iterations "
-                        f"on a {args.redatum_storage} kernel + {nref} float32 refinement step of {nin} iterations",
+                        f"on a {args.redatum_storage} kernel + {nref} float32 refinement step of {nin} iterations "
+                        f"({args.redatum_ref_storage} reference kernel)",
             "solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "solves_timed": len(times),
             "p50_ms": 1e3 * med, "p99_ms": 1e3 * max(times),
             "iterations": out["iters"], "final_residual": out["final_residual"],
@@ -523,7 +526,7 @@ def main():
     ap.add_argument("--nv", type=int, default=1)
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--nf", type=int, default=0, help="override nfmax (smaller profiling case)")
-    ap.add_argument("--storage", default="c64", choices=["c64", "c16f", "cbf16", "ce4m3"])
+    ap.add_argument("--storage", default="c64", choices=["c64", "c16f", "cbf16", "ce4m3", "c32s"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-redatum", action="store_true")
@@ -535,6 +538,7 @@ def main():
     ap.add_argument("--redatum-solves", type=int, default=3)
     ap.add_argument("--redatum-storage", default="c16f", choices=["c16f", "cbf16"])
     ap.add_argument("--redatum-refine-iters", type=int, default=5)
+    ap.add_argument("--redatum-ref-storage", default="c32s", choices=["c64", "c32s"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -48,7 +48,10 @@ typedef enum {
     MDC_C64 = 0,    /* complex float32 (the paper's complex64 kernel, Table 1) */
     MDC_C16F = 1,   /* complex float16, one float32 scale per (frequency, row) */
     MDC_CBF16 = 2,  /* complex bfloat16, one float32 scale per (frequency, row) */
-    MDC_CE4M3 = 3   /* complex FP8 E4M3, one float32 scale per (frequency, row) */
+    MDC_CE4M3 = 3,  /* complex FP8 E4M3, one float32 scale per (frequency, row) */
+    MDC_C32S = 4    /* complex as an FP16 pair hi + lo per component (about 22 significant bits,
+                       float32-level accuracy), one float32 scale per (frequency, row); 8 bytes per
+                       value like complex64, but products run on FP16 tensor cores */
 } mdc_storage;
 
 /* mdc_forward / mdc_adjoint flags */
@@ -170,16 +173,17 @@ int marchenko_lsqr(mdc_handle R, const int* window, const float* fd_plus, int nv
  * and float32-operator refinement (iterative refinement of the least-squares solution).
  *
  *   R        handle with any storage (typically MDC_C16F/MDC_CBF16) used inside LSQR.
- *   R_ref    complex64 handle (MDC_C64) of the same kernel, same shape: it computes the data
- *            vector d, the residuals d - M x, the Green's functions and the final check.
+ *   R_ref    float32-accurate handle (MDC_C64, or MDC_C32S whose products run on tensor cores)
+ *            of the same kernel and shape: it computes the data vector d, the residuals
+ *            d - M x, the Green's functions and the final check.
  *   niter    LSQR iterations of the first solve (from x = 0).
  *   nrefine  outer refinement steps: each recomputes r = d - M_ref x in float32 and runs
  *            niter_refine further LSQR iterations on R, adding the correction to x.
  *   resid    host double[(niter + 1) + nrefine * (niter_refine + 1)] or NULL: for each solve,
  *            its right-hand-side norm then its residual estimates (-1 where not reached).
  *   final_residual  host double or NULL: ||d - M_ref x|| / ||d||, accumulated in float64.
- * Other arguments as marchenko_lsqr.  Blocking.  MDC_ERR_ARG if R_ref is not MDC_C64 or the
- * shapes differ.
+ * Other arguments as marchenko_lsqr.  Blocking.  MDC_ERR_ARG if R_ref is neither MDC_C64 nor
+ * MDC_C32S or the shapes differ.
  */
 int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int* window, const float* fd_plus,
                            int nv, int niter, int nrefine, int niter_refine, double tol,
@@ -206,8 +210,8 @@ typedef struct mdc_server* mdc_server_handle;
 
 enum { MDC_JOB_QUEUED = 0, MDC_JOB_RUNNING = 1, MDC_JOB_DONE = 2, MDC_JOB_FAILED = 3 };
 
-/* srv_create -- R: kernel used inside LSQR (nr == ns); R_ref: complex64 reference of the same
- * kernel or NULL (then R serves for data and Green's functions, and nrefine must be 0).
+/* srv_create -- R: kernel used inside LSQR (nr == ns); R_ref: float32-accurate reference of the
+ * same kernel (MDC_C64 or MDC_C32S) or NULL (then R serves for data and Green's functions, and nrefine must be 0).
  * hbm_budget_bytes bounds the device memory of running jobs' state (about 48 bytes per
  * time sample per column); max_cols bounds the stacked columns (2 per virtual point).
  * The server owns R's scratch while it exists.  Allocates; blocking. */
@@ -259,6 +263,13 @@ int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage);
  * kernels the handle has launched since creation (timing on or off).
  */
 int mdc_timing(mdc_handle h, int enable);
+/* mdc_set_option -- MDC_OPT_GRAPHS (value 1/0): when on, a marchenko_lsqr or
+ * marchenko_lsqr_refined call whose arguments (sizes, iteration counts, tolerance and every
+ * pointer) repeat an earlier call on this handle replays that call's CUDA graph: the whole solve
+ * (data vector, all LSQR iterations, refinement, Green's functions) is captured on first use with
+ * a workspace the handle keeps (up to 4 cached solves; turning the option off frees them). */
+#define MDC_OPT_GRAPHS 1
+int mdc_set_option(mdc_handle h, int option, int value);
 /* mdc_device_status -- synchronise `stream` and report MDC_ERR_TIMEOUT if a kernel of this
  * handle gave up a bounded device-side wait since the last check (the flag is then cleared). */
 int mdc_device_status(mdc_handle h, void* stream);

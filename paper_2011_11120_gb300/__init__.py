@@ -18,8 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmdc_gb300.so")
 
 MDC_OK = 0
-MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3 = 0, 1, 2, 3
-STORAGE = {"c64": MDC_C64, "c16f": MDC_C16F, "cbf16": MDC_CBF16, "ce4m3": MDC_CE4M3}
+MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3, MDC_C32S = 0, 1, 2, 3, 4
+STORAGE = {"c64": MDC_C64, "c16f": MDC_C16F, "cbf16": MDC_CBF16, "ce4m3": MDC_CE4M3, "c32s": MDC_C32S}
 MDC_CONJ_KERNEL = 0x1
 KC_RFFT, KC_PRODUCT_FWD, KC_PRODUCT_ADJ, KC_IRFFT, KC_SOLVER = range(5)
 KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj": KC_PRODUCT_ADJ,
@@ -45,6 +45,7 @@ SIGNATURES = {
     "mdc_timing_read": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64)]),
     "mdc_launch_count": (_i64, [_vp]),
     "mdc_device_status": (_i, [_vp, _vp]),
+    "mdc_set_option": (_i, [_vp, _i, _i]),
     "srv_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _i64, _i, _i, _i, _vp]),
     "srv_submit": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
     "srv_step": (_i, [_vp, ctypes.POINTER(_i)]),
@@ -194,6 +195,13 @@ def mdc_timing_read(h, kernel_class) -> tuple:
 
 def mdc_launch_count(h) -> int:
     return int(lib().mdc_launch_count(h))
+
+
+MDC_OPT_GRAPHS = 1
+
+
+def mdc_set_option(h, option: int, value: int) -> None:
+    _check(lib().mdc_set_option(h, option, value), "mdc_set_option")
 
 
 def mdc_device_status(h, stream=None) -> None:

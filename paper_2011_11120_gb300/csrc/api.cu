@@ -52,6 +52,7 @@ extern "C" int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage) {
         case MDC_C16F:
         case MDC_CBF16: return n * 4 + (int64_t)nfmax * nr * 4;
         case MDC_CE4M3: return n * 2 + (int64_t)nfmax * nr * 4;
+        case MDC_C32S: return n * 8 + (int64_t)nfmax * nr * 4;
         default: return -1;
     }
 }
@@ -74,6 +75,8 @@ extern "C" int mdc_last_cuda_error(void) { return g_last_cuda_error; }
 
 static void free_plan(mdc_plan* p) {
     if (!p) return;
+    if (p->graph_free)
+        for (void* g : p->graph_cache) p->graph_free(g);
     cudaFree(p->G);
     cudaFree(p->gscale);
     cudaFree(p->tw);
@@ -95,7 +98,7 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
     *out = nullptr;
     if (!G || nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
     if (!(dt > 0.0) || !(dr > 0.0) || !std::isfinite(dt) || !std::isfinite(dr)) return MDC_ERR_ARG;
-    if (storage < MDC_C64 || storage > MDC_CE4M3) return MDC_ERR_ARG;
+    if (storage < MDC_C64 || storage > MDC_C32S) return MDC_ERR_ARG;
     if ((int64_t)nr * nfmax > (int64_t)1 << 31) return MDC_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     mdc_plan* p = new (std::nothrow) mdc_plan();
@@ -161,10 +164,10 @@ int mdc::ensure_scratch(mdc_plan* p, int ncols) {
         p->nv_cap = ncols;
     }
     // tensor-core operand for the FP16/BF16 copies (used from 8 columns on)
-    if ((p->storage == MDC_C16F || p->storage == MDC_CBF16) && ncols > p->tc_cap) {
+    if (storage_16bit(p->storage) && ncols > p->tc_cap) {
         void* b = nullptr;
         float* sg = nullptr;
-        cudaError_t e = cudaMalloc(&b, tc_scratch_elems(p, ncols) * 2);
+        cudaError_t e = cudaMalloc(&b, tc_scratch_elems(p, ncols) * 2 * (p->storage == MDC_C32S ? 2 : 1));
         if (e == cudaSuccess) e = cudaMalloc(&sg, (size_t)p->nf * ncols * sizeof(float));
         if (e != cudaSuccess) {
             cudaFree(b);
@@ -267,6 +270,22 @@ extern "C" int mdc_timing_read(mdc_handle h, int cls, double* total_ms, int64_t*
 }
 
 extern "C" int64_t mdc_launch_count(mdc_handle h) { return h ? h->launch_count : -1; }
+
+extern "C" int mdc_set_option(mdc_handle h, int option, int value) {
+    if (!h) return MDC_ERR_ARG;
+    switch (option) {
+        case MDC_OPT_GRAPHS:
+            h->graphs = value != 0;
+            if (!h->graphs && h->graph_free) {
+                cudaDeviceSynchronize();
+                for (void* g : h->graph_cache) h->graph_free(g);
+                h->graph_cache.clear();
+            }
+            return MDC_OK;
+        default:
+            return MDC_ERR_ARG;
+    }
+}
 
 extern "C" int mdc_device_status(mdc_handle h, void* stream) {
     if (!h) return MDC_ERR_ARG;

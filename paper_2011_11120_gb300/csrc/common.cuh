@@ -68,6 +68,9 @@ struct mdc_plan {
     int tc_cap = 0;
     int* err_flag = nullptr;    // device int: non-zero after a bounded device wait gave up
     bool force_tc = false;      // FP16/BF16: tensor-core products for every column count
+    bool graphs = false;        // capture repeated solves into CUDA graphs (mdc_set_option)
+    std::vector<void*> graph_cache;   // solver workspaces with their instantiated graphs
+    void (*graph_free)(void*) = nullptr;
     int64_t launch_count = 0;
     mdc::TimingState timing;
 };
@@ -132,9 +135,13 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol);
 // Quantise a complex64 kernel [nf][nr][ns] into the plan's reduced-storage copy and row scales.
 void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s);
 
-// Bytes of one stored complex value.
+// Bytes of one stored complex value (MDC_C32S: 4 in each of its two planes).
 inline int storage_bytes(int storage) {
-    return storage == MDC_C64 ? 8 : (storage == MDC_CE4M3 ? 2 : 4);
+    return (storage == MDC_C64 || storage == MDC_C32S) ? 8 : (storage == MDC_CE4M3 ? 2 : 4);
+}
+// Storage held in 16-bit halves that the tensor-core path can consume.
+inline bool storage_16bit(int storage) {
+    return storage == MDC_C16F || storage == MDC_CBF16 || storage == MDC_C32S;
 }
 
 void set_cuda_error(cudaError_t e);

@@ -206,8 +206,11 @@ template <int N1, int N2> struct FourStep {
     static constexpr int P0 = 8192 / NT;
     static constexpr int P = P0 > 32 ? 32 : (P0 < 8 ? 8 : P0);     // complex sequences per CTA
     static constexpr int CT = 2 * P;                                  // real columns per CTA
-    static constexpr int RS = P + 1;
-    static constexpr int BP = ((8 - (N2 * RS) % 16) % 16 + 16) % 16;
+    // Rows of P complex values, unpadded, plus BP slots after every block of N2 rows: with P = 8
+    // two consecutive rows (or blocks, in pass B) then fill all 16 bank pairs, and rows stay
+    // 16-byte aligned for vector accesses.
+    static constexpr int RS = P;
+    static constexpr int BP = P == 8 ? 8 : 0;
     static constexpr int ZSIZE = NT * RS + N1 * BP;                  // float2 elements
     static constexpr size_t smem = (size_t)(NT / 2 + ZSIZE) * sizeof(float2) + FFT_THREADS * 32;
     __device__ static __forceinline__ int zi(int t, int j) { return t * RS + (t / N2) * BP + j; }
@@ -288,11 +291,17 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 const int q = threadIdx.x + (b0 + u) * FFT_THREADS;
-                const int t = q / Q, cl = 4 * (q % Q);
-                put(t, cl, v[u].x);
-                put(t, cl + 1, v[u].y);
-                put(t, cl + 2, v[u].z);
-                put(t, cl + 3, v[u].w);
+                const int t = q / Q, cl = 4 * (q % Q), c = c0 + cl;
+                float4 w = v[u];
+                if (a.cut) {
+                    const int tau = t < (NT >> 1) ? t : NT - t;
+                    if (tau >= a.cut[c]) w.x = 0.f;
+                    if (tau >= a.cut[c + 1]) w.y = 0.f;
+                    if (tau >= a.cut[c + 2]) w.z = 0.f;
+                    if (tau >= a.cut[c + 3]) w.w = 0.f;
+                }
+                w.x *= sc; w.y *= sc; w.z *= sc; w.w *= sc;
+                *reinterpret_cast<float4*>(z + F::zi(t, cl >> 1)) = w;
             }
         }
     } else {
@@ -322,11 +331,24 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
     }
     __syncthreads();
     four_step<N1, N2>(z, tw);
+    // Bins k < nf sit in rows rho = k1 * N2 + k2 (k = k1 + N1 * k2): the first ceil((nf - k1) / N1)
+    // rows of each block k1.  Walk them in storage order so a warp reads consecutive rows.
+    const int qn = a.nf / N1, rn = a.nf % N1;
     for (int idx = threadIdx.x; idx < a.nf * CT; idx += FFT_THREADS) {
-        const int k = idx / CT, cl = idx % CT, c = c0 + cl;
+        const int ir = idx / CT, cl = idx % CT, c = c0 + cl;
         if (c >= a.C) continue;
+        int k1, k2;
+        if (ir < rn * (qn + 1)) {
+            k1 = ir / (qn + 1);
+            k2 = ir % (qn + 1);
+        } else {
+            const int i2 = ir - rn * (qn + 1);
+            k1 = rn + i2 / qn;
+            k2 = i2 % qn;
+        }
+        const int k = k1 + N1 * k2;
         const int j = cl >> 1;
-        const float2 Z = z[F::zi(out_row<N1, N2>(k), j)];
+        const float2 Z = z[F::zi(k1 * N2 + k2, j)];
         const float2 Zm = z[F::zi(out_row<N1, N2>((NT - k) & (NT - 1)), j)];
         float2 r;
         if ((cl & 1) == 0) r = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
@@ -416,18 +438,21 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
             for (int i = 0; i < 4; ++i) cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
 #pragma unroll 1
             for (int b0 = 0; b0 < PER; b0 += B) {
+                // storage row rho holds time sample t = (rho % N2) * N1 + rho / N2
                 float4 bv[B], pv[B];
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
-                    const size_t o = (size_t)(t0 + (b0 + u) * TS) * a.C + cq;
+                    const int rho = t0 + (b0 + u) * TS;
+                    const size_t o = (size_t)((rho % N2) * N1 + rho / N2) * a.C + cq;
                     bv[u] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
                     pv[u] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
-                    const int t = t0 + (b0 + u) * TS;
-                    const int row = out_row<N1, N2>(t);
-                    const float2 z0 = z[F::zi(row, 2 * q)], z1 = z[F::zi(row, 2 * q + 1)];
+                    const int rho = t0 + (b0 + u) * TS;
+                    const int t = (rho % N2) * N1 + rho / N2;
+                    const float4 zz = *reinterpret_cast<const float4*>(z + F::zi(rho, 2 * q));
+                    const float2 z0 = make_float2(zz.x, zz.y), z1 = make_float2(zz.z, zz.w);
                     const int tau = t < (NT >> 1) ? t : NT - t;
                     float v[4] = {z0.x, z0.y, z1.x, z1.y};
                     const float bb[4] = {bv[u].x, bv[u].y, bv[u].z, bv[u].w};
@@ -466,15 +491,17 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
             float bv[B], pv[B];
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int t = t0 + (b0 + u) * TS;
+                const int rho = t0 + (b0 + u) * TS;
+                const int t = (rho % N2) * N1 + rho / N2;
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                 bv[u] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
                 pv[u] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int t = t0 + (b0 + u) * TS;
-                const float2 zz = z[F::zi(out_row<N1, N2>(t), cl >> 1)];
+                const int rho = t0 + (b0 + u) * TS;
+                const int t = (rho % N2) * N1 + rho / N2;
+                const float2 zz = z[F::zi(rho, cl >> 1)];
                 float val = ((cl & 1) ? zz.y : zz.x) * a.scale;
                 const int tau = t < (NT >> 1) ? t : NT - t;
                 if (tau >= cut) val = 0.f;

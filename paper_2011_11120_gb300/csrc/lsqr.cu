@@ -259,12 +259,16 @@ struct Solver {
             set_cuda_error(e);
             return MDC_ERR_OOM;
         }
+        reset();
+        return MDC_OK;
+    }
+    // Per-solve initial state (stream-ordered; part of a captured graph when graphs are on).
+    void reset() {
         cudaMemsetAsync(xs, 0, X_COUNT * sizeof(double), s);
         cudaMemsetAsync(act, 0, nact * sizeof(int), s);
         cudaMemsetAsync(iters, 0, nsolves * sizeof(int), s);
         LaunchScope ls(p, s, MDC_KC_SOLVER);
         fill_d<<<1, 256, 0, s>>>(resid, nresid, -1.0);
-        return MDC_OK;
     }
 
     void rfft(mdc_plan* q, const float* x, const float* x2, const int* cutp, Coef scale, int conj, int voff,
@@ -407,15 +411,49 @@ struct Solver {
     }
 };
 
-}  // namespace
+struct GraphEntry {
+    // key
+    mdc_plan* pr;
+    const int* cut;
+    const float* fd;
+    float* out[4];
+    int nv, niter, nref, niter_ref;
+    double tol;
+    bool want_final;
+    // value
+    Solver* S = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
-// Solve Eq. 5 with LSQR on kernel p; with a reference kernel pr != p, refine: each outer step
-// recomputes u-hat = d - M_pr x in float32 and runs niter_ref further LSQR iterations on p
-// from the current x (the correction accumulates into x).
-int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, int nv, int niter, int nref,
-                  int niter_ref, double tol, float* fm, float* fmp, float* gm, float* gp, double* resid_h,
-                  double* final_h, int* iters_h, cudaStream_t s) {
-    Solver S;
+void free_graph_entry(void* q) {
+    GraphEntry* g = static_cast<GraphEntry*>(q);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    delete g->S;
+    delete g;
+}
+
+// The device work of one solve: data vector, LSQR (and refinement solves), residual check, Eq. 6.
+void solve_body(Solver& S, const float* fd, int niter, int nref, int niter_ref, double tol, float* fm, float* fmp,
+                float* gm, float* gp, bool want_final) {
+    S.data_pass(fd);
+    S.lsqr(fm, fmp, niter, tol, true, S.act, S.resid, S.iters);
+    int aoff = niter + 2, roff = niter + 1;
+    for (int o = 0; o < nref; ++o) {
+        S.residual_pass(fm, fmp);
+        S.lsqr(fm, fmp, niter_ref, tol, false, S.act + aoff, S.resid + roff, S.iters + 1 + o);
+        aoff += niter_ref + 2;
+        roff += niter_ref + 1;
+    }
+    if (want_final) {
+        S.residual_pass(fm, fmp);
+        LaunchScope ls(S.p, S.s, MDC_KC_SOLVER);
+        norm_ratio<<<1, RED_THREADS, 0, S.s>>>(S.csU, 2 * S.C, S.xs + X_DNORM, S.xs + X_FINAL);
+    }
+    if (gm || gp) S.greens(fd, fm, fmp, gm, gp);
+}
+
+void init_solver(Solver& S, mdc_plan* p, mdc_plan* pr, const int* cut, int nv, int niter, int nref, int niter_ref,
+                 cudaStream_t s) {
     S.p = p;
     S.pr = pr;
     S.nv = nv;
@@ -427,42 +465,88 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
     S.nsolves = 1 + nref;
     S.nresid = (niter + 1) + nref * (niter_ref + 1);
     S.nact = (niter + 2) + nref * (niter_ref + 2);
+}
+
+}  // namespace
+
+// Solve Eq. 5 with LSQR on kernel p; with a reference kernel pr != p, refine: each outer step
+// recomputes u-hat = d - M_pr x in float32 and runs niter_ref further LSQR iterations on p
+// from the current x (the correction accumulates into x).
+int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, int nv, int niter, int nref,
+                  int niter_ref, double tol, float* fm, float* fmp, float* gm, float* gp, double* resid_h,
+                  double* final_h, int* iters_h, cudaStream_t s) {
     int st = ensure_scratch(p, 2 * nv);
     if (st == MDC_OK && pr != p) st = ensure_scratch(pr, 2 * nv);
     if (st != MDC_OK) return st;
-    const bool refine = nref > 0;
-    st = S.alloc(refine || final_h != nullptr);
-    if (st != MDC_OK) return st;
-
-    S.data_pass(fd);
-    S.lsqr(fm, fmp, niter, tol, true, S.act, S.resid, S.iters);
-    int aoff = niter + 2, roff = niter + 1;
-    for (int o = 0; o < nref; ++o) {
-        S.residual_pass(fm, fmp);
-        S.lsqr(fm, fmp, niter_ref, tol, false, S.act + aoff, S.resid + roff, S.iters + 1 + o);
-        aoff += niter_ref + 2;
-        roff += niter_ref + 1;
+    const bool keep_data = nref > 0 || final_h != nullptr;
+    Solver local;
+    Solver* S = &local;
+    GraphEntry* ge = nullptr;
+    if (p->graphs) {
+        for (void* q : p->graph_cache) {
+            GraphEntry* g = static_cast<GraphEntry*>(q);
+            if (g->pr == pr && g->cut == cut && g->fd == fd && g->out[0] == fm && g->out[1] == fmp && g->out[2] == gm &&
+                g->out[3] == gp && g->nv == nv && g->niter == niter && g->nref == nref && g->niter_ref == niter_ref &&
+                g->tol == tol && g->want_final == (final_h != nullptr) && g->S->s == s) {
+                ge = g;
+                break;
+            }
+        }
+        if (!ge) {
+            ge = new GraphEntry{pr, cut, fd, {fm, fmp, gm, gp}, nv, niter, nref, niter_ref, tol, final_h != nullptr};
+            ge->S = new Solver();
+            init_solver(*ge->S, p, pr, cut, nv, niter, nref, niter_ref, s);
+            st = ge->S->alloc(keep_data);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = st == MDC_OK ? cudaStreamSynchronize(s) : cudaErrorMemoryAllocation;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                ge->S->reset();
+                solve_body(*ge->S, fd, niter, nref, niter_ref, tol, fm, fmp, gm, gp, final_h != nullptr);
+                e = cudaStreamEndCapture(s, &graph);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge->exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess || st != MDC_OK) {
+                cudaGetLastError();
+                set_cuda_error(e);
+                free_graph_entry(ge);
+                return st != MDC_OK ? st : MDC_ERR_CUDA;
+            }
+            p->graph_free = free_graph_entry;
+            if (p->graph_cache.size() >= 4) {
+                cudaStreamSynchronize(s);
+                free_graph_entry(p->graph_cache.front());
+                p->graph_cache.erase(p->graph_cache.begin());
+            }
+            p->graph_cache.push_back(ge);
+        }
+        S = ge->S;
+        cudaError_t e = cudaGraphLaunch(ge->exec, s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            return MDC_ERR_CUDA;
+        }
+    } else {
+        init_solver(local, p, pr, cut, nv, niter, nref, niter_ref, s);
+        st = local.alloc(keep_data);
+        if (st != MDC_OK) return st;
+        solve_body(local, fd, niter, nref, niter_ref, tol, fm, fmp, gm, gp, final_h != nullptr);
     }
-    if (final_h) {
-        S.residual_pass(fm, fmp);
-        LaunchScope ls(p, s, MDC_KC_SOLVER);
-        norm_ratio<<<1, RED_THREADS, 0, s>>>(S.csU, 2 * S.C, S.xs + X_DNORM, S.xs + X_FINAL);
-    }
-    if (gm || gp) S.greens(fd, fm, fmp, gm, gp);
 
-    std::vector<double> sch(S_COUNT), rh(S.nresid), xh(X_COUNT);
-    std::vector<int> ih(S.nsolves);
-    cudaError_t e = cudaMemcpyAsync(sch.data(), S.sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rh.data(), S.resid, S.nresid * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(xh.data(), S.xs, X_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ih.data(), S.iters, S.nsolves * sizeof(int), cudaMemcpyDeviceToHost, s);
+    std::vector<double> sch(S_COUNT), rh(S->nresid), xh(X_COUNT);
+    std::vector<int> ih(S->nsolves);
+    cudaError_t e = cudaMemcpyAsync(sch.data(), S->sc, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rh.data(), S->resid, S->nresid * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xh.data(), S->xs, X_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ih.data(), S->iters, S->nsolves * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_cuda_error(e);
         return MDC_ERR_CUDA;
     }
-    if (resid_h) for (int i = 0; i < S.nresid; ++i) resid_h[i] = rh[i];
+    if (resid_h) for (int i = 0; i < S->nresid; ++i) resid_h[i] = rh[i];
     if (final_h) *final_h = xh[X_FINAL];
     if (iters_h) {
         int tot = 0;
@@ -494,7 +578,7 @@ extern "C" int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int*
     if (!R || !R_ref || !window || !fd_plus || !f_minus || !f_mplus || nv < 1 || niter < 1) return MDC_ERR_ARG;
     if (nrefine < 0 || (nrefine > 0 && niter_refine < 1)) return MDC_ERR_ARG;
     if (R->nr != R->ns || R_ref->nr != R->nr || R_ref->ns != R->ns || R_ref->nt != R->nt ||
-        R_ref->nf != R->nf || R_ref->storage != MDC_C64)
+        R_ref->nf != R->nf || (R_ref->storage != MDC_C64 && R_ref->storage != MDC_C32S))
         return MDC_ERR_ARG;
     if (!std::isfinite(tol)) return MDC_ERR_ARG;
     return mdc::run_marchenko(R, R_ref, window, fd_plus, nv, niter, nrefine, niter_refine, tol, f_minus, f_mplus,
@@ -657,8 +741,8 @@ extern "C" int srv_create(mdc_server** out, mdc_handle R, mdc_handle R_ref, int6
     if (!out) return MDC_ERR_ARG;
     *out = nullptr;
     if (!R || hbm_budget_bytes <= 0 || max_cols < 2 || R->nr != R->ns || nrefine < 0) return MDC_ERR_ARG;
-    if (R_ref && (R_ref->storage != MDC_C64 || R_ref->nr != R->nr || R_ref->ns != R->ns || R_ref->nt != R->nt ||
-                  R_ref->nf != R->nf))
+    if (R_ref && ((R_ref->storage != MDC_C64 && R_ref->storage != MDC_C32S) || R_ref->nr != R->nr ||
+                  R_ref->ns != R->ns || R_ref->nt != R->nt || R_ref->nf != R->nf))
         return MDC_ERR_ARG;
     if (nrefine > 0 && (!R_ref || niter_refine < 1)) return MDC_ERR_ARG;
     mdc_server* v = new (std::nothrow) mdc_server();

@@ -31,6 +31,7 @@ template <> struct Fmt<MDC_C64> { static constexpr int CPV = 2; };
 template <> struct Fmt<MDC_C16F> { static constexpr int CPV = 4; };
 template <> struct Fmt<MDC_CBF16> { static constexpr int CPV = 4; };
 template <> struct Fmt<MDC_CE4M3> { static constexpr int CPV = 8; };
+template <> struct Fmt<MDC_C32S> { static constexpr int CPV = 4; };   // per plane (hi, lo)
 
 __device__ __forceinline__ float2 dec_h2(unsigned w) {
     __half2 h = *reinterpret_cast<__half2*>(&w);
@@ -46,12 +47,13 @@ __device__ __forceinline__ float2 dec_e4m3x2(unsigned short w) {
 }
 
 // Decode one 16-byte vector into CPV complex values (in storage units; row scale applied elsewhere).
+// MDC_C32S decodes each plane like MDC_C16F; the caller adds the lo plane (decode2).
 template <int FMT>
 __device__ __forceinline__ void decode(const uint4& v, float2* c) {
     if constexpr (FMT == MDC_C64) {
         c[0] = make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
         c[1] = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
-    } else if constexpr (FMT == MDC_C16F) {
+    } else if constexpr (FMT == MDC_C16F || FMT == MDC_C32S) {
         c[0] = dec_h2(v.x); c[1] = dec_h2(v.y); c[2] = dec_h2(v.z); c[3] = dec_h2(v.w);
     } else if constexpr (FMT == MDC_CBF16) {
         c[0] = dec_b2(v.x); c[1] = dec_b2(v.y); c[2] = dec_b2(v.z); c[3] = dec_b2(v.w);
@@ -66,6 +68,18 @@ __device__ __forceinline__ void decode(const uint4& v, float2* c) {
 }
 
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
+
+// Load and decode the vector at g[i]; for the split format add its lo plane at g[i + lo].
+template <int FMT>
+__device__ __forceinline__ void load_decode(const uint4* g, size_t i, int64_t lo, float2* c) {
+    decode<FMT>(ld_stream(g + i), c);
+    if constexpr (FMT == MDC_C32S) {
+        float2 l[4];
+        decode<FMT>(ld_stream(g + i + lo), l);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = cadd(c[j], l[j]);
+    }
+}
 
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.x = fmaf(a.x, b.x, acc.x);
@@ -222,7 +236,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ X, int ldi, int voff_i,
-    float2* __restrict__ Y, int ldo, int voff_o, const int* active) {
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo) {
     constexpr int CPV = Fmt<FMT>::CPV;
     if (active && *active == 0) return;
     extern __shared__ __align__(16) float2 xs[];
@@ -245,22 +259,20 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
         for (int v = 0; v < NVC; ++v) acc[v] = make_float2(0.f, 0.f);
         int i = lane;
         for (; i + 96 < nvec; i += 128) {
-            uint4 gv[4];
+            float2 c4[4][CPV];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) gv[u] = ld_stream(g + i + 32 * u);
+            for (int u = 0; u < 4; ++u) load_decode<FMT>(g, i + 32 * u, lo, c4[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                float2 c[CPV];
-                decode<FMT>(gv[u], c);
 #pragma unroll
                 for (int j = 0; j < CPV; ++j)
 #pragma unroll
-                    for (int v = 0; v < NVC; ++v) cfma(acc[v], c[j], xs[(j * nvec + i + 32 * u) * NVC + v]);
+                    for (int v = 0; v < NVC; ++v) cfma(acc[v], c4[u][j], xs[(j * nvec + i + 32 * u) * NVC + v]);
             }
         }
         for (; i < nvec; i += 32) {
             float2 c[CPV];
-            decode<FMT>(ld_stream(g + i), c);
+            load_decode<FMT>(g, i, lo, c);
 #pragma unroll
             for (int j = 0; j < CPV; ++j)
 #pragma unroll
@@ -289,7 +301,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ Yin, int ldi, int voff_i,
-    float2* __restrict__ Xout, int ldo, int voff_o, const int* active) {
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo) {
     constexpr int CPV = Fmt<FMT>::CPV;
     constexpr int TILE = 32 * CPV;
     constexpr int W = GEMV_THREADS / 32;
@@ -321,24 +333,22 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     if (live) {
         int r = warp;
         for (; r + 3 * W < nr; r += 4 * W) {
-            uint4 gv[4];
+            float2 c4[4][CPV];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) gv[u] = ld_stream(g + (size_t)(r + u * W) * nvec);
+            for (int u = 0; u < 4; ++u) load_decode<FMT>(g, (size_t)(r + u * W) * nvec, lo, c4[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                float2 c[CPV];
-                decode<FMT>(gv[u], c);
 #pragma unroll
                 for (int v = 0; v < NVC; ++v) {
                     const float2 y = ys[(r + u * W) * NVC + v];
 #pragma unroll
-                    for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c[j], y);
+                    for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c4[u][j], y);
                 }
             }
         }
         for (; r < nr; r += W) {
             float2 c[CPV];
-            decode<FMT>(ld_stream(g + (size_t)r * nvec), c);
+            load_decode<FMT>(g, (size_t)r * nvec, lo, c);
 #pragma unroll
             for (int v = 0; v < NVC; ++v) {
                 const float2 y = ys[r * NVC + v];
@@ -372,18 +382,24 @@ template <> struct Bytes<MDC_C64> { static constexpr int v = 8; };
 template <> struct Bytes<MDC_C16F> { static constexpr int v = 4; };
 template <> struct Bytes<MDC_CBF16> { static constexpr int v = 4; };
 template <> struct Bytes<MDC_CE4M3> { static constexpr int v = 2; };
+template <> struct Bytes<MDC_C32S> { static constexpr int v = 4; };   // per plane
 
 // Two consecutive complex values starting at (even) element e of a kernel row.
 template <int FMT>
-__device__ __forceinline__ void load2(const unsigned char* row, int e, float2& c0, float2& c1) {
+__device__ __forceinline__ void load2(const unsigned char* row, int e, float2& c0, float2& c1, size_t lo = 0) {
     if constexpr (FMT == MDC_C64) {
         const float4 v = *reinterpret_cast<const float4*>(row + (size_t)e * 8);
         c0 = make_float2(v.x, v.y);
         c1 = make_float2(v.z, v.w);
-    } else if constexpr (FMT == MDC_C16F || FMT == MDC_CBF16) {
+    } else if constexpr (FMT == MDC_C16F || FMT == MDC_CBF16 || FMT == MDC_C32S) {
         const uint2 v = *reinterpret_cast<const uint2*>(row + (size_t)e * 4);
-        if constexpr (FMT == MDC_C16F) { c0 = dec_h2(v.x); c1 = dec_h2(v.y); }
-        else { c0 = dec_b2(v.x); c1 = dec_b2(v.y); }
+        if constexpr (FMT == MDC_CBF16) { c0 = dec_b2(v.x); c1 = dec_b2(v.y); }
+        else { c0 = dec_h2(v.x); c1 = dec_h2(v.y); }
+        if constexpr (FMT == MDC_C32S) {
+            const uint2 l = *reinterpret_cast<const uint2*>(row + lo + (size_t)e * 4);
+            c0 = cadd(c0, dec_h2(l.x));
+            c1 = cadd(c1, dec_h2(l.y));
+        }
     } else {
         const unsigned v = *reinterpret_cast<const unsigned*>(row + (size_t)e * 2);
         c0 = dec_e4m3x2((unsigned short)(v & 0xffffu));
@@ -395,7 +411,7 @@ template <int FMT, bool ADJ>
 __global__ void __launch_bounds__(256) cgemm_simt(
     const unsigned char* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ B, int ldb, int voff_b,
-    float2* __restrict__ Cm, int ldc, int voff_c, int N, const int* active) {
+    float2* __restrict__ Cm, int ldc, int voff_c, int N, const int* active, size_t lo) {
     if (active && *active == 0) return;
     constexpr int BPC = Bytes<FMT>::v;
     const int M = ADJ ? ns : nr;
@@ -418,14 +434,14 @@ __global__ void __launch_bounds__(256) cgemm_simt(
         if (!ADJ) {
             const int m = tid >> 2, kq = (tid & 3) * 2;
             float2 c0 = make_float2(0.f, 0.f), c1 = c0;
-            if (m0 + m < M) load2<FMT>(Gk + (size_t)(m0 + m) * ldg * BPC, kt + kq, c0, c1);
+            if (m0 + m < M) load2<FMT>(Gk + (size_t)(m0 + m) * ldg * BPC, kt + kq, c0, c1, lo);
             As[kq][m] = c0;
             As[kq + 1][m] = c1;
         } else {
             const int kk = tid >> 5, mq = (tid & 31) * 2;
             float2 c0 = make_float2(0.f, 0.f), c1 = c0;
             if (kt + kk < K) {
-                load2<FMT>(Gk + (size_t)(kt + kk) * ldg * BPC, m0 + mq, c0, c1);
+                load2<FMT>(Gk + (size_t)(kt + kk) * ldg * BPC, m0 + mq, c0, c1, lo);
                 const float sc = (FMT == MDC_C64) ? 1.f : sck[kt + kk];
                 c0 = make_float2(c0.x * sc, -c0.y * sc);
                 c1 = make_float2(c1.x * sc, -c1.y * sc);
@@ -473,6 +489,12 @@ __global__ void __launch_bounds__(256) cgemm_simt(
     }
 }
 
+// Offset of the split format's lo plane (bytes, and 16-byte vectors); 0 for other formats.
+size_t lo_plane_bytes(const mdc_plan* p) {
+    return p->storage == MDC_C32S ? (size_t)p->nf * p->nr * p->ldg * 4 : 0;
+}
+int64_t lo_plane_vec(const mdc_plan* p) { return (int64_t)(lo_plane_bytes(p) / 16); }
+
 template <int FMT, int NVC>
 void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                      int voff_o, cudaStream_t s, const int* active) {
@@ -496,7 +518,7 @@ void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
     }
     gemv_fwd<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
         reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-        ldo, voff_o, active);
+        ldo, voff_o, active, lo_plane_vec(p));
 }
 
 template <int FMT, int NVC>
@@ -525,7 +547,7 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
     }
     gemv_adj<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
         reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-        ldo, voff_o, active);
+        ldo, voff_o, active, lo_plane_vec(p));
 }
 
 template <int FMT>
@@ -554,10 +576,10 @@ void product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_
     const unsigned char* G = reinterpret_cast<const unsigned char*>(p->G);
     if (adjoint)
         cgemm_simt<FMT, true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
-                                                   out, ldo, voff_o, ncol, active);
+                                                   out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
     else
         cgemm_simt<FMT, false><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
-                                                    out, ldo, voff_o, ncol, active);
+                                                    out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
 }
 
 }  // namespace
@@ -572,6 +594,7 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
         case MDC_C64: product_fmt<MDC_C64>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
         case MDC_C16F: product_fmt<MDC_C16F>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
         case MDC_CBF16: product_fmt<MDC_CBF16>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+        case MDC_C32S: product_fmt<MDC_C32S>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
         default: product_fmt<MDC_CE4M3>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
     }
 }
@@ -583,7 +606,7 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
 template <int FMT>
 __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ G, int ns, int ldg,
                                                      unsigned char* __restrict__ Q, float* __restrict__ scale) {
-    constexpr float QMAX = FMT == MDC_C16F ? 32768.f : (FMT == MDC_CBF16 ? 1.f : 448.f);
+    constexpr float QMAX = (FMT == MDC_C16F || FMT == MDC_C32S) ? 32768.f : (FMT == MDC_CBF16 ? 1.f : 448.f);
     const size_t row = blockIdx.x;
     const float2* g = G + row * ns;
     float m = 0.f;
@@ -608,6 +631,13 @@ __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ 
         v.y *= inv;
         if constexpr (FMT == MDC_C16F) {
             reinterpret_cast<__half2*>(Q)[row * ldg + s] = __floats2half2_rn(v.x, v.y);
+        } else if constexpr (FMT == MDC_C32S) {
+            // hi = RNE(v), lo = RNE(v - hi): the pair carries about 22 significant bits
+            const __half2 hi = __floats2half2_rn(v.x, v.y);
+            const float2 h = __half22float2(hi);
+            reinterpret_cast<__half2*>(Q)[row * ldg + s] = hi;
+            reinterpret_cast<__half2*>(Q)[(size_t)gridDim.x * ldg + row * ldg + s] =
+                __floats2half2_rn(v.x - h.x, v.y - h.y);
         } else if constexpr (FMT == MDC_CBF16) {
             reinterpret_cast<__nv_bfloat162*>(Q)[row * ldg + s] = __floats2bfloat162_rn(v.x, v.y);
         } else {
@@ -624,6 +654,7 @@ void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s) {
         case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
         case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
         case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
+        case MDC_C32S: quantize_rows<MDC_C32S><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
         default: break;
     }
 }

@@ -138,11 +138,16 @@ struct TcArgs {
     int* err;
 };
 
-template <int BN> struct TcStages { static constexpr int v = BN >= 256 ? 4 : (BN >= 128 ? 6 : 8); };
+// Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies.
+template <int BN, bool SPLIT> struct TcStages {
+    static constexpr int bytes = (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
+    static constexpr int fit = (198 * 1024) / bytes;
+    static constexpr int v = fit > 8 ? 8 : fit;
+};
 
-template <int BN>
+template <int BN, bool SPLIT>
 constexpr size_t tc_smem_bytes() {
-    return (size_t)TcStages<BN>::v * (TC_BM * 128 + BN * 128) + 1024 + 512;
+    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -153,15 +158,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // column tile fastest, then the row tile, then the frequency.  The TMA/MMA stage ring runs
 // continuously across tiles and the accumulator is double-buffered in TMEM (2 x BN columns),
 // so the epilogue of one tile overlaps the main loop of the next.
-template <bool ADJ, int BN>
+template <bool ADJ, int BN, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a,
                    uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
     if (active && *active == 0) return;
-    constexpr int STAGES = TcStages<BN>::v;
+    constexpr int STAGES = TcStages<BN, SPLIT>::v;
     constexpr uint32_t A_BYTES = TC_BM * 128;
     constexpr uint32_t B_BYTES = BN * 128;
-    constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo
+    constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -207,13 +214,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
                     mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-                    if (!ADJ) {
-                        tma_load_3d(sa, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
-                    } else {
-                        tma_load_3d(sa, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
-                        tma_load_3d(sa + A_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+#pragma unroll
+                    for (int h = 0; h < (SPLIT ? 2 : 1); ++h) {
+                        const CUtensorMap* ma = h ? &tmA2 : &tmA;
+                        const CUtensorMap* mb = h ? &tmB2 : &tmB;
+                        const uint32_t ha = sa + h * (A_BYTES + B_BYTES), hb = ha + A_BYTES;
+                        if (!ADJ) {
+                            tma_load_3d(ha, ma, full0 + 8 * s, kb * TC_BK, m0, k);
+                        } else {
+                            tma_load_3d(ha, ma, full0 + 8 * s, m0, kb * TC_BK, k);
+                            tma_load_3d(ha + A_BYTES / 2, ma, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+                        }
+                        tma_load_3d(hb, mb, full0 + 8 * s, kb * TC_BK, n0, k);
                     }
-                    tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
                 }
             }
             // drain: every copy this thread issued must have landed before the CTA can exit
@@ -238,13 +251,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                    const uint32_t sa2 = sb + B_BYTES, sb2 = sa2 + A_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk) {
                         // K-major: +32 bytes per 16 elements inside the swizzled row; MN-major: +16 rows
-                        const uint64_t ad =
-                            ADJ ? sdesc(sa + kk * 2048, A_BYTES / 2, 1024) : sdesc(sa + kk * 32, 16, 1024);
+                        const uint32_t ao = ADJ ? kk * 2048 : kk * 32;
+                        const uint32_t lbo = ADJ ? A_BYTES / 2 : 16;
+                        const uint64_t ad = sdesc(sa + ao, lbo, 1024);
                         const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
                         umma_f16(d, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                        if (SPLIT) {
+                            // hi*lo + lo*hi: the dropped lo*lo term is below 2^-22 relative
+                            umma_f16(d, ad, sdesc(sb2 + kk * 32, 16, 1024), idesc, 1u);
+                            umma_f16(d, sdesc(sa2 + ao, lbo, 1024), bd, idesc, 1u);
+                        }
                     }
                     umma_commit(empty0 + 8 * s);
                 }
@@ -327,10 +347,10 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
 }
 
 // forward: X[k][s][ldi] (voff, ncol columns) -> BT[k][n'][2*ldg], sigma[k][n]
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X, int ldi, int voff, int ns,
                                                    int ncol, int ldg, int rows_pad, T* __restrict__ BT,
-                                                   float* __restrict__ sigma, const int* active) {
+                                                   float* __restrict__ sigma, const int* active, size_t plane) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * 8;
     const float2* Xk = X + (size_t)k * ns * ldi + voff;
@@ -368,20 +388,28 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
             }
             T* r0 = Bk + (size_t)(2 * n) * kp + 2 * (size_t)s;
             T* r1 = r0 + kp;
-            r0[0] = cvt<T>(v.x);
+            const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
+            r0[0] = hx;
             r0[1] = cvt<T>(-v.y);
-            r1[0] = cvt<T>(v.y);
-            r1[1] = cvt<T>(v.x);
+            r1[0] = hy;
+            r1[1] = hx;
+            if (SPLIT) {
+                const float lx = v.x - (float)hx, ly = v.y - (float)hy;
+                r0[plane] = cvt<T>(lx);
+                r0[plane + 1] = cvt<T>(-ly);
+                r1[plane] = cvt<T>(ly);
+                r1[plane + 1] = cvt<T>(lx);
+            }
         }
     }
 }
 
 // adjoint: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] -> BT[k][n''][kpitch], sigma[k][n]
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y, int ldi, int voff, int nr,
                                                    int ncol, const float* __restrict__ gscale, int kpitch,
                                                    int rows_pad, T* __restrict__ BT, float* __restrict__ sigma,
-                                                   const int* active) {
+                                                   const int* active, size_t plane) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * 8;
     const float2* Yk = Y + (size_t)k * nr * ldi + voff;
@@ -419,8 +447,13 @@ __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y,
                 v.x *= f;
                 v.y *= f;
             }
-            Bk[(size_t)(2 * n) * kpitch + r] = cvt<T>(v.x);
-            Bk[(size_t)(2 * n + 1) * kpitch + r] = cvt<T>(v.y);
+            const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
+            Bk[(size_t)(2 * n) * kpitch + r] = hx;
+            Bk[(size_t)(2 * n + 1) * kpitch + r] = hy;
+            if (SPLIT) {
+                Bk[plane + (size_t)(2 * n) * kpitch + r] = cvt<T>(v.x - (float)hx);
+                Bk[plane + (size_t)(2 * n + 1) * kpitch + r] = cvt<T>(v.y - (float)hy);
+            }
         }
     }
 }
@@ -472,19 +505,19 @@ int sm_count() {
     return n;
 }
 
-template <bool ADJ, int BN>
-void launch_tc(const CUtensorMap& A, const CUtensorMap& B, const TcArgs& a, uint32_t idesc, dim3 grid,
-               cudaStream_t s, const int* active) {
+template <bool ADJ, int BN, bool SPLIT>
+void launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
+               const int* active) {
     static bool attr = false;
-    const size_t smem = tc_smem_bytes<BN>();
+    const size_t smem = tc_smem_bytes<BN, SPLIT>();
     if (!attr) {
-        cudaFuncSetAttribute(tc_gemm_kernel<ADJ, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_gemm_kernel<ADJ, BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     const int n_tiles = (int)(grid.x * grid.y * grid.z);
     const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
-    tc_gemm_kernel<ADJ, BN><<<ctas, TC_THREADS, smem, s>>>(A, B, a, idesc, active, (int)grid.x, (int)grid.y,
-                                                           n_tiles);
+    tc_gemm_kernel<ADJ, BN, SPLIT><<<ctas, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc,
+                                                                  active, (int)grid.x, (int)grid.y, n_tiles);
 }
 
 }  // namespace
@@ -503,47 +536,68 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
 }
 
 bool tc_supported(const mdc_plan* p, int ncol) {
-    return (p->storage == MDC_C16F || p->storage == MDC_CBF16) && (ncol >= 8 || p->force_tc) && p->tcB != nullptr &&
-           ncol <= p->tc_cap && encode_fn() != nullptr;
+    return storage_16bit(p->storage) && (ncol >= 8 || p->force_tc) && p->tcB != nullptr && ncol <= p->tc_cap &&
+           encode_fn() != nullptr;
 }
 
 // Per-frequency product on tensor cores; returns false if it could not be launched.
 bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                        int voff_o, int ncol, cudaStream_t s, const int* active) {
     const bool bf16 = p->storage == MDC_CBF16;
+    const bool split = p->storage == MDC_C32S;
     const int rows_pad = tc_rows_pad(ncol);
     const int bn = pick_bn(2 * ncol);
     const int kpitch = (int)round_up(p->nr, 8);
-    // B operand
-    dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
-    if (!adjoint) {
-        if (bf16)
-            tc_prep_fwd<__nv_bfloat16><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
-                                                          (__nv_bfloat16*)p->tcB, p->tcSigma, active);
-        else
-            tc_prep_fwd<__half><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
-                                                   (__half*)p->tcB, p->tcSigma, active);
-    } else {
-        if (bf16)
-            tc_prep_adj<__nv_bfloat16><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch,
-                                                          rows_pad, (__nv_bfloat16*)p->tcB, p->tcSigma, active);
-        else
-            tc_prep_adj<__half><<<pg, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch, rows_pad,
-                                                   (__half*)p->tcB, p->tcSigma, active);
-    }
-    // tensor maps: A over the kernel copy [nf][nr][2*ldg] (16-bit reals), B over the prepared operand
     const uint64_t kp = 2 * (uint64_t)p->ldg;
-    CUtensorMap A, B;
-    bool ok;
+    // B operand (and its lo half for the split format, one plane further)
+    const size_t plane = (size_t)p->nf * rows_pad * (adjoint ? (size_t)kpitch : (size_t)kp);
+    dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
+#define MDC_PREP(KER, T, SP, ...) KER<T, SP><<<pg, 256, 0, s>>>(__VA_ARGS__, active, plane)
     if (!adjoint) {
-        ok = make_map_3d(&A, p->G, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 128) &&
-             make_map_3d(&B, p->tcB, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bn);
+        if (bf16)
+            MDC_PREP(tc_prep_fwd, __nv_bfloat16, false, in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
+                     (__nv_bfloat16*)p->tcB, p->tcSigma);
+        else if (split)
+            MDC_PREP(tc_prep_fwd, __half, true, in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
+                     (__half*)p->tcB, p->tcSigma);
+        else
+            MDC_PREP(tc_prep_fwd, __half, false, in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
+                     (__half*)p->tcB, p->tcSigma);
     } else {
-        ok = make_map_3d(&A, p->G, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 64) &&
-             make_map_3d(&B, p->tcB, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
-                         (uint64_t)kpitch * 2 * rows_pad, 64, bn);
+        if (bf16)
+            MDC_PREP(tc_prep_adj, __nv_bfloat16, false, in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch, rows_pad,
+                     (__nv_bfloat16*)p->tcB, p->tcSigma);
+        else if (split)
+            MDC_PREP(tc_prep_adj, __half, true, in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch, rows_pad,
+                     (__half*)p->tcB, p->tcSigma);
+        else
+            MDC_PREP(tc_prep_adj, __half, false, in, ldi, voff_i, p->nr, ncol, p->gscale, kpitch, rows_pad,
+                     (__half*)p->tcB, p->tcSigma);
+    }
+#undef MDC_PREP
+    // tensor maps: A over the kernel copy [nf][nr][2*ldg] (16-bit reals), B over the prepared operand
+    CUtensorMap maps[4];
+    const unsigned char* G = static_cast<const unsigned char*>(p->G);
+    const unsigned char* Bp = static_cast<const unsigned char*>(p->tcB);
+    const size_t glo = split ? (size_t)p->nf * p->nr * p->ldg * 4 : 0;   // lo plane of the kernel
+    const size_t blo = plane * 2;                                          // lo plane of B (bytes)
+    bool ok = true;
+    for (int h = 0; h < (split ? 2 : 1) && ok; ++h) {
+        const void* ga = G + h * glo;
+        const void* gb = Bp + h * blo;
+        if (!adjoint)
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 128) &&
+                 make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bn);
+        else
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 64) &&
+                 make_map_3d(&maps[2 * h + 1], gb, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
+                             (uint64_t)kpitch * 2 * rows_pad, 64, bn);
     }
     if (!ok) return false;
+    if (!split) {
+        maps[2] = maps[0];
+        maps[3] = maps[1];
+    }
     TcArgs a{};
     a.kstages = adjoint ? (p->nr + TC_BK - 1) / TC_BK : (int)(kp / TC_BK);
     a.nout = adjoint ? p->ns : p->nr;
@@ -560,10 +614,15 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
                            ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     const int mrows = adjoint ? (int)(kp / TC_BM) : (p->nr + TC_BM - 1) / TC_BM;
     dim3 grid((unsigned)(rows_pad / bn), (unsigned)mrows, (unsigned)p->nf);
-#define MDC_TC_CASE(BNV)                                                         \
-    case BNV:                                                                    \
-        if (adjoint) launch_tc<true, BNV>(A, B, a, idesc, grid, s, active);      \
-        else launch_tc<false, BNV>(A, B, a, idesc, grid, s, active);             \
+#define MDC_TC_CASE(BNV)                                                                   \
+    case BNV:                                                                              \
+        if (split) {                                                                       \
+            if (adjoint) launch_tc<true, BNV, true>(maps, a, idesc, grid, s, active);      \
+            else launch_tc<false, BNV, true>(maps, a, idesc, grid, s, active);             \
+        } else {                                                                           \
+            if (adjoint) launch_tc<true, BNV, false>(maps, a, idesc, grid, s, active);     \
+            else launch_tc<false, BNV, false>(maps, a, idesc, grid, s, active);            \
+        }                                                                                  \
         break;
     switch (bn) {
         MDC_TC_CASE(32)

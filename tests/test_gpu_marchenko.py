@@ -141,3 +141,33 @@ def test_refined_rejects_reduced_reference():
         a.marchenko_refined(b, torch.zeros((4, 1), dtype=torch.int32, device="cuda"), fd, 3)
     a.close()
     b.close()
+
+
+def test_marchenko_graph_replay_matches_direct_solve():
+    """MDC_OPT_GRAPHS: the repeated solve is captured once and replayed; results equal the
+    direct solve bit for bit, replays read the current contents of the input buffers, and a
+    replay issues no host-side kernel launches."""
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(5, 128, 40, 2, 200.0)
+    Gt = torch.from_numpy(G.astype(np.complex64)).cuda()
+    op = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c16f")
+    ref = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c32s")
+    cut_t, fd_t = torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda()
+    nv = fd.shape[2]
+    direct = op.marchenko_refined(ref, cut_t, fd_t, 10, nrefine=1, niter_refine=4)
+    m.mdc_set_option(op.h, m.MDC_OPT_GRAPHS, 1)
+    outs = [torch.empty_like(fd_t) for _ in range(4)]
+    for rep in range(3):
+        n0 = m.mdc_launch_count(op.h)
+        resid, fin, iters = m.marchenko_lsqr_refined(op.h, ref.h, cut_t, fd_t, nv, 10, 1, 4, 0.0, *outs)
+        if rep > 0:
+            assert m.mdc_launch_count(op.h) == n0      # replay: no host launches
+        assert iters == direct["iters"] and fin == direct["final_residual"]
+        for o, k in zip(outs, ("f_minus", "f_mplus", "g_minus", "g_plus")):
+            assert torch.equal(o, direct[k])
+    fd_t.mul_(2.0)
+    m.marchenko_lsqr_refined(op.h, ref.h, cut_t, fd_t, nv, 10, 1, 4, 0.0, *outs)
+    assert torch.equal(outs[0], 2.0 * direct["f_minus"])
+    m.mdc_set_option(op.h, m.MDC_OPT_GRAPHS, 0)
+    op.close()
+    ref.close()
