@@ -174,12 +174,49 @@ __host__ __device__ constexpr int brev_bits(int i, int bits) {
 }
 __host__ __device__ constexpr int clog2(int n) { return n <= 1 ? 0 : 1 + clog2(n / 2); }
 
-// In-register R-point DFT, a[k] = sum_n a[n] w^(n k), w = tw[nt/R] (tw holds W_nt^j, j < nt/2).
-// Decimation in frequency (natural order in, bit-reversed order out), then a compile-time
-// permutation back to natural order: every array index is a constant after unrolling.
-template <int R, int STRIDE>
-__device__ __forceinline__ void reg_fft(float2 (&a)[R], const float2* tw) {
+// Roots of unity as compile-time constants: cos and sin of 2*pi/R from the half-angle identities
+// (cos(t/2) = sqrt((1 + cos t) / 2), sin(t/2) = sin t / (2 cos(t/2))) starting at t = pi/2, then
+// powers by angle addition, all in double precision and rounded once to float.
+struct Rot {
+    double c, s;
+};
+constexpr double newton_sqrt(double x) {
+    double r = x > 1.0 ? x : 1.0;
+    for (int i = 0; i < 64; ++i) r = 0.5 * (r + x / r);
+    return r;
+}
+constexpr Rot unit_root(int R, int m) {   // exp(+2 pi i m / R)
+    Rot b{0.0, 1.0};
+    if (R == 1) b = Rot{1.0, 0.0};
+    if (R == 2) b = Rot{-1.0, 0.0};
+    for (int r = 4; r < R; r *= 2) {
+        const double c = newton_sqrt(0.5 * (1.0 + b.c));
+        b = Rot{c, b.s / (2.0 * c)};
+    }
+    Rot w{1.0, 0.0};
+    for (int i = 0; i < m; ++i) w = Rot{w.c * b.c - w.s * b.s, w.s * b.c + w.c * b.s};
+    return w;
+}
+
+// exp(-2 pi i m / 32) for m < 16: every twiddle of the in-register DFTs (R <= 32) is one of
+// these; as constant-bank operands they need no load.
+#define MDC_ROOT32(m) float2{(float)unit_root(32, m).c, -(float)unit_root(32, m).s}
+__constant__ float2 kRoot32[16] = {
+    MDC_ROOT32(0),  MDC_ROOT32(1),  MDC_ROOT32(2),  MDC_ROOT32(3),  MDC_ROOT32(4),  MDC_ROOT32(5),
+    MDC_ROOT32(6),  MDC_ROOT32(7),  MDC_ROOT32(8),  MDC_ROOT32(9),  MDC_ROOT32(10), MDC_ROOT32(11),
+    MDC_ROOT32(12), MDC_ROOT32(13), MDC_ROOT32(14), MDC_ROOT32(15)};
+#undef MDC_ROOT32
+
+// Length-R DFT (R <= 32) of a register array, forward sign exp(-2 pi i n k / R) or, with INV,
+// the inverse sign (unscaled): decimation in frequency (natural order in, bit-reversed order
+// out), then a compile-time permutation back to natural order.  After unrolling every index
+// and twiddle choice is a constant: quarter turns are a swap, eighth turns take the
+// equal-magnitude short form, the rest multiply by a table constant.
+template <int R, bool INV>
+__device__ __forceinline__ void reg_fft(float2 (&a)[R]) {
+    static_assert(R <= 32, "register DFT length");
     constexpr int L = clog2(R);
+    constexpr float h8 = (float)unit_root(8, 1).c;
 #pragma unroll
     for (int st = 0; st < L; ++st) {
         const int h = R >> (st + 1);          // half span of this stage
@@ -189,8 +226,22 @@ __device__ __forceinline__ void reg_fft(float2 (&a)[R], const float2* tw) {
             for (int j = 0; j < h; ++j) {
                 const float2 u = a[g + j], v = a[g + j + h];
                 a[g + j] = cadd(u, v);
-                const float2 d = csub(u, v);
-                a[g + j + h] = (j == 0) ? d : cmul(d, tw[j * (1 << st) * STRIDE]);
+                float2 d = csub(u, v);
+                const int m = j << st;       // twiddle exp(-+2 pi i m / R)
+                if (m == 0) {
+                } else if (4 * m == R) {
+                    d = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+                } else if (8 * m == R) {
+                    d = INV ? make_float2(h8 * (d.x - d.y), h8 * (d.x + d.y))
+                            : make_float2(h8 * (d.x + d.y), h8 * (d.y - d.x));
+                } else if (8 * m == 3 * R) {
+                    d = INV ? make_float2(-h8 * (d.x + d.y), h8 * (d.x - d.y))
+                            : make_float2(h8 * (d.y - d.x), -h8 * (d.x + d.y));
+                } else {
+                    const float2 w = kRoot32[m * (32 / R)];
+                    d = cmul(d, INV ? cconj(w) : w);
+                }
+                a[g + j + h] = d;
             }
         }
     }
@@ -220,7 +271,8 @@ __device__ __forceinline__ float2 tw_full(const float2* tw, int m, int nt) {
     return m < (nt >> 1) ? tw[m] : make_float2(-tw[m - (nt >> 1)].x, -tw[m - (nt >> 1)].y);
 }
 
-template <int N1, int N2>
+// tw: the twiddle table W_NT^m, m < NT/2, of the transform's sign (conjugated for INV).
+template <int N1, int N2, bool INV>
 __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
     using F = FourStep<N1, N2>;
     constexpr int P = F::P;
@@ -229,7 +281,7 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
         float2 r[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) r[n1] = z[F::zi(n1 * N2 + n2, j)];
-        reg_fft<N1, N2>(r, tw);
+        reg_fft<N1, INV>(r);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
             const float2 v = k1 == 0 ? r[0] : cmul(r[k1], tw_full(tw, n2 * k1, F::NT));
@@ -242,7 +294,7 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
         float2 r[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) r[n2] = z[F::zi(k1 * N2 + n2, j)];
-        reg_fft<N2, N1>(r, tw);
+        reg_fft<N2, INV>(r);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) z[F::zi(k1 * N2 + k2, j)] = r[k2];
     }
@@ -330,10 +382,12 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
         }
     }
     __syncthreads();
-    four_step<N1, N2>(z, tw);
+    four_step<N1, N2, false>(z, tw);
     // Bins k < nf sit in rows rho = k1 * N2 + k2 (k = k1 + N1 * k2): the first ceil((nf - k1) / N1)
     // rows of each block k1.  Walk them in storage order so a warp reads consecutive rows.
     const int qn = a.nf / N1, rn = a.nf % N1;
+    const bool same_s = (a.nv % CT) == 0;
+    const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
     for (int idx = threadIdx.x; idx < a.nf * CT; idx += FFT_THREADS) {
         const int ir = idx / CT, cl = idx % CT, c = c0 + cl;
         if (c >= a.C) continue;
@@ -354,7 +408,8 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
         if ((cl & 1) == 0) r = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
         else               r = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
         if (a.conj) r.y = -r.y;
-        const int s = c / a.nv, v = c - s * a.nv;
+        // all columns of the tile share the spatial index s0 when nv is a multiple of CT
+        const int s = same_s ? s0 : c / a.nv, v = same_s ? v0 + cl : c - s * a.nv;
         a.X[((size_t)k * a.S + s) * a.ldv + a.voff + v] = r;
     }
 }
@@ -376,6 +431,9 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         if (k >= a.nf && NT - k >= a.nf) z[F::zi(k, idx % P)] = make_float2(0.f, 0.f);
     }
     // Each loaded bin kk < nf of the two columns fills Z[kk] and its Hermitian mirror Z[NT - kk].
+    // When nv is a multiple of CT every column of this CTA has the same spatial index s0.
+    const bool same_s = (a.nv % CT) == 0;
+    const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
     {
         const int items = a.nf * P;
         constexpr int B = 8;
@@ -389,7 +447,17 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
                 Bv[u] = A[u];
                 if (idx < items) {
                     const int j = idx % P, kk = idx / P, ca = c0 + 2 * j;
-                    if (ca < a.C) {
+                    if (same_s && ca + 1 < a.C) {
+                        const size_t ia = ((size_t)kk * a.S + s0) * a.ldv + a.voff + v0 + 2 * j;
+                        if ((ia & 1) == 0) {
+                            const float4 q = *reinterpret_cast<const float4*>(a.Y + ia);
+                            A[u] = make_float2(q.x, q.y);
+                            Bv[u] = make_float2(q.z, q.w);
+                        } else {
+                            A[u] = a.Y[ia];
+                            Bv[u] = a.Y[ia + 1];
+                        }
+                    } else if (ca < a.C) {
                         const int sa = ca / a.nv, va = ca - sa * a.nv;
                         const size_t ia = ((size_t)kk * a.S + sa) * a.ldv + a.voff + va;
                         if (ca + 1 < a.C) {
@@ -423,7 +491,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         }
     }
     __syncthreads();
-    four_step<N1, N2>(z, tw);
+    four_step<N1, N2, true>(z, tw);
 
     const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
@@ -431,7 +499,8 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         // four adjacent columns per thread: 16-byte loads and stores
         constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, B = PER < 8 ? PER : 8;
         const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
-        double ss[4] = {0.0, 0.0, 0.0, 0.0};
+        const bool want_ss = a.colsum != nullptr;
+        float ss[4] = {0.f, 0.f, 0.f, 0.f};   // per-thread partial sums of squares (<= 16 terms)
         if (cq < a.C) {
             int cut[4];
 #pragma unroll
@@ -461,7 +530,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
                     for (int i = 0; i < 4; ++i) {
                         float val = tau >= cut[i] ? 0.f : v[i] * a.scale;
                         v[i] = am * val + ab * bb[i] + ap * pp[i];
-                        ss[i] += (double)v[i] * (double)v[i];
+                        if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                     }
                     *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
                 }
@@ -469,7 +538,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         }
         if (a.colsum) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = ss[i];
+            for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = (double)ss[i];
             __syncthreads();
             if (threadIdx.x < CT && c0 + (int)threadIdx.x < a.C) {
                 const int qq = threadIdx.x / 4, ii = threadIdx.x % 4;
@@ -481,7 +550,8 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         return;
     }
     const int cl = threadIdx.x % CT, c = c0 + cl;
-    double ss = 0.0;
+    const bool want_ss = a.colsum != nullptr;
+    float ss = 0.f;   // per-thread partial sum of squares (<= 64 terms)
     if (c < a.C) {
         const int cut = a.cut ? a.cut[c] : 0x7fffffff;
         constexpr int TS = FFT_THREADS / CT, PER = NT / TS, B = PER < 8 ? PER : 8;
@@ -508,12 +578,12 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
                 const float r = am * val + ab * bv[u] + ap * pv[u];
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                 a.out[(size_t)to * a.C + c] = r;
-                ss += (double)r * (double)r;
+                if (want_ss) ss = fmaf(r, r, ss);
             }
         }
     }
     if (a.colsum) {
-        red[threadIdx.x] = ss;
+        red[threadIdx.x] = (double)ss;
         __syncthreads();
         if (threadIdx.x < CT && c < a.C) {
             double tot = 0.0;
