@@ -261,6 +261,51 @@ def run_redatum(args, dev):
                              "iterations": plain["iters"], "storage": "c64"}}
 
 
+def run_mdd(args, dev):
+    """Multi-dimensional deconvolution (Eq. 8): a stand-in down-going Green's function G+ between
+    the 61 x 61 surface grid and a 29 x 29 lattice of focusing points (nt=1024, nfmax=200), one
+    batch of 20 virtual sources per LSQR solve, complex64 (FP32 SIMT products) and FP16 (tensor
+    cores) kernel copies; the FP16 result is compared with the complex64 one."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from synth import gpu as sgpu
+    cfg = synth.config(2)
+    d = synth.draw(cfg)
+    xs = synth.focus_lattice(29, synth.GRID_DX, 0.5 * synth.GRID_DX * (cfg.n_side - 1))
+    Gp = sgpu.rect_kernel_on_device(cfg, synth.grid_xy(cfg.n_side), xs, d)
+    nv, niter = 20, args.mdd_iters
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg.seed)
+    g = torch.randn((cfg.nt, cfg.nr, nv), generator=gen, device=dev, dtype=torch.float32)
+    out = {}
+    sol = {}
+    for storage in ("c64", "c16f"):
+        op = mdc.MDC(Gp, cfg.nt, cfg.dt, cfg.dr, storage=storage)
+        r = op.mdd(g, niter)                               # warm-up
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            r = op.mdd(g, niter)
+            times.append(time.perf_counter() - t0)
+        op.close()
+        med = statistics.median(times)
+        sol[storage] = r["r"]
+        n_mdc = 2 * niter + 1
+        out[storage] = {"solves_per_s": 1.0 / med, "virtual_sources_per_s": nv / med, "ms_per_solve": 1e3 * med,
+                        "ms_per_mdc": 1e3 * med / n_mdc, "iterations": r["iters"],
+                        "kernel_gb": cfg.nf * cfg.nr * len(xs) * BYTES_PER_COMPLEX[storage] / 1e9,
+                        "tflops_products": 8.0 * cfg.nf * cfg.nr * len(xs) * nv * n_mdc / med / 1e12}
+    del Gp
+    torch.cuda.empty_cache()
+    a, b = sol["c16f"].double(), sol["c64"].double()
+    out["c16f"]["rel_l2_vs_c64"] = float((a - b).norm() / b.norm())
+    out["workload"] = (f"MDD (Eq. 8) by LSQR, G+ {cfg.nr} receivers (61x61, 20 m) x {len(xs)} focusing points "
+                       f"(29x29, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, {cfg.n_events} hyperbolic events, "
+                       f"{nv} virtual sources per batch, {niter} iterations")
+    return out
+
+
 def serve_loop(mdc, srv, arrivals, pool, horizon, drain):
     """Submit arrivals (t, nv, niter, tol, entry) as their time comes, step the server, and
     collect completed jobs; returns (completed records, jobs still queued or running)."""
@@ -508,6 +553,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_redatum:
         result["redatum"] = run_redatum(args, dev)
+    if world == 1 and not args.no_mdd:
+        result["mdd"] = run_mdd(args, dev)
     if world == 1 and not args.no_serving:
         result["serving"] = run_serving(args, dev)
     if world == 1 and not args.no_cpu_baseline:
@@ -531,6 +578,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-redatum", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mdd", action="store_true")
+    ap.add_argument("--mdd-iters", type=int, default=10)
     ap.add_argument("--serving-config", type=int, default=5)
     ap.add_argument("--serving-rate", type=float, default=50.0)
     ap.add_argument("--serving-horizon", type=float, default=20.0)

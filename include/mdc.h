@@ -88,6 +88,16 @@ typedef enum {
 int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
                double dt, double dr, int storage, void* stream);
 
+/* mdc_create_weighted -- as mdc_create, with a per-column integration weight: the kernel's
+ * column s (integration point x_R) is multiplied by weights[s] before it is copied or
+ * quantised, so the operator integrates with dt * dr * weights[s].  This is the receiver-
+ * dependent scaling for irregular geometries (areal extent of each receiver's Voronoi cell)
+ * that the paper pre-multiplies into the kernel before the batched products (Theory section,
+ * discretisation paragraph; irregular-geometry example).  weights: host double[ns], finite
+ * and >= 0 (MDC_ERR_ARG otherwise), read during the call.  Pass dr = 1 for weights in m^2. */
+int mdc_create_weighted(mdc_handle* out, const void* G, const double* weights, int nfmax, int nr, int ns, int nt,
+                        double dt, double dr, int storage, void* stream);
+
 /*
  * mdc_forward -- y = C x (Eq. 3, left), or y = R* x with MDC_CONJ_KERNEL (Eq. 5).
  *   x  device float32 [nt][ns][nv] (input function f, integration axis ns).
@@ -190,6 +200,31 @@ int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int* window, co
                            float* f_minus, float* f_mplus, float* g_minus, float* g_plus,
                            double* resid, double* final_residual, int* iters_done, void* stream);
 
+/* marchenko_neumann -- Eq. 5 by its Neumann series, the forward-only scheme of the solution
+ * discussion in Section "Marchenko redatuming": with N = [[0, Theta R], [Theta R*, 0]] and
+ * d = [Theta R f_d+; 0], x_k = d + N x_{k-1} from x_0 = 0, so the result is the partial sum
+ * sum_{j<niter} N^j d (one forward pass of 2nv columns per term after the first).  It
+ * converges only when the spectral radius of N is below 1.  niter = 0 gives f- = f_m+ = 0, for
+ * which Eq. 6 yields the single-scattering Green's functions g0- = R f_d+ and g+ = P f_d+.
+ * Arguments and layouts as marchenko_lsqr (g_minus, g_plus nullable); niter >= 0; nr == ns.
+ * Blocking. */
+int marchenko_neumann(mdc_handle R, const int* window, const float* fd_plus, int nv, int niter,
+                      float* f_minus, float* f_mplus, float* g_minus, float* g_plus, void* stream);
+
+/* mdd_lsqr -- multi-dimensional deconvolution, Eq. 8 (Section "Source-side redatuming via
+ * Multi-dimensional deconvolution"): the local reflectivity r solving g- = G+ r by LSQR
+ * (Paige-Saunders, x0 = 0, float64 scalars on the device, float32 vectors), one batch of nv
+ * virtual sources per call.  Gplus: handle whose kernel is the down-going Green's function
+ * G+[nf][nr][ns] (nr = receivers x_S, ns = focusing points x_F; rectangular allowed; any
+ * storage).  g_minus: device float32 [nt][nr][nv] (data, caller-owned, not modified);
+ * r: device float32 [nt][ns][nv] (output).  niter >= 1 iterations, or fewer when
+ * ||r_k|| <= tol * ||g-|| (tol > 0).  resid: host double[niter + 1] (residual-norm estimates,
+ * -1 after the stop; may be NULL); *iters_done: iterations performed (may be NULL).  Each
+ * iteration is one forward and one adjoint MDC.  Blocking.  MDC_ERR_NUMERIC on a non-finite
+ * recurrence. */
+int mdd_lsqr(mdc_handle Gplus, const float* g_minus, int nv, int niter, double tol, float* r, double* resid,
+             int* iters_done, void* stream);
+
 /* ------------------------------------------------------------------------------------
  * Serving: continuous batching of redatuming jobs (Eq. 5 for groups of focusing points,
  * the paper's embarrassingly parallel level of the Discussion, served on one GPU).
@@ -239,6 +274,29 @@ int srv_poll(mdc_server_handle s, int64_t job_id, int* state, int* iters, double
 int srv_release(mdc_server_handle s, int64_t job_id);
 /* srv_stats -- queued and running job counts, bytes and columns in use. */
 int srv_stats(mdc_server_handle s, int* queued, int* running, int64_t* bytes_in_use, int* cols_in_use);
+/* srv_checkpoint -- serialise every queued and running job into host memory so that a server
+ * built later (another process, after a failure) can carry on with srv_resume.  The record holds
+ * each job's inputs and, for a running job, its whole solver state (LSQR vectors and float64
+ * scalars, iterate, refinement stage), so the resumed solve continues bit for bit where it
+ * stopped.  Completed jobs are not included (their outputs are already in the caller's
+ * buffers).  buf == NULL: only *bytes is set (the size needed); otherwise cap >= *bytes
+ * (MDC_ERR_ARG if smaller).  Call between srv_step calls; blocking.  The format is native-endian
+ * with fixed-width fields, for the same library version.  The paper has no counterpart. */
+int srv_checkpoint(mdc_server_handle s, void* buf, int64_t cap, int64_t* bytes);
+/* srv_resume -- rebuild the jobs of a checkpoint on a server with no queued or running jobs,
+ * created over kernels of the same shape and storage formats with the same refinement
+ * settings (MDC_ERR_ARG otherwise; MDC_ERR_STATE if the server has live jobs or already knows
+ * one of the ids; MDC_ERR_BUDGET if the running jobs do not fit its budget or column
+ * capacity, in which case nothing changes).  Jobs keep their ids, order and progress; ids
+ * (capacity max_ids, may be NULL) receives them in checkpoint order and *n_jobs their count.
+ * The server keeps its own copy of queued jobs' inputs.  Resumed jobs have no output buffers:
+ * srv_step returns MDC_ERR_STATE until srv_bind has been called for each.  Blocking. */
+int srv_resume(mdc_server_handle s, const void* buf, int64_t bytes, int64_t* ids, int max_ids, int* n_jobs);
+/* srv_bind -- give a queued or running job (normally a resumed one) its four host output
+ * buffers [nt][ns][nv] (each may be NULL), as srv_submit does.  MDC_ERR_STATE for a job that
+ * has completed. */
+int srv_bind(mdc_server_handle s, int64_t job_id, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+             float* g_plus_host);
 /* srv_destroy -- drop all jobs and free the server (the handles stay valid). */
 int srv_destroy(mdc_server_handle s);
 
@@ -263,6 +321,22 @@ int64_t mdc_kernel_bytes(int nfmax, int nr, int ns, int storage);
  * kernels the handle has launched since creation (timing on or off).
  */
 int mdc_timing(mdc_handle h, int enable);
+/*
+ * mdc_autotune -- choose, per direction and per column count (buckets 1, 2, 4, ... up to
+ * ncol_max), the fastest per-frequency product variant for this handle by timing every variant
+ * that can run on the handle's own buffers: the GEMV (up to 4 columns), the SIMT GEMM, and, for
+ * 16-bit storage, the tensor-core GEMM with each column-tile width (32, 64, 128, 256).  Later
+ * products use the variant of the smallest bucket holding their column count (the serving
+ * engine still forces tensor cores so a job's arithmetic does not depend on its batch).  With
+ * the environment variable MDC_AUTOTUNE_CACHE naming a file, a stored table for the same device,
+ * shape and storage is reused instead of timing, and new tables are appended (JSON lines).
+ * Blocking; allocates scratch for ncol_max columns.  All variants compute the same operator.
+ */
+int mdc_autotune(mdc_handle h, int ncol_max, void* stream);
+/* mdc_autotune_choice -- the variant selected for ncol columns: *path 0 = default rule, 1 = GEMV,
+ * 2 = SIMT GEMM, 3 = tensor cores with column tile *bn. */
+int mdc_autotune_choice(mdc_handle h, int adjoint, int ncol, int* path, int* bn);
+
 /* mdc_set_option -- MDC_OPT_GRAPHS (value 1/0): when on, a marchenko_lsqr or
  * marchenko_lsqr_refined call whose arguments (sizes, iteration counts, tolerance and every
  * pointer) repeat an earlier call on this handle replays that call's CUDA graph: the whole solve

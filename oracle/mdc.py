@@ -43,6 +43,13 @@ def batch_matmul(G: np.ndarray, X: np.ndarray) -> np.ndarray:
     return np.matmul(G, X)
 
 
+def weighted_kernel(G: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Receiver-dependent integration weights (the areal extent of each point's Voronoi cell for
+    an irregular geometry) pre-multiplied into the kernel's columns, the integration axis, before
+    the batched products (Theory section, discretisation paragraph)."""
+    return np.asarray(G, np.complex128) * np.asarray(w, np.float64)[None, None, :]
+
+
 def forward(G: np.ndarray, x: np.ndarray, dt: float, dr: float) -> np.ndarray:
     """g = C f (Eq. 3, left): x [nt, ns, nv] -> y [nt, nr, nv]."""
     G = np.asarray(G, dtype=np.complex128)

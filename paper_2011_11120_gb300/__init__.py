@@ -29,6 +29,7 @@ KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj":
 _vp, _i, _d, _u, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_int64
 SIGNATURES = {
     "mdc_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i, _i, _d, _d, _i, _vp]),
+    "mdc_create_weighted": (_i, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(_d), _i, _i, _i, _i, _d, _d, _i, _vp]),
     "mdc_forward": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_adjoint": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_reserve": (_i, [_vp, _i]),
@@ -37,6 +38,8 @@ SIGNATURES = {
                             ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
     "marchenko_lsqr_refined": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d, _vp, _vp, _vp, _vp,
                                     ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
+    "marchenko_neumann": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _vp, _vp]),
+    "mdd_lsqr": (_i, [_vp, _vp, _i, _i, _d, _vp, ctypes.POINTER(_d), ctypes.POINTER(_i), _vp]),
     "mdc_destroy": (_i, [_vp]),
     "mdc_strerror": (ctypes.c_char_p, [_i]),
     "mdc_last_cuda_error": (_i, []),
@@ -46,6 +49,8 @@ SIGNATURES = {
     "mdc_launch_count": (_i64, [_vp]),
     "mdc_device_status": (_i, [_vp, _vp]),
     "mdc_set_option": (_i, [_vp, _i, _i]),
+    "mdc_autotune": (_i, [_vp, _i, _vp]),
+    "mdc_autotune_choice": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "srv_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _i64, _i, _i, _i, _vp]),
     "srv_submit": (_i, [_vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp, _vp, _vp, ctypes.POINTER(_i64)]),
     "srv_step": (_i, [_vp, ctypes.POINTER(_i)]),
@@ -53,6 +58,9 @@ SIGNATURES = {
                       ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "srv_release": (_i, [_vp, _i64]),
     "srv_stats": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i)]),
+    "srv_checkpoint": (_i, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "srv_resume": (_i, [_vp, _vp, _i64, ctypes.POINTER(_i64), _i, ctypes.POINTER(_i)]),
+    "srv_bind": (_i, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "srv_destroy": (_i, [_vp]),
 }
 
@@ -108,15 +116,25 @@ def _ptr(t: Optional[torch.Tensor], dtype=None, name="tensor"):
 
 
 # ------------------------------------------------------------------ ABI-named calls
-def mdc_create(G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None) -> ctypes.c_void_p:
-    """Build an MDC handle from a complex64 CUDA tensor G[nfmax, nr, ns] (copied)."""
+def mdc_create(G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None,
+               weights=None) -> ctypes.c_void_p:
+    """Build an MDC handle from a complex64 CUDA tensor G[nfmax, nr, ns] (copied).  ``weights``
+    (length ns, e.g. Voronoi cell areas) multiplies the kernel's columns (mdc_create_weighted)."""
     if G.dtype != torch.complex64 or G.dim() != 3:
         raise ValueError("G must be complex64 [nfmax, nr, ns]")
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
     h = ctypes.c_void_p()
     nf, nr, ns = G.shape
-    _check(lib().mdc_create(ctypes.byref(h), _ptr(G, name="G"), nf, nr, ns, nt, dt, dr, st, _stream(stream)),
-           "mdc_create")
+    if weights is None:
+        _check(lib().mdc_create(ctypes.byref(h), _ptr(G, name="G"), nf, nr, ns, nt, dt, dr, st, _stream(stream)),
+               "mdc_create")
+    else:
+        w = np.ascontiguousarray(np.asarray(weights, np.float64).reshape(-1))
+        if w.shape[0] != ns:
+            raise ValueError("weights needs one value per kernel column")
+        _check(lib().mdc_create_weighted(ctypes.byref(h), _ptr(G, name="G"),
+                                         w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nf, nr, ns, nt, dt, dr,
+                                         st, _stream(stream)), "mdc_create_weighted")
     return h
 
 
@@ -151,6 +169,26 @@ def marchenko_lsqr(h, window: torch.Tensor, fd_plus: torch.Tensor, nv: int, nite
                               _ptr(f_mplus, torch.float32, "f_mplus"), _ptr(g_minus, torch.float32, "g_minus"),
                               _ptr(g_plus, torch.float32, "g_plus"), resid, ctypes.byref(it), _stream(stream))
     _check(st, "marchenko_lsqr")
+    return [resid[i] for i in range(niter + 1)], it.value
+
+
+def marchenko_neumann(h, window: torch.Tensor, fd_plus: torch.Tensor, nv: int, niter: int,
+                      f_minus: torch.Tensor, f_mplus: torch.Tensor, g_minus=None, g_plus=None, stream=None):
+    """Eq. 5 by its Neumann series (niter terms; 0 gives the single-scattering Green's functions)."""
+    st = lib().marchenko_neumann(h, _ptr(window, torch.int32, "window"), _ptr(fd_plus, torch.float32, "fd_plus"),
+                                 nv, niter, _ptr(f_minus, torch.float32, "f_minus"),
+                                 _ptr(f_mplus, torch.float32, "f_mplus"), _ptr(g_minus, torch.float32, "g_minus"),
+                                 _ptr(g_plus, torch.float32, "g_plus"), _stream(stream))
+    _check(st, "marchenko_neumann")
+
+
+def mdd_lsqr(h, g_minus: torch.Tensor, nv: int, niter: int, tol: float, r: torch.Tensor, stream=None):
+    """Eq. 8 by LSQR: r [nt][ns][nv] from g_minus [nt][nr][nv]; returns (resid list, iterations)."""
+    resid = (ctypes.c_double * (niter + 1))()
+    it = ctypes.c_int(0)
+    st = lib().mdd_lsqr(h, _ptr(g_minus, torch.float32, "g_minus"), nv, niter, tol, _ptr(r, torch.float32, "r"),
+                        resid, ctypes.byref(it), _stream(stream))
+    _check(st, "mdd_lsqr")
     return [resid[i] for i in range(niter + 1)], it.value
 
 
@@ -198,6 +236,18 @@ def mdc_launch_count(h) -> int:
 
 
 MDC_OPT_GRAPHS = 1
+PATHS = {0: "default", 1: "gemv", 2: "simt", 3: "tensor-core"}
+
+
+def mdc_autotune(h, ncol_max: int, stream=None) -> None:
+    _check(lib().mdc_autotune(h, ncol_max, _stream(stream)), "mdc_autotune")
+
+
+def mdc_autotune_choice(h, adjoint: bool, ncol: int) -> tuple:
+    pa, bn = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().mdc_autotune_choice(h, 1 if adjoint else 0, ncol, ctypes.byref(pa), ctypes.byref(bn)),
+           "mdc_autotune_choice")
+    return PATHS[pa.value], bn.value
 
 
 def mdc_set_option(h, option: int, value: int) -> None:
@@ -213,10 +263,10 @@ def mdc_device_status(h, stream=None) -> None:
 class MDC:
     """Owning wrapper: ``MDC(G, nt, dt, dr)``, ``.forward(x)``, ``.adjoint(y)``, ``.marchenko(...)``."""
 
-    def __init__(self, G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None):
+    def __init__(self, G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", stream=None, weights=None):
         self.nf, self.nr, self.ns = G.shape
         self.nt, self.dt, self.dr = nt, dt, dr
-        self.h = mdc_create(G, nt, dt, dr, storage, stream)
+        self.h = mdc_create(G, nt, dt, dr, storage, stream, weights)
 
     def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, conj=False, stream=None):
         nv = x.shape[2]
@@ -240,6 +290,21 @@ class MDC:
         gm, gp = (mk(), mk()) if greens else (None, None)
         resid, iters = marchenko_lsqr(self.h, window, fd_plus, nv, niter, tol, fm, fmp, gm, gp, stream)
         return {"f_minus": fm, "f_mplus": fmp, "g_minus": gm, "g_plus": gp, "resid": resid, "iters": iters}
+
+    def mdd(self, g_minus: torch.Tensor, niter: int, tol: float = 0.0, stream=None):
+        """Local reflectivity r solving g- = G+ r (this handle's kernel is G+), Eq. 8."""
+        nt, _, nv = g_minus.shape
+        r = torch.empty((nt, self.ns, nv), dtype=torch.float32, device=g_minus.device)
+        resid, iters = mdd_lsqr(self.h, g_minus, nv, niter, tol, r, stream)
+        return {"r": r, "resid": resid, "iters": iters}
+
+    def neumann(self, window: torch.Tensor, fd_plus: torch.Tensor, niter: int, greens: bool = True, stream=None):
+        nv = fd_plus.shape[2]
+        mk = lambda: torch.empty_like(fd_plus)  # noqa: E731
+        fm, fmp = mk(), mk()
+        gm, gp = (mk(), mk()) if greens else (None, None)
+        marchenko_neumann(self.h, window, fd_plus, nv, niter, fm, fmp, gm, gp, stream)
+        return {"f_minus": fm, "f_mplus": fmp, "g_minus": gm, "g_plus": gp}
 
     def marchenko_refined(self, ref: "MDC", window: torch.Tensor, fd_plus: torch.Tensor, niter: int,
                           nrefine: int = 1, niter_refine: int = 10, tol: float = 0.0, greens: bool = True,
@@ -329,6 +394,35 @@ def srv_stats(v) -> dict:
     b = ctypes.c_int64(0)
     _check(lib().srv_stats(v, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(c)), "srv_stats")
     return {"queued": q.value, "running": r.value, "bytes": b.value, "cols": c.value}
+
+
+def srv_checkpoint(v) -> bytearray:
+    """Serialised queued and running jobs (inputs and solver state) as a host byte array."""
+    n = ctypes.c_int64(0)
+    _check(lib().srv_checkpoint(v, None, 0, ctypes.byref(n)), "srv_checkpoint")
+    buf = bytearray(n.value)
+    cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+    _check(lib().srv_checkpoint(v, ctypes.addressof(cbuf), len(buf), ctypes.byref(n)), "srv_checkpoint")
+    del cbuf
+    return buf
+
+
+def srv_resume(v, data) -> list:
+    """Rebuild the jobs of a checkpoint on an idle server; returns their ids in checkpoint order."""
+    data = bytes(data)
+    n = ctypes.c_int(0)
+    # job count: the tenth 32-bit field after the 8-byte tag of the header
+    njobs = int(np.frombuffer(data, np.int32, count=1, offset=8 + 4 * 9)[0]) if len(data) >= 48 else 1
+    cnt = min(max(1, njobs), max(1, len(data) // 72))    # a job record takes at least 72 bytes
+    ids = (ctypes.c_int64 * cnt)()
+    _check(lib().srv_resume(v, data, len(data), ids, cnt, ctypes.byref(n)), "srv_resume")
+    return [int(ids[i]) for i in range(n.value)]
+
+
+def srv_bind(v, job_id: int, outputs=(None, None, None, None)) -> None:
+    """Host output buffers (f-, f_m+, g-, g+; float32 [nt][ns][nv], may be None) of a resumed job."""
+    o = [_hptr(a) for a in outputs]
+    _check(lib().srv_bind(v, job_id, o[0], o[1], o[2], o[3]), "srv_bind")
 
 
 def srv_destroy(v) -> None:

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-Xptxas", "-v"] + ARCH
 
-SOURCES = ["api.cu", "fft.cu", "product.cu", "lsqr.cu", "static_scratch.cu", "tc_gemm.cu"]
+SOURCES = ["api.cu", "fft.cu", "product.cu", "lsqr.cu", "static_scratch.cu", "mdd.cu", "tc_gemm.cu"]
 
 
 def nvcc() -> str:

@@ -77,6 +77,9 @@ static void free_plan(mdc_plan* p) {
     if (!p) return;
     if (p->graph_free)
         for (void* g : p->graph_cache) p->graph_free(g);
+    if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
+    for (cudaEvent_t e : p->graph_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(p->G);
     cudaFree(p->gscale);
     cudaFree(p->tw);
@@ -92,8 +95,17 @@ static void free_plan(mdc_plan* p) {
     delete p;
 }
 
-extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
-                          double dt, double dr, int storage, void* stream) {
+// Column weights (receiver integration areas) multiply the library's copy of the kernel.
+__global__ void scale_columns(float2* __restrict__ G, int ns, size_t ldg, const float* __restrict__ w) {
+    float2* g = G + (size_t)blockIdx.x * ldg;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const float2 v = g[s];
+        g[s] = make_float2(v.x * w[s], v.y * w[s]);
+    }
+}
+
+static int create_plan(mdc_handle* out, const void* G, const double* weights, int nfmax, int nr, int ns, int nt,
+                       double dt, double dr, int storage, void* stream) {
     if (!out) return MDC_ERR_ARG;
     *out = nullptr;
     if (!G || nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
@@ -108,6 +120,14 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
     p->ldg = round_up(ns, G_PITCH_ALIGN);
     const size_t rowbytes = (size_t)p->ldg * storage_bytes(storage);
     cudaError_t e = cudaMalloc(&p->G, rowbytes * nr * nfmax);
+    float* w_d = nullptr;
+    if (weights && e == cudaSuccess) {
+        std::vector<float> wf(ns);
+        for (int i = 0; i < ns; ++i) wf[i] = (float)weights[i];
+        e = cudaMalloc(&w_d, sizeof(float) * ns);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w_d, wf.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // wf is a host temporary
+    }
     if (storage == MDC_C64) {
         if (e == cudaSuccess) e = cudaMemcpy2DAsync(p->G, rowbytes, G, (size_t)ns * sizeof(float2),
                                                     (size_t)ns * sizeof(float2), (size_t)nr * nfmax,
@@ -115,10 +135,14 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
         if (e == cudaSuccess && p->ldg > ns)
             e = cudaMemset2DAsync((char*)p->G + (size_t)ns * sizeof(float2), rowbytes, 0,
                                   (size_t)(p->ldg - ns) * sizeof(float2), (size_t)nr * nfmax, s);
+        if (e == cudaSuccess && w_d) {
+            scale_columns<<<(unsigned)((int64_t)nr * nfmax), 256, 0, s>>>(static_cast<float2*>(p->G), ns, p->ldg, w_d);
+            e = cudaGetLastError();
+        }
     } else {
         if (e == cudaSuccess) e = cudaMalloc(&p->gscale, sizeof(float) * (size_t)nr * nfmax);
         if (e == cudaSuccess) {
-            launch_quantize(p, static_cast<const float2*>(G), s);
+            launch_quantize(p, static_cast<const float2*>(G), w_d, s);
             e = cudaGetLastError();
         }
     }
@@ -135,6 +159,7 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
                                                   cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
+    if (w_d) cudaFree(w_d);
     if (e != cudaSuccess) {
         set_cuda_error(e);
         free_plan(p);
@@ -143,6 +168,19 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
     }
     *out = p;
     return MDC_OK;
+}
+
+extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
+                          double dt, double dr, int storage, void* stream) {
+    return create_plan(out, G, nullptr, nfmax, nr, ns, nt, dt, dr, storage, stream);
+}
+
+extern "C" int mdc_create_weighted(mdc_handle* out, const void* G, const double* weights, int nfmax, int nr,
+                                   int ns, int nt, double dt, double dr, int storage, void* stream) {
+    if (!weights) return MDC_ERR_ARG;
+    for (int i = 0; i < ns; ++i)
+        if (!std::isfinite(weights[i]) || weights[i] < 0.0) return MDC_ERR_ARG;
+    return create_plan(out, G, weights, nfmax, nr, ns, nt, dt, dr, storage, stream);
 }
 
 int mdc::ensure_scratch(mdc_plan* p, int ncols) {
@@ -270,6 +308,28 @@ extern "C" int mdc_timing_read(mdc_handle h, int cls, double* total_ms, int64_t*
 }
 
 extern "C" int64_t mdc_launch_count(mdc_handle h) { return h ? h->launch_count : -1; }
+
+namespace mdc {
+int autotune(mdc_plan* p, int ncol_max, cudaStream_t s);
+}
+
+extern "C" int mdc_autotune(mdc_handle h, int ncol_max, void* stream) {
+    if (!h || ncol_max < 1) return MDC_ERR_ARG;
+    return mdc::autotune(h, ncol_max, (cudaStream_t)stream);
+}
+
+extern "C" int mdc_autotune_choice(mdc_handle h, int adjoint, int ncol, int* path, int* bn) {
+    if (!h || ncol < 1 || !path || !bn) return MDC_ERR_ARG;
+    *path = 0;
+    *bn = 0;
+    for (const ProductChoice& c : h->tune[adjoint ? 1 : 0])
+        if (ncol <= c.ncol) {
+            *path = c.path;
+            *bn = c.bn;
+            break;
+        }
+    return MDC_OK;
+}
 
 extern "C" int mdc_set_option(mdc_handle h, int option, int value) {
     if (!h) return MDC_ERR_ARG;

@@ -39,6 +39,14 @@ constexpr int G_PITCH_ALIGN = 64;
 // ------------------------------------------------------------------ plan
 struct EventPair { cudaEvent_t a, b; };
 
+// Product variant chosen by the autotuner for column counts up to `ncol`.
+enum ProductPath { PATH_AUTO = 0, PATH_GEMV = 1, PATH_SIMT = 2, PATH_TC = 3 };
+struct ProductChoice {
+    int ncol;
+    int path;
+    int bn;     // tensor-core column tile (PATH_TC)
+};
+
 struct TimingState {
     bool on = false;
     std::vector<EventPair> pool;
@@ -69,7 +77,10 @@ struct mdc_plan {
     int* err_flag = nullptr;    // device int: non-zero after a bounded device wait gave up
     bool force_tc = false;      // FP16/BF16: tensor-core products for every column count
     bool graphs = false;        // capture repeated solves into CUDA graphs (mdc_set_option)
+    std::vector<mdc::ProductChoice> tune[2];   // autotuned variants [forward, adjoint], ascending ncol
     std::vector<void*> graph_cache;   // solver workspaces with their instantiated graphs
+    cudaStream_t graph_stream = nullptr;   // private stream for capture and replay
+    cudaEvent_t graph_ev[2] = {nullptr, nullptr};
     void (*graph_free)(void*) = nullptr;
     int64_t launch_count = 0;
     mdc::TimingState timing;
@@ -129,11 +140,14 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
 // Tensor-core products (tc_gemm.cu).
 bool tc_supported(const mdc_plan* p, int ncol);
 bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
-                       int voff_o, int ncol, cudaStream_t s, const int* active);
+                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override = 0);
+// One product with an explicit variant (autotuner); returns false if the variant cannot run.
+bool launch_product_variant(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out,
+                            int ldo, int voff_o, int ncol, cudaStream_t s, int path, int bn);
 size_t tc_scratch_elems(const mdc_plan* p, int ncol);
 
 // Quantise a complex64 kernel [nf][nr][ns] into the plan's reduced-storage copy and row scales.
-void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s);
+void launch_quantize(mdc_plan* p, const float2* G, const float* w, cudaStream_t s);
 
 // Bytes of one stored complex value (MDC_C32S: 4 in each of its two planes).
 inline int storage_bytes(int storage) {

@@ -21,189 +21,13 @@
 #include <vector>
 
 #include "common.cuh"
+#include "lsqr_core.cuh"
 
 namespace mdc {
 
 int ensure_scratch(mdc_plan* p, int ncols);
 
 namespace {
-
-enum Slot {
-    S_ALPHA, S_BETA, S_RHO, S_RHOBAR, S_PHI, S_PHIBAR, S_C, S_S, S_THETA, S_BETA1,
-    S_INV_ALPHA, S_INV_BETA, S_U_PREV, S_V_PREV, S_KX, S_KW, S_STATUS, S_COUNT
-};
-
-constexpr int RED_THREADS = 1024;
-
-__device__ double block_sum(const double* v, int n) {
-    __shared__ double red[RED_THREADS];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += RED_THREADS) acc += v[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    const double r = red[0];
-    __syncthreads();
-    return r;
-}
-
-// beta_1 = ||d||, u_1 = d / beta_1 (Paige-Saunders initialisation).
-__global__ void __launch_bounds__(RED_THREADS) lsqr_init_beta(double* sc, const double* cs, int n,
-                                                              double* resid, int* act1) {
-    const double b = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) {
-        sc[S_BETA] = b;
-        sc[S_BETA1] = b;
-        sc[S_PHIBAR] = b;
-        sc[S_INV_BETA] = b > 0.0 ? 1.0 / b : 0.0;
-        sc[S_V_PREV] = 0.0;
-        sc[S_STATUS] = isfinite(b) ? 0.0 : 1.0;
-        resid[0] = b;
-        *act1 = (b > 0.0 && isfinite(b)) ? 1 : 0;
-    }
-}
-
-// alpha_1 v_1 = M^H u_1, w_1 = v_1, rhobar_1 = alpha_1.
-__global__ void __launch_bounds__(RED_THREADS) lsqr_init_alpha(double* sc, const double* cs, int n,
-                                                               int* act1) {
-    if (*act1 == 0) return;
-    const double a = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) {
-        sc[S_ALPHA] = a;
-        sc[S_RHOBAR] = a;
-        sc[S_INV_ALPHA] = a > 0.0 ? 1.0 / a : 0.0;
-        sc[S_U_PREV] = a > 0.0 ? -a * sc[S_INV_BETA] : 0.0;
-        if (!isfinite(a)) { sc[S_STATUS] = 1.0; *act1 = 0; }
-        if (a == 0.0) *act1 = 0;   // M^H d = 0: x = 0 is a least-squares solution
-    }
-}
-
-// After u-hat = M v - alpha u: beta = ||u-hat||, coefficients for the M^H step.
-__global__ void __launch_bounds__(RED_THREADS) lsqr_beta(double* sc, const double* cs, int n,
-                                                         const int* act) {
-    if (*act == 0) return;
-    const double b = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) {
-        sc[S_BETA] = b;
-        sc[S_INV_BETA] = b > 0.0 ? 1.0 / b : 0.0;
-        sc[S_V_PREV] = -b * sc[S_INV_ALPHA];
-        if (!isfinite(b)) sc[S_STATUS] = 1.0;
-    }
-}
-
-// After v-hat = M^H u - beta v: alpha, the plane rotation, and the x/w coefficients.
-__global__ void __launch_bounds__(RED_THREADS) lsqr_alpha_rotate(double* sc, const double* cs, int n,
-                                                                 const int* act, int* act_next,
-                                                                 double* resid, int* iters, int it,
-                                                                 int niter, double tol) {
-    if (*act == 0) return;
-    double a = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) {
-        const double b = sc[S_BETA];
-        if (b == 0.0) a = 0.0;
-        sc[S_ALPHA] = a;
-        sc[S_INV_ALPHA] = a > 0.0 ? 1.0 / a : 0.0;
-        const double rhobar = sc[S_RHOBAR], phibar = sc[S_PHIBAR];
-        const double rho = hypot(rhobar, b);
-        const double c = rhobar / rho, s = b / rho;
-        const double theta = s * a;
-        sc[S_RHO] = rho; sc[S_C] = c; sc[S_S] = s; sc[S_THETA] = theta;
-        sc[S_RHOBAR] = -c * a;
-        sc[S_PHI] = c * phibar;
-        sc[S_PHIBAR] = s * phibar;
-        sc[S_KX] = sc[S_PHI] / rho;
-        sc[S_KW] = -theta / rho;
-        sc[S_U_PREV] = -a * sc[S_INV_BETA];
-        resid[it] = sc[S_PHIBAR];
-        *iters = it;
-        bool bad = !isfinite(a) || !isfinite(rho) || sc[S_STATUS] != 0.0;
-        if (bad) sc[S_STATUS] = 1.0;
-        const bool stop = bad || a == 0.0 || b == 0.0 || it >= niter ||
-                          (tol > 0.0 && sc[S_PHIBAR] <= tol * sc[S_BETA1]);
-        *act_next = stop ? 0 : 1;
-    }
-}
-
-// x += (phi/rho) w ;  w = v-hat / alpha - (theta/rho) w, over both blocks.
-__global__ void lsqr_xw(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
-                        float* __restrict__ w1, float* __restrict__ w2,
-                        const float* __restrict__ v1, const float* __restrict__ v2,
-                        const double* sc, const int* act) {
-    if (*act == 0) return;
-    const float kx = (float)sc[S_KX], kw = (float)sc[S_KW], ia = (float)sc[S_INV_ALPHA];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float w = w1[i];
-        x1[i] += kx * w;
-        w1[i] = ia * v1[i] + kw * w;
-        w = w2[i];
-        x2[i] += kx * w;
-        w2[i] = ia * v2[i] + kw * w;
-    }
-}
-
-// w_1 = v_1 = v-hat / alpha_1, x_0 = 0.
-__global__ void lsqr_xw_init(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
-                             float* __restrict__ w1, float* __restrict__ w2,
-                             const float* __restrict__ v1, const float* __restrict__ v2,
-                             const double* sc) {
-    const float ia = (float)sc[S_INV_ALPHA];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        x1[i] = 0.f;
-        x2[i] = 0.f;
-        w1[i] = ia * v1[i];
-        w2[i] = ia * v2[i];
-    }
-}
-
-__global__ void vec_add(int64_t n, const float* a, const float* b, float* out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = a[i] + b[i];
-}
-
-__global__ void fill_d(double* p, int n, double v) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
-}
-
-int elementwise_grid(int64_t n) {
-    int64_t g = (n + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
-    return (int)(g < 1 ? 1 : g);
-}
-
-// sqrt(sum of column sums) / reference norm, written to out (the FP64 residual check).
-__global__ void __launch_bounds__(RED_THREADS) norm_ratio(const double* cs, int n, const double* ref, double* out) {
-    const double v = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) *out = (*ref > 0.0) ? v / *ref : v;
-}
-__global__ void __launch_bounds__(RED_THREADS) norm_store(const double* cs, int n, double* out) {
-    const double v = sqrt(block_sum(cs, n));
-    if (threadIdx.x == 0) *out = v;
-}
-
-__global__ void copy_f(int64_t n, const float* a, float* out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = a[i];
-}
-
-// w_1 = v_1 = v-hat / alpha_1; x is kept (refinement continues from the current solution).
-__global__ void lsqr_w_init(int64_t n, float* __restrict__ w1, float* __restrict__ w2,
-                            const float* __restrict__ v1, const float* __restrict__ v2, const double* sc) {
-    const float ia = (float)sc[S_INV_ALPHA];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        w1[i] = ia * v1[i];
-        w2[i] = ia * v2[i];
-    }
-}
-
-enum Extra { X_DNORM, X_FINAL, X_COUNT };
 
 // Work state of one Marchenko solve (Eq. 5) on one GPU stream.
 struct Solver {
@@ -395,6 +219,31 @@ struct Solver {
         }
     }
 
+    // Neumann series of Eq. 5 (forward passes only): x_k = d + N x_{k-1} from x_0 = 0, with
+    // N [a; b] = [Theta R b ; Theta R* a] and d = [D1; 0] (data_pass with keep_data); after niter
+    // passes x = sum_{j<niter} N^j d.  Both halves of N come from one forward product over 2nv
+    // columns; the spectra are taken before x is overwritten, so the update is in place.
+    void neumann(float* x1, float* x2, int niter) {
+        const Coef zero = C1(0.f);
+        if (niter == 0) {
+            cudaMemsetAsync(x1, 0, B * sizeof(float), s);
+            cudaMemsetAsync(x2, 0, B * sizeof(float), s);
+            return;
+        }
+        {
+            LaunchScope ls(p, s, MDC_KC_SOLVER);
+            copy_f<<<elementwise_grid(B), 256, 0, s>>>(B, D1(), x1);
+        }
+        cudaMemsetAsync(x2, 0, B * sizeof(float), s);
+        for (int k = 2; k <= niter; ++k) {
+            rfft(p, x2, nullptr, nullptr, C1(1.f), 0, 0, nullptr);
+            rfft(p, x1, nullptr, nullptr, C1(1.f), 1, nv, nullptr);
+            launch_product(p, false, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, nullptr);
+            irfft(p, 0, 0, x1, C1(1.f), cut, D1(), C1(1.f), zero, nullptr, 0, nullptr);
+            irfft(p, nv, 1, x2, C1(1.f), cut, nullptr, zero, zero, nullptr, 0, nullptr);
+        }
+    }
+
     // Eq. 6: g- = R f+ - f-,  g+* = f+ - R* f-,  f+ = f_d+ + f_m+ ; g+ = time reversal of g+*
     void greens(const float* fd, const float* fm, const float* fmp, float* gm, float* gp) {
         const Coef zero = C1(0.f);
@@ -482,12 +331,26 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
     Solver local;
     Solver* S = &local;
     GraphEntry* ge = nullptr;
+    cudaStream_t caller = s;
     if (p->graphs) {
+        // capture and replay on the handle's own stream (the legacy default stream cannot be
+        // captured), ordered after and before the caller's stream with events
+        if (!p->graph_stream) {
+            if (cudaStreamCreateWithFlags(&p->graph_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->graph_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->graph_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return MDC_ERR_CUDA;
+            }
+        }
+        s = p->graph_stream;
+        cudaEventRecord(p->graph_ev[0], caller);
+        cudaStreamWaitEvent(s, p->graph_ev[0], 0);
         for (void* q : p->graph_cache) {
             GraphEntry* g = static_cast<GraphEntry*>(q);
             if (g->pr == pr && g->cut == cut && g->fd == fd && g->out[0] == fm && g->out[1] == fmp && g->out[2] == gm &&
                 g->out[3] == gp && g->nv == nv && g->niter == niter && g->nref == nref && g->niter_ref == niter_ref &&
-                g->tol == tol && g->want_final == (final_h != nullptr) && g->S->s == s) {
+                g->tol == tol && g->want_final == (final_h != nullptr)) {
                 ge = g;
                 break;
             }
@@ -523,10 +386,13 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
         }
         S = ge->S;
         cudaError_t e = cudaGraphLaunch(ge->exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(p->graph_ev[1], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, p->graph_ev[1], 0);
         if (e != cudaSuccess) {
             set_cuda_error(e);
             return MDC_ERR_CUDA;
         }
+        s = caller;
     } else {
         init_solver(local, p, pr, cut, nv, niter, nref, niter_ref, s);
         st = local.alloc(keep_data);
@@ -585,6 +451,31 @@ extern "C" int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int*
                               g_minus, g_plus, resid, final_residual, iters_done, (cudaStream_t)stream);
 }
 
+extern "C" int marchenko_neumann(mdc_handle R, const int* window, const float* fd_plus, int nv, int niter,
+                                 float* f_minus, float* f_mplus, float* g_minus, float* g_plus, void* stream) {
+    if (!R || !window || !fd_plus || !f_minus || !f_mplus || nv < 1 || niter < 0) return MDC_ERR_ARG;
+    if (R->nr != R->ns) return MDC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = mdc::ensure_scratch(R, 2 * nv);
+    if (st != MDC_OK) return st;
+    mdc::Solver S;
+    mdc::init_solver(S, R, R, window, nv, 1, 0, 0, s);
+    st = S.alloc(true);
+    if (st != MDC_OK) return st;
+    S.data_pass(fd_plus);
+    S.neumann(f_minus, f_mplus, niter);
+    if (g_minus || g_plus) S.greens(fd_plus, f_minus, f_mplus, g_minus, g_plus);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        mdc::set_cuda_error(e);
+        return MDC_ERR_CUDA;
+    }
+    int err = 0;
+    cudaMemcpy(&err, R->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    return err ? MDC_ERR_TIMEOUT : MDC_OK;
+}
+
 // ======================================================================== serving
 // Continuous batching of redatuming jobs (Eq. 5 systems for groups of focusing points).
 // Each job keeps its own LSQR state (vectors and float64 scalars) resident on the device.
@@ -595,6 +486,7 @@ extern "C" int marchenko_lsqr_refined(mdc_handle R, mdc_handle R_ref, const int*
 // a solve move to refinement (float32 residual on the reference kernel) or complete
 // (Green's functions, results copied to the caller's host buffers).
 #include <chrono>
+#include <cstring>
 #include <deque>
 #include <unordered_map>
 
@@ -625,6 +517,9 @@ struct ServeJob {
     double final_resid = -1.0;
     double t_submit = 0.0, t_start = 0.0, t_done = 0.0;
     int64_t bytes = 0;
+    bool bound = true;           // false for a resumed job until srv_bind gives its outputs
+    std::vector<int> cut_own;    // inputs held by the server (resumed queued jobs)
+    std::vector<float> fd_own;
 };
 
 }  // namespace
@@ -716,6 +611,119 @@ int start_job(mdc_server* v, ServeJob* j) {
     return MDC_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint format
+// Native-endian, fixed-width records: a header, then per queued or running job a record, its
+// inputs (window, f_d+) and, for a running job, every device array of its solver state.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nf, nr, ns, nt, storage, ref_storage, nref, niter_ref, njobs;
+    int64_t next_id;
+};
+struct CkptJob {
+    int64_t id;
+    int32_t nv, niter, state, solve, it, aoff, roff, nresid, nact, nsolves;
+    double tol, age_submit, age_start;
+};
+constexpr char kCkptMagic[8] = {'M', 'D', 'C', 'S', 'R', 'V', 0, 1};
+constexpr int kCkptVersion = 1;
+
+// The device arrays of a running job, in checkpoint order: (pointer, bytes).
+std::vector<std::pair<void*, size_t>> job_arrays(ServeJob* j) {
+    Solver* S = j->S;
+    const size_t fb = (size_t)S->B * sizeof(float);
+    std::vector<std::pair<void*, size_t>> v;
+    for (float* b : S->blk) v.emplace_back(b, fb);
+    v.emplace_back(j->x[0], fb);
+    v.emplace_back(j->x[1], fb);
+    v.emplace_back(S->csU, 2 * (size_t)S->C * sizeof(double));
+    v.emplace_back(S->csV, 2 * (size_t)S->C * sizeof(double));
+    v.emplace_back(S->sc, S_COUNT * sizeof(double));
+    v.emplace_back(S->xs, X_COUNT * sizeof(double));
+    v.emplace_back(S->resid, (size_t)S->nresid * sizeof(double));
+    v.emplace_back(S->act, (size_t)S->nact * sizeof(int));
+    v.emplace_back(S->iters, (size_t)S->nsolves * sizeof(int));
+    return v;
+}
+
+int64_t ckpt_job_bytes(const mdc_plan* p, const CkptJob& r) {
+    const int64_t C = (int64_t)p->ns * r.nv, B = (int64_t)p->nt * C;
+    int64_t n = (int64_t)sizeof(CkptJob) + C * 4 + B * 4;
+    if (r.state == JOB_RUNNING)
+        n += 9 * B * 4 + 4 * C * 8 + (S_COUNT + X_COUNT + r.nresid) * 8 + (int64_t)(r.nact + r.nsolves) * 4;
+    return n;
+}
+
+CkptJob ckpt_record(ServeJob* j, double now) {
+    CkptJob r{};
+    r.id = j->id;
+    r.nv = j->nv;
+    r.niter = j->niter;
+    r.state = j->state;
+    r.solve = j->solve;
+    r.it = j->it;
+    r.aoff = j->aoff;
+    r.roff = j->roff;
+    r.nresid = j->S ? j->S->nresid : 0;
+    r.nact = j->S ? j->S->nact : 0;
+    r.nsolves = j->S ? j->S->nsolves : 0;
+    r.tol = j->tol;
+    r.age_submit = now - j->t_submit;
+    r.age_start = j->state == JOB_RUNNING ? now - j->t_start : 0.0;
+    return r;
+}
+
+// Device state of a resumed running job: buffers as start_job allocates them, contents from the
+// checkpoint (cur points at the job's window).
+int restore_job(mdc_server* v, ServeJob* j, const CkptJob& r, const unsigned char* cur) {
+    mdc_plan* p = v->p;
+    const int64_t C = (int64_t)p->ns * j->nv, B = (int64_t)p->nt * C;
+    cudaError_t e = cudaMallocAsync((void**)&j->cut_d, C * sizeof(int), v->s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&j->fd_d, B * sizeof(float), v->s);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMallocAsync((void**)&j->x[i], B * sizeof(float), v->s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_cuda_error(e);
+        free_job_device(v, j);
+        return MDC_ERR_OOM;
+    }
+    Solver* S = new Solver();
+    S->p = p;
+    S->pr = v->pr;
+    S->nv = j->nv;
+    S->n = p->ns;
+    S->C = (int)C;
+    S->B = B;
+    S->s = v->s;
+    S->cut = j->cut_d;
+    S->async_alloc = true;
+    S->nsolves = r.nsolves;
+    S->nresid = r.nresid;
+    S->nact = r.nact;
+    j->S = S;
+    int st = S->alloc(true);
+    if (st != MDC_OK) {
+        free_job_device(v, j);
+        return st;
+    }
+    S->layout(0, 0);
+    e = cudaMemcpyAsync(j->cut_d, cur, C * sizeof(int), cudaMemcpyHostToDevice, v->s);
+    cur += C * sizeof(int);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(j->fd_d, cur, B * sizeof(float), cudaMemcpyHostToDevice, v->s);
+    cur += B * sizeof(float);
+    for (auto& a : job_arrays(j)) {
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(a.first, cur, a.second, cudaMemcpyHostToDevice, v->s);
+        cur += a.second;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->s);   // the checkpoint buffer may go after return
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        free_job_device(v, j);
+        return MDC_ERR_CUDA;
+    }
+    return MDC_OK;
+}
+
 // Complete a finished job: float32 residual check, Green's functions, results to the host.
 void finish_job(mdc_server* v, ServeJob* j) {
     Solver* S = j->S;
@@ -797,6 +805,10 @@ extern "C" int srv_submit(mdc_server* v, const int* window_host, const float* fd
 
 extern "C" int srv_step(mdc_server* v, int* completed) {
     if (!v) return MDC_ERR_ARG;
+    for (ServeJob* j : v->queue)
+        if (!j->bound) return MDC_ERR_STATE;
+    for (ServeJob* j : v->running)
+        if (!j->bound) return MDC_ERR_STATE;
     int ndone = 0;
     // 1. admission, in arrival order, while memory and columns allow
     while (!v->queue.empty()) {
@@ -954,6 +966,193 @@ extern "C" int srv_stats(mdc_server* v, int* queued, int* running, int64_t* byte
     if (running) *running = (int)v->running.size();
     if (bytes_in_use) *bytes_in_use = v->used;
     if (cols_in_use) *cols_in_use = v->cols;
+    return MDC_OK;
+}
+
+extern "C" int srv_checkpoint(mdc_server* v, void* buf, int64_t cap, int64_t* bytes) {
+    if (!v || !bytes) return MDC_ERR_ARG;
+    std::vector<ServeJob*> js(v->running.begin(), v->running.end());
+    js.insert(js.end(), v->queue.begin(), v->queue.end());
+    const double now = now_s();
+    int64_t need = (int64_t)sizeof(CkptHeader);
+    for (ServeJob* j : js) need += ckpt_job_bytes(v->p, ckpt_record(j, now));
+    *bytes = need;
+    if (!buf) return MDC_OK;
+    if (cap < need) return MDC_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(v->s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return MDC_ERR_CUDA;
+    }
+    unsigned char* cur = static_cast<unsigned char*>(buf);
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.version = kCkptVersion;
+    h.nf = v->p->nf;
+    h.nr = v->p->nr;
+    h.ns = v->p->ns;
+    h.nt = v->p->nt;
+    h.storage = v->p->storage;
+    h.ref_storage = v->pr->storage;
+    h.nref = v->nref;
+    h.niter_ref = v->niter_ref;
+    h.njobs = (int32_t)js.size();
+    h.next_id = v->next_id;
+    std::memcpy(cur, &h, sizeof h);
+    cur += sizeof h;
+    const int ns = v->p->ns, nt = v->p->nt;
+    for (ServeJob* j : js) {
+        const CkptJob r = ckpt_record(j, now);
+        std::memcpy(cur, &r, sizeof r);
+        cur += sizeof r;
+        const size_t nv = (size_t)j->nv, C = (size_t)ns * nv, B = (size_t)nt * C;
+        if (j->state == JOB_RUNNING) {
+            e = cudaMemcpyAsync(cur, j->cut_d, C * sizeof(int), cudaMemcpyDeviceToHost, v->s);
+            cur += C * sizeof(int);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cur, j->fd_d, B * sizeof(float), cudaMemcpyDeviceToHost, v->s);
+            cur += B * sizeof(float);
+            for (auto& a : job_arrays(j)) {
+                if (e != cudaSuccess) break;
+                e = cudaMemcpyAsync(cur, a.first, a.second, cudaMemcpyDeviceToHost, v->s);
+                cur += a.second;
+            }
+            if (e != cudaSuccess) {
+                set_cuda_error(e);
+                return MDC_ERR_CUDA;
+            }
+        } else {
+            // queued: the inputs still live in host memory, rows of ld values
+            for (size_t i = 0; i < (size_t)ns; ++i) std::memcpy(cur + i * nv * 4, j->cut_h + i * j->ld, nv * 4);
+            cur += C * sizeof(int);
+            for (size_t i = 0; i < (size_t)ns * nt; ++i) std::memcpy(cur + i * nv * 4, j->fd_h + i * j->ld, nv * 4);
+            cur += B * sizeof(float);
+        }
+    }
+    e = cudaStreamSynchronize(v->s);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return MDC_ERR_CUDA;
+    }
+    return MDC_OK;
+}
+
+extern "C" int srv_resume(mdc_server* v, const void* buf, int64_t bytes, int64_t* ids, int max_ids, int* n_jobs) {
+    if (!v || !buf || bytes < (int64_t)sizeof(CkptHeader)) return MDC_ERR_ARG;
+    if (!v->queue.empty() || !v->running.empty()) return MDC_ERR_STATE;
+    const unsigned char* base = static_cast<const unsigned char*>(buf);
+    CkptHeader h;
+    std::memcpy(&h, base, sizeof h);
+    if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != kCkptVersion || h.njobs < 0)
+        return MDC_ERR_ARG;
+    if (h.nf != v->p->nf || h.nr != v->p->nr || h.ns != v->p->ns || h.nt != v->p->nt ||
+        h.storage != v->p->storage || h.ref_storage != v->pr->storage || h.nref != v->nref ||
+        h.niter_ref != v->niter_ref)
+        return MDC_ERR_ARG;
+    if (ids && max_ids < h.njobs) return MDC_ERR_ARG;
+    // pass 1: validate every record against the buffer, the budget and the ids in use
+    std::vector<CkptJob> recs(h.njobs);
+    std::vector<int64_t> offs(h.njobs);
+    int64_t off = sizeof h, used = v->used;
+    int cols = v->cols;
+    for (int q = 0; q < h.njobs; ++q) {
+        if (off + (int64_t)sizeof(CkptJob) > bytes) return MDC_ERR_ARG;
+        std::memcpy(&recs[q], base + off, sizeof(CkptJob));
+        const CkptJob& r = recs[q];
+        if (r.nv < 1 || r.niter < 1 || (r.state != JOB_QUEUED && r.state != JOB_RUNNING) || v->jobs.count(r.id) ||
+            r.id >= h.next_id)
+            return r.id >= 0 && v->jobs.count(r.id) ? MDC_ERR_STATE : MDC_ERR_ARG;
+        if (r.state == JOB_RUNNING) {
+            if (r.nsolves != 1 + v->nref || r.nresid != (r.niter + 1) + v->nref * (v->niter_ref + 1) ||
+                r.nact != (r.niter + 2) + v->nref * (v->niter_ref + 2) || r.solve < 0 || r.solve > v->nref)
+                return MDC_ERR_ARG;
+            used += job_bytes(v->p, r.nv);
+            cols += 2 * r.nv;
+        }
+        offs[q] = off + (int64_t)sizeof(CkptJob);
+        off += ckpt_job_bytes(v->p, r);
+        if (off > bytes) return MDC_ERR_ARG;
+    }
+    if (used > v->budget || cols > v->max_cols) return MDC_ERR_BUDGET;
+    // pass 2: rebuild the jobs (running ones with their device state), in checkpoint order
+    const double now = now_s();
+    std::vector<ServeJob*> made;
+    int st = MDC_OK;
+    for (int q = 0; q < h.njobs && st == MDC_OK; ++q) {
+        const CkptJob& r = recs[q];
+        ServeJob* j = new (std::nothrow) ServeJob();
+        if (!j) {
+            st = MDC_ERR_OOM;
+            break;
+        }
+        j->id = r.id;
+        j->nv = r.nv;
+        j->niter = r.niter;
+        j->tol = r.tol;
+        j->ld = r.nv;
+        j->bytes = job_bytes(v->p, r.nv);
+        j->t_submit = now - r.age_submit;
+        j->bound = false;
+        const unsigned char* cur = base + offs[q];
+        if (r.state == JOB_RUNNING) {
+            j->t_start = now - r.age_start;
+            j->solve = r.solve;
+            j->it = r.it;
+            j->aoff = r.aoff;
+            j->roff = r.roff;
+            st = restore_job(v, j, r, cur);
+            if (st != MDC_OK) {
+                delete j;
+                break;
+            }
+            j->state = JOB_RUNNING;
+        } else {
+            const size_t C = (size_t)v->p->ns * r.nv, B = (size_t)v->p->nt * C;
+            j->cut_own.resize(C);
+            j->fd_own.resize(B);
+            std::memcpy(j->cut_own.data(), cur, C * sizeof(int));
+            std::memcpy(j->fd_own.data(), cur + C * sizeof(int), B * sizeof(float));
+            j->cut_h = j->cut_own.data();
+            j->fd_h = j->fd_own.data();
+        }
+        made.push_back(j);
+    }
+    if (st != MDC_OK) {
+        for (ServeJob* j : made) {
+            if (j->S) free_job_device(v, j);
+            delete j;
+        }
+        cudaStreamSynchronize(v->s);
+        return st;
+    }
+    for (ServeJob* j : made) {
+        v->jobs[j->id] = j;
+        if (j->state == JOB_RUNNING) {
+            v->running.push_back(j);
+            v->used += j->bytes;
+            v->cols += 2 * j->nv;
+        } else {
+            v->queue.push_back(j);
+        }
+    }
+    if (h.next_id > v->next_id) v->next_id = h.next_id;
+    if (ids)
+        for (int q = 0; q < h.njobs; ++q) ids[q] = made[q]->id;
+    if (n_jobs) *n_jobs = h.njobs;
+    return MDC_OK;
+}
+
+extern "C" int srv_bind(mdc_server* v, int64_t id, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+                        float* g_plus_host) {
+    if (!v) return MDC_ERR_ARG;
+    auto it = v->jobs.find(id);
+    if (it == v->jobs.end()) return MDC_ERR_ARG;
+    ServeJob* j = it->second;
+    if (j->state != JOB_QUEUED && j->state != JOB_RUNNING) return MDC_ERR_STATE;
+    j->out[0] = f_minus_host;
+    j->out[1] = f_mplus_host;
+    j->out[2] = g_minus_host;
+    j->out[3] = g_plus_host;
+    j->bound = true;
     return MDC_OK;
 }
 

@@ -1,0 +1,192 @@
+// LSQR building blocks shared by the Marchenko (Eq. 5) and multi-dimensional deconvolution
+// (Eq. 8) solvers: the float64 scalar recurrences of Paige and Saunders (1982), run on the
+// device by one CTA with fixed-order sums, and the float32 vector updates.  Each translation
+// unit that includes this header gets its own copies (internal linkage).
+#pragma once
+
+#include <cmath>
+
+#include "common.cuh"
+
+namespace mdc {
+namespace {
+
+enum Slot {
+    S_ALPHA, S_BETA, S_RHO, S_RHOBAR, S_PHI, S_PHIBAR, S_C, S_S, S_THETA, S_BETA1,
+    S_INV_ALPHA, S_INV_BETA, S_U_PREV, S_V_PREV, S_KX, S_KW, S_STATUS, S_COUNT
+};
+
+constexpr int RED_THREADS = 1024;
+
+__device__ double block_sum(const double* v, int n) {
+    __shared__ double red[RED_THREADS];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += RED_THREADS) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// beta_1 = ||d||, u_1 = d / beta_1 (Paige-Saunders initialisation).
+__global__ void __launch_bounds__(RED_THREADS) lsqr_init_beta(double* sc, const double* cs, int n,
+                                                              double* resid, int* act1) {
+    const double b = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) {
+        sc[S_BETA] = b;
+        sc[S_BETA1] = b;
+        sc[S_PHIBAR] = b;
+        sc[S_INV_BETA] = b > 0.0 ? 1.0 / b : 0.0;
+        sc[S_V_PREV] = 0.0;
+        sc[S_STATUS] = isfinite(b) ? 0.0 : 1.0;
+        resid[0] = b;
+        *act1 = (b > 0.0 && isfinite(b)) ? 1 : 0;
+    }
+}
+
+// alpha_1 v_1 = M^H u_1, w_1 = v_1, rhobar_1 = alpha_1.
+__global__ void __launch_bounds__(RED_THREADS) lsqr_init_alpha(double* sc, const double* cs, int n,
+                                                               int* act1) {
+    if (*act1 == 0) return;
+    const double a = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) {
+        sc[S_ALPHA] = a;
+        sc[S_RHOBAR] = a;
+        sc[S_INV_ALPHA] = a > 0.0 ? 1.0 / a : 0.0;
+        sc[S_U_PREV] = a > 0.0 ? -a * sc[S_INV_BETA] : 0.0;
+        if (!isfinite(a)) { sc[S_STATUS] = 1.0; *act1 = 0; }
+        if (a == 0.0) *act1 = 0;   // M^H d = 0: x = 0 is a least-squares solution
+    }
+}
+
+// After u-hat = M v - alpha u: beta = ||u-hat||, coefficients for the M^H step.
+__global__ void __launch_bounds__(RED_THREADS) lsqr_beta(double* sc, const double* cs, int n,
+                                                         const int* act) {
+    if (*act == 0) return;
+    const double b = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) {
+        sc[S_BETA] = b;
+        sc[S_INV_BETA] = b > 0.0 ? 1.0 / b : 0.0;
+        sc[S_V_PREV] = -b * sc[S_INV_ALPHA];
+        if (!isfinite(b)) sc[S_STATUS] = 1.0;
+    }
+}
+
+// After v-hat = M^H u - beta v: alpha, the plane rotation, and the x/w coefficients.
+__global__ void __launch_bounds__(RED_THREADS) lsqr_alpha_rotate(double* sc, const double* cs, int n,
+                                                                 const int* act, int* act_next,
+                                                                 double* resid, int* iters, int it,
+                                                                 int niter, double tol) {
+    if (*act == 0) return;
+    double a = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) {
+        const double b = sc[S_BETA];
+        if (b == 0.0) a = 0.0;
+        sc[S_ALPHA] = a;
+        sc[S_INV_ALPHA] = a > 0.0 ? 1.0 / a : 0.0;
+        const double rhobar = sc[S_RHOBAR], phibar = sc[S_PHIBAR];
+        const double rho = hypot(rhobar, b);
+        const double c = rhobar / rho, s = b / rho;
+        const double theta = s * a;
+        sc[S_RHO] = rho; sc[S_C] = c; sc[S_S] = s; sc[S_THETA] = theta;
+        sc[S_RHOBAR] = -c * a;
+        sc[S_PHI] = c * phibar;
+        sc[S_PHIBAR] = s * phibar;
+        sc[S_KX] = sc[S_PHI] / rho;
+        sc[S_KW] = -theta / rho;
+        sc[S_U_PREV] = -a * sc[S_INV_BETA];
+        resid[it] = sc[S_PHIBAR];
+        *iters = it;
+        bool bad = !isfinite(a) || !isfinite(rho) || sc[S_STATUS] != 0.0;
+        if (bad) sc[S_STATUS] = 1.0;
+        const bool stop = bad || a == 0.0 || b == 0.0 || it >= niter ||
+                          (tol > 0.0 && sc[S_PHIBAR] <= tol * sc[S_BETA1]);
+        *act_next = stop ? 0 : 1;
+    }
+}
+
+// x += (phi/rho) w ;  w = v-hat / alpha - (theta/rho) w, over both blocks.
+__global__ void lsqr_xw(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
+                        float* __restrict__ w1, float* __restrict__ w2,
+                        const float* __restrict__ v1, const float* __restrict__ v2,
+                        const double* sc, const int* act) {
+    if (*act == 0) return;
+    const float kx = (float)sc[S_KX], kw = (float)sc[S_KW], ia = (float)sc[S_INV_ALPHA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float w = w1[i];
+        x1[i] += kx * w;
+        w1[i] = ia * v1[i] + kw * w;
+        w = w2[i];
+        x2[i] += kx * w;
+        w2[i] = ia * v2[i] + kw * w;
+    }
+}
+
+// w_1 = v_1 = v-hat / alpha_1, x_0 = 0.
+__global__ void lsqr_xw_init(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
+                             float* __restrict__ w1, float* __restrict__ w2,
+                             const float* __restrict__ v1, const float* __restrict__ v2,
+                             const double* sc) {
+    const float ia = (float)sc[S_INV_ALPHA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x1[i] = 0.f;
+        x2[i] = 0.f;
+        w1[i] = ia * v1[i];
+        w2[i] = ia * v2[i];
+    }
+}
+
+__global__ void vec_add(int64_t n, const float* a, const float* b, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] + b[i];
+}
+
+__global__ void fill_d(double* p, int n, double v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+int elementwise_grid(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// sqrt(sum of column sums) / reference norm, written to out (the FP64 residual check).
+__global__ void __launch_bounds__(RED_THREADS) norm_ratio(const double* cs, int n, const double* ref, double* out) {
+    const double v = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) *out = (*ref > 0.0) ? v / *ref : v;
+}
+__global__ void __launch_bounds__(RED_THREADS) norm_store(const double* cs, int n, double* out) {
+    const double v = sqrt(block_sum(cs, n));
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void copy_f(int64_t n, const float* a, float* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i];
+}
+
+// w_1 = v_1 = v-hat / alpha_1; x is kept (refinement continues from the current solution).
+__global__ void lsqr_w_init(int64_t n, float* __restrict__ w1, float* __restrict__ w2,
+                            const float* __restrict__ v1, const float* __restrict__ v2, const double* sc) {
+    const float ia = (float)sc[S_INV_ALPHA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        w1[i] = ia * v1[i];
+        w2[i] = ia * v2[i];
+    }
+}
+
+enum Extra { X_DNORM, X_FINAL, X_COUNT };
+
+}  // namespace
+}  // namespace mdc

@@ -550,13 +550,19 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         ldo, voff_o, active, lo_plane_vec(p));
 }
 
-template <int FMT>
-void product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
-                 int voff_o, int ncol, cudaStream_t s, const int* active) {
-    constexpr int TILE = 32 * Fmt<FMT>::CPV;
+bool gemv_fits(const mdc_plan* p, bool adjoint, int ncol, int cpv) {
     const int64_t stage = (int64_t)(adjoint ? p->nr : p->ldg) * ncol * (int64_t)sizeof(float2);
-    const int64_t red = (int64_t)(GEMV_THREADS / 32) * TILE * ncol * (int64_t)sizeof(float2);
-    if (ncol <= gemv_max_columns() && stage <= 200 * 1024 && red <= 200 * 1024) {
+    const int64_t red = (int64_t)(GEMV_THREADS / 32) * 32 * cpv * ncol * (int64_t)sizeof(float2);
+    return ncol <= gemv_max_columns() && stage <= 200 * 1024 && red <= 200 * 1024;
+}
+
+// path: PATH_GEMV or PATH_SIMT (PATH_AUTO: GEMV when it fits, else SIMT)
+template <int FMT>
+bool product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
+                 int voff_o, int ncol, cudaStream_t s, const int* active, int path) {
+    const bool fits = gemv_fits(p, adjoint, ncol, Fmt<FMT>::CPV);
+    if (path == PATH_GEMV && !fits) return false;
+    if (fits && path != PATH_SIMT) {
 #define MDC_GEMV_CASE(n)                                                                       \
     case n:                                                                                    \
         if (adjoint) gemv_adj_launch<FMT, n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active); \
@@ -569,7 +575,7 @@ void product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_
             MDC_GEMV_CASE(4)
         }
 #undef MDC_GEMV_CASE
-        return;
+        return true;
     }
     const int M = adjoint ? p->ns : p->nr;
     dim3 grid((ncol + GBN - 1) / GBN, (M + GBM - 1) / GBM, p->nf);
@@ -580,23 +586,52 @@ void product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_
     else
         cgemm_simt<FMT, false><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
                                                     out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
+    return true;
+}
+
+bool product_simt_or_gemv(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
+                          int voff_o, int ncol, cudaStream_t s, const int* active, int path) {
+    switch (p->storage) {
+        case MDC_C64: return product_fmt<MDC_C64>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path);
+        case MDC_C16F: return product_fmt<MDC_C16F>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path);
+        case MDC_CBF16: return product_fmt<MDC_CBF16>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path);
+        case MDC_C32S: return product_fmt<MDC_C32S>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path);
+        default: return product_fmt<MDC_CE4M3>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path);
+    }
 }
 
 }  // namespace
+
+bool launch_product_variant(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out,
+                            int ldo, int voff_o, int ncol, cudaStream_t s, int path, int bn) {
+    if (path == PATH_TC)
+        return storage_16bit(p->storage) && p->tcB && ncol <= p->tc_cap &&
+               launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, nullptr, bn);
+    return product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, nullptr, path);
+}
 
 void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
                     float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
                     const int* active) {
     LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
-    if (tc_supported(p, ncol) && launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active))
-        return;
-    switch (p->storage) {
-        case MDC_C64: product_fmt<MDC_C64>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
-        case MDC_C16F: product_fmt<MDC_C16F>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
-        case MDC_CBF16: product_fmt<MDC_CBF16>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
-        case MDC_C32S: product_fmt<MDC_C32S>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
-        default: product_fmt<MDC_CE4M3>(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active); break;
+    int path = PATH_AUTO, bn = 0;
+    if (!p->force_tc) {
+        // autotuned variant of the smallest tuned bucket holding ncol columns
+        for (const ProductChoice& c : p->tune[adjoint ? 1 : 0])
+            if (ncol <= c.ncol) {
+                path = c.path;
+                bn = c.bn;
+                break;
+            }
     }
+    if (path == PATH_TC || (path == PATH_AUTO && tc_supported(p, ncol))) {
+        if (storage_16bit(p->storage) && p->tcB && ncol <= p->tc_cap &&
+            launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, bn))
+            return;
+        path = PATH_AUTO;
+    }
+    if (!product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path))
+        product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, PATH_AUTO);
 }
 
 // ------------------------------------------------------------------ quantiser
@@ -605,13 +640,19 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
 // 448 (E4M3 largest finite).  Padding columns s >= ns are written as zeros.
 template <int FMT>
 __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ G, int ns, int ldg,
-                                                     unsigned char* __restrict__ Q, float* __restrict__ scale) {
+                                                     unsigned char* __restrict__ Q, float* __restrict__ scale,
+                                                     const float* __restrict__ w) {
     constexpr float QMAX = (FMT == MDC_C16F || FMT == MDC_C32S) ? 32768.f : (FMT == MDC_CBF16 ? 1.f : 448.f);
     const size_t row = blockIdx.x;
     const float2* g = G + row * ns;
     float m = 0.f;
-    for (int s = threadIdx.x; s < ns; s += 256) {
+    // optional column weights multiply the kernel before it is quantised
+    auto at = [&](int s) {
         const float2 v = g[s];
+        return w ? make_float2(v.x * w[s], v.y * w[s]) : v;
+    };
+    for (int s = threadIdx.x; s < ns; s += 256) {
+        const float2 v = at(s);
         m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
     __shared__ float red[256];
@@ -626,7 +667,7 @@ __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ 
     const float inv = rowmax > 0.f ? QMAX / rowmax : 0.f;
     if (threadIdx.x == 0) scale[row] = sc;
     for (int s = threadIdx.x; s < ldg; s += 256) {
-        float2 v = s < ns ? g[s] : make_float2(0.f, 0.f);
+        float2 v = s < ns ? at(s) : make_float2(0.f, 0.f);
         v.x *= inv;
         v.y *= inv;
         if constexpr (FMT == MDC_C16F) {
@@ -647,16 +688,156 @@ __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ 
     }
 }
 
-void launch_quantize(mdc_plan* p, const float2* G, cudaStream_t s) {
+void launch_quantize(mdc_plan* p, const float2* G, const float* w, cudaStream_t s) {
     const unsigned rows = (unsigned)((int64_t)p->nf * p->nr);
     unsigned char* Q = reinterpret_cast<unsigned char*>(p->G);
     switch (p->storage) {
-        case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
-        case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
-        case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
-        case MDC_C32S: quantize_rows<MDC_C32S><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale); break;
+        case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
+        case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
+        case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
+        case MDC_C32S: quantize_rows<MDC_C32S><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
         default: break;
     }
+}
+
+}  // namespace mdc
+
+// ------------------------------------------------------------------ autotuner
+// For each direction and each column-count bucket (1, 2, 4, ..., up to ncol_max) time every
+// variant that can run -- GEMV (<= 4 columns), SIMT GEMM, and for 16-bit storage the tensor-core
+// GEMM with column tiles of 32, 64, 128 and 256 -- on the handle's own spectra with CUDA events
+// (one warm-up, median of three), and keep the fastest.  The table maps ncol to the variant of
+// the smallest bucket >= ncol.  With MDC_AUTOTUNE_CACHE set, tables are read from / appended to
+// that file (one JSON object per line) keyed by device name, shape and storage.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+namespace mdc {
+
+int ensure_scratch(mdc_plan* p, int ncols);
+
+static std::string tune_key(const mdc_plan* p) {
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s|nf=%d|nr=%d|ns=%d|nt=%d|storage=%d", prop.name, p->nf, p->nr, p->ns, p->nt,
+             p->storage);
+    for (char* c = buf; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return buf;
+}
+
+static bool tune_load(mdc_plan* p, const std::string& key, int ncol_max) {
+    const char* path = getenv("MDC_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    std::string want = "\"key\": \"" + key + "\"";
+    char line[1 << 16];
+    bool found = false;
+    while (fgets(line, sizeof(line), f)) {
+        if (!strstr(line, want.c_str())) continue;
+        int cmax = 0;
+        const char* q = strstr(line, "\"ncol_max\": ");
+        if (!q || sscanf(q + 12, "%d", &cmax) != 1 || cmax < ncol_max) continue;
+        q = strstr(line, "\"choices\": [");
+        if (!q) continue;
+        q += 12;
+        std::vector<ProductChoice> t[2];
+        int d, n, pa, bn, used;
+        while (sscanf(q, " [%d, %d, %d, %d]%n", &d, &n, &pa, &bn, &used) == 4 && (d == 0 || d == 1)) {
+            t[d].push_back(ProductChoice{n, pa, bn});
+            q += used;
+            while (*q == ',' || *q == ' ') ++q;
+        }
+        if (!t[0].empty() && !t[1].empty()) {
+            p->tune[0] = t[0];
+            p->tune[1] = t[1];
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_store(const mdc_plan* p, const std::string& key, int ncol_max) {
+    const char* path = getenv("MDC_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"ncol_max\": %d, \"choices\": [", key.c_str(), ncol_max);
+    bool first = true;
+    for (int d = 0; d < 2; ++d)
+        for (const ProductChoice& c : p->tune[d]) {
+            fprintf(f, "%s[%d, %d, %d, %d]", first ? "" : ", ", d, c.ncol, c.path, c.bn);
+            first = false;
+        }
+    fprintf(f, "]}\n");
+    fclose(f);
+}
+
+int autotune(mdc_plan* p, int ncol_max, cudaStream_t s) {
+    const std::string key = tune_key(p);
+    if (tune_load(p, key, ncol_max)) return MDC_OK;
+    int st = ensure_scratch(p, ncol_max);
+    if (st != MDC_OK) return st;
+    const size_t nspace = (size_t)(p->nr > p->ns ? p->nr : p->ns);
+    cudaMemsetAsync(p->specA, 0, (size_t)p->nf * nspace * p->nv_cap * sizeof(float2), s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    p->tune[0].clear();
+    p->tune[1].clear();
+    for (int d = 0; d < 2; ++d) {
+        const bool adj = d == 1;
+        for (int n = 1;; n *= 2) {
+            const int ncol = n < ncol_max ? n : ncol_max;
+            struct Cand { int path, bn; };
+            std::vector<Cand> cands;
+            if (ncol <= gemv_max_columns()) cands.push_back({PATH_GEMV, 0});
+            cands.push_back({PATH_SIMT, 0});
+            if (storage_16bit(p->storage) && p->tcB)
+                for (int bn = 32; bn <= 256; bn *= 2)
+                    if (bn / 2 <= 2 * ncol || bn == 32) cands.push_back({PATH_TC, bn});
+            float best = 1e30f;
+            ProductChoice pick{ncol, PATH_AUTO, 0};
+            for (const Cand& c : cands) {
+                if (!launch_product_variant(p, adj, p->specA, ncol, 0, p->specB, ncol, 0, ncol, s, c.path, c.bn))
+                    continue;
+                float t[3];
+                for (int r = 0; r < 3; ++r) {
+                    cudaEventRecord(e0, s);
+                    launch_product_variant(p, adj, p->specA, ncol, 0, p->specB, ncol, 0, ncol, s, c.path, c.bn);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&t[r], e0, e1);
+                }
+                const float med = t[0] < t[1] ? (t[1] < t[2] ? t[1] : (t[0] < t[2] ? t[2] : t[0]))
+                                              : (t[0] < t[2] ? t[0] : (t[1] < t[2] ? t[2] : t[1]));
+                if (med < best) {
+                    best = med;
+                    pick = ProductChoice{ncol, c.path, c.bn};
+                }
+            }
+            p->tune[d].push_back(pick);
+            if (ncol >= ncol_max) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        p->tune[0].clear();
+        p->tune[1].clear();
+        return MDC_ERR_CUDA;
+    }
+    tune_store(p, key, ncol_max);
+    return MDC_OK;
 }
 
 }  // namespace mdc

@@ -34,6 +34,10 @@ namespace {
 constexpr int TC_THREADS = 192;
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
+// Split format: reduction stages per tensor-core accumulation chunk.  Each chunk's partial sum is
+// added into float32 registers by the epilogue (round to nearest), so the tensor core's own
+// accumulation spans at most TC_KCHUNK * TC_BK products per output.
+constexpr int TC_KCHUNK = 4;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -236,14 +240,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             long g = 0;
-            int i = 0;
+            long i = 0;                 // accumulation chunks issued (one per tile unless SPLIT)
             bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
-                const int buf = i & 1;
-                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) break;
+            const int kc = SPLIT ? TC_KCHUNK : a.kstages;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
+              for (int kb0 = 0; kb0 < a.kstages && ok; kb0 += kc, ++i) {
+                const int buf = (int)(i & 1);
+                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * BN);
-                for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+                const int kb1 = kb0 + kc < a.kstages ? kb0 + kc : a.kstages;
+                for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
                         ok = false;
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint32_t lbo = ADJ ? A_BYTES / 2 : 16;
                         const uint64_t ad = sdesc(sa + ao, lbo, 1024);
                         const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
-                        umma_f16(d, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                        umma_f16(d, ad, bd, idesc, ((kb - kb0) | kk) != 0 ? 1u : 0u);
                         if (SPLIT) {
                             // hi*lo + lo*hi: the dropped lo*lo term is below 2^-22 relative
                             umma_f16(d, ad, sdesc(sb2 + kk * 32, 16, 1024), idesc, 1u);
@@ -269,24 +279,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     umma_commit(empty0 + 8 * s);
                 }
                 umma_commit(accf0 + 8 * buf);
-            }
+              }
         }
     } else {
         const int q = warp & 3;
         const int row = q * 32 + lane;
-        int i = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-            const int buf = i & 1;
-            if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) break;
-            tc_fence_after();
+        long i = 0;                     // accumulation chunks consumed
+        const int nch = SPLIT ? (a.kstages + TC_KCHUNK - 1) / TC_KCHUNK : 1;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             const int k = tile / per_freq, rem = tile - k * per_freq;
             const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
             const float* sig = a.sigma + (size_t)k * a.ncol;
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(taddr + c0, v);
+            // store 16 accumulator columns c0.. of this thread's row
+            auto emit = [&](int c0, const float* v) {
                 const int nb = (n0 + c0) >> 1;
                 if (!ADJ) {
                     const int r = m0 + row;
@@ -298,14 +303,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int n = nb + j;
                             if (n < a.ncol) {
                                 const float f = gs / sig[n];
-                                dst[n] = make_float2(__uint_as_float(v[2 * j]) * f, __uint_as_float(v[2 * j + 1]) * f);
+                                dst[n] = make_float2(v[2 * j] * f, v[2 * j + 1] * f);
                             }
                         }
                     }
                 } else {
                     float p[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) p[j] = __shfl_xor_sync(0xffffffffu, __uint_as_float(v[j]), 1);
+                    for (int j = 0; j < 16; ++j) p[j] = __shfl_xor_sync(0xffffffffu, v[j], 1);
                     const int sidx = (m0 + row) >> 1;
                     if ((lane & 1) == 0 && sidx < a.nout) {
                         float2* dst = a.out + ((size_t)k * a.nout + sidx) * a.ldo + a.voff_o;
@@ -314,16 +319,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int n = nb + j;
                             if (n < a.ncol) {
                                 const float f = 1.f / sig[n];
-                                const float re = __uint_as_float(v[2 * j]) + p[2 * j + 1];
-                                const float im = __uint_as_float(v[2 * j + 1]) - p[2 * j];
+                                const float re = v[2 * j] + p[2 * j + 1];
+                                const float im = v[2 * j + 1] - p[2 * j];
                                 dst[n] = make_float2(re * f, im * f);
                             }
                         }
                     }
                 }
+            };
+            bool ok = true;
+            if constexpr (SPLIT) {
+                // sum the chunks' partial accumulators in float32 registers, then store
+                float acc[BN];
+#pragma unroll
+                for (int c = 0; c < BN; ++c) acc[c] = 0.f;
+                for (int ch = 0; ch < nch; ++ch, ++i) {
+                    const int buf = (int)(i & 1);
+                    if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += 16) {
+                        uint32_t v[16];
+                        tmem_ld16(taddr + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(acce0 + 8 * buf);
+                }
+                if (!ok) break;
+#pragma unroll
+                for (int c0 = 0; c0 < BN; c0 += 16) emit(c0, acc + c0);
+            } else {
+                const int buf = (int)(i & 1);
+                if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) break;
+                tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr + c0, v);
+                    float f[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
+                    emit(c0, f);
+                }
+                tc_fence_before();
+                mbar_arrive(acce0 + 8 * buf);
+                ++i;
             }
-            tc_fence_before();
-            mbar_arrive(acce0 + 8 * buf);
         }
     }
     tc_fence_before();
@@ -542,11 +590,14 @@ bool tc_supported(const mdc_plan* p, int ncol) {
 
 // Per-frequency product on tensor cores; returns false if it could not be launched.
 bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
-                       int voff_o, int ncol, cudaStream_t s, const int* active) {
+                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override) {
     const bool bf16 = p->storage == MDC_CBF16;
     const bool split = p->storage == MDC_C32S;
-    const int rows_pad = tc_rows_pad(ncol);
-    const int bn = pick_bn(2 * ncol);
+    int bn = bn_override ? bn_override : pick_bn(2 * ncol);
+    if (split && bn > 128) bn = 128;   // the split epilogue keeps a BN-wide float32 row in registers
+    if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return false;
+    const int rows_pad = (2 * ncol + bn - 1) / bn * bn;
+    if (rows_pad > tc_rows_pad(p->tc_cap)) return false;
     const int kpitch = (int)round_up(p->nr, 8);
     const uint64_t kp = 2 * (uint64_t)p->ldg;
     // B operand (and its lo half for the split format, one plane further)
@@ -617,8 +668,9 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
 #define MDC_TC_CASE(BNV)                                                                   \
     case BNV:                                                                              \
         if (split) {                                                                       \
-            if (adjoint) launch_tc<true, BNV, true>(maps, a, idesc, grid, s, active);      \
-            else launch_tc<false, BNV, true>(maps, a, idesc, grid, s, active);             \
+            constexpr int BS = BNV > 128 ? 128 : BNV;                                      \
+            if (adjoint) launch_tc<true, BS, true>(maps, a, idesc, grid, s, active);       \
+            else launch_tc<false, BS, true>(maps, a, idesc, grid, s, active);              \
         } else {                                                                           \
             if (adjoint) launch_tc<true, BNV, false>(maps, a, idesc, grid, s, active);     \
             else launch_tc<false, BNV, false>(maps, a, idesc, grid, s, active);            \

@@ -62,6 +62,29 @@ def grid_xy(n_side: int, dx: float = GRID_DX):
     return np.stack([ix * dx, iy * dx], axis=1).astype(np.float64)
 
 
+def irregular_subset(n_side: int, fraction: float = 0.5, seed: int = 0):
+    """Sorted flat indices of a random subset of the n_side x n_side grid (an irregular geometry,
+    as in the paper's example that keeps half of the regular sources and receivers)."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 7919 + seed))
+    n = n_side * n_side
+    return np.sort(rng.choice(n, size=max(1, int(round(fraction * n))), replace=False))
+
+
+def voronoi_areas(xy: np.ndarray, lo: float, hi: float, res: int = 2048):
+    """Areal extent of each point's Voronoi cell inside the square [lo, hi]^2 (m^2), from a
+    res x res raster of cell centres assigned to their nearest point.  Input weights for the
+    spatial integration of irregular geometries; they sum to (hi - lo)^2."""
+    xy = np.asarray(xy, np.float64)
+    h = (hi - lo) / res
+    c = lo + h * (np.arange(res) + 0.5)
+    counts = np.zeros(len(xy), np.int64)
+    for r0 in range(0, res, 64):                  # rows of the raster in blocks
+        px, py = np.meshgrid(c, c[r0:r0 + 64], indexing="xy")
+        d2 = (px[..., None] - xy[:, 0]) ** 2 + (py[..., None] - xy[:, 1]) ** 2
+        counts += np.bincount(np.argmin(d2, axis=-1).ravel(), minlength=len(xy))
+    return counts * h * h
+
+
 def signed_time_index(nt: int):
     """Signed circular time sample tau(t) = t for t < nt/2, else t - nt."""
     t = np.arange(nt)
@@ -211,6 +234,32 @@ def kernel(cfg: Config, d: Optional[Draw] = None, ks=None, rows=None, cols=None)
         ph = np.exp(-2j * np.pi * cyc)                      # [E, R, S]
         out[ik] = W[ik] * np.tensordot(d.amp, ph, axes=(0, 0))
     return out * d.scale
+
+
+def kernel_between(cfg: Config, d: Draw, xy_rows, xy_cols, ks=None):
+    """The hyperbolic-event formula of ``kernel`` between two point sets [nr, 2] and [ns, 2] (m),
+    e.g. surface receivers x_S by focusing points x_F for a stand-in down-going Green's
+    function G+ of Eq. 8; complex128 [len(ks), nr, ns]."""
+    ks = np.arange(cfg.nf) if ks is None else np.asarray(ks)
+    xr = np.asarray(xy_rows, np.float64)
+    xs = np.asarray(xy_cols, np.float64)
+    d2 = ((xr[:, None, :] - xs[None, :, :]) ** 2).sum(-1)
+    tau = np.sqrt(d.t0[:, None, None] ** 2 + d2[None] / (d.vel[:, None, None] ** 2))
+    f = ks.astype(np.float64) / (cfg.nt * cfg.dt)
+    W = ricker_spectrum(f)
+    out = np.zeros((len(ks), len(xr), len(xs)), dtype=np.complex128)
+    for ik in range(len(ks)):
+        cyc = f[ik] * tau
+        cyc = cyc - np.rint(cyc)
+        out[ik] = W[ik] * np.tensordot(d.amp, np.exp(-2j * np.pi * cyc), axes=(0, 0))
+    return out * d.scale
+
+
+def focus_lattice(n: int, spacing: float, centre: float):
+    """n x n focusing points [n*n, 2] (m) on a square lattice centred at (centre, centre)."""
+    off = centre - 0.5 * spacing * (n - 1)
+    i = np.arange(n * n)
+    return np.stack([off + spacing * (i % n), off + spacing * (i // n)], axis=1).astype(np.float64)
 
 
 # --------------------------------------------------------------------------- inputs

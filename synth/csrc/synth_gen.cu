@@ -71,3 +71,63 @@ extern "C" int synth_kernel_c64(void* G, int nf, int n_side, double dx, double d
     if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
     return 0;
 }
+
+// Rectangular variant: rows and columns are arbitrary point sets (x, y in m), e.g. surface
+// receivers by subsurface focusing points for the down-going Green's function of Eq. 8.
+__global__ void synth_kernel_rect(float2* __restrict__ G, SynthParams P, int nr, int ns,
+                                  const double* __restrict__ xr, const double* __restrict__ xs) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nr * ns) return;
+    const int64_t r = idx / ns, s = idx - r * ns;
+    const double ddx = xr[2 * r] - xs[2 * s], ddy = xr[2 * r + 1] - xs[2 * s + 1];
+    const double d2 = ddx * ddx + ddy * ddy;
+    double step[SYNTH_MAX_EVENTS], cur[SYNTH_MAX_EVENTS];
+    for (int e = 0; e < P.E; ++e) {
+        const double tau = sqrt(P.t0[e] * P.t0[e] + d2 / (P.vel[e] * P.vel[e]));
+        const double ph = P.df * tau;
+        step[e] = ph - floor(ph);
+        cur[e] = 0.0;
+    }
+    for (int k = 0; k < P.nf; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int e = 0; e < P.E; ++e) {
+            float sn, cs;
+            const double c = cur[e] - rint(cur[e]);
+            sincospif((float)(2.0 * c), &sn, &cs);
+            re += P.amp[e] * (double)cs;
+            im -= P.amp[e] * (double)sn;
+            double nx = cur[e] + step[e];
+            cur[e] = nx >= 1.0 ? nx - 1.0 : nx;
+        }
+        const double w = c_wscale[k];
+        G[((int64_t)k * nr + r) * ns + s] = make_float2((float)(w * re), (float)(w * im));
+    }
+}
+
+extern "C" int synth_kernel_rect_c64(void* G, int nf, int nr, int ns, const double* xy_rows, const double* xy_cols,
+                                     double df, int E, const double* t0, const double* vel, const double* amp,
+                                     const double* wscale, void* stream) {
+    if (!G || !xy_rows || !xy_cols || nf < 1 || nf > SYNTH_MAX_NF || nr < 1 || ns < 1 || E < 1 ||
+        E > SYNTH_MAX_EVENTS)
+        return -1;
+    SynthParams P{};
+    P.nf = nf; P.n_side = 0; P.E = E; P.dx = 0.0; P.df = df;
+    for (int e = 0; e < E; ++e) { P.t0[e] = t0[e]; P.vel[e] = vel[e]; P.amp[e] = amp[e]; }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *xr = nullptr, *xs = nullptr;
+    if (cudaMalloc(&xr, sizeof(double) * 2 * nr) != cudaSuccess) return -2;
+    if (cudaMalloc(&xs, sizeof(double) * 2 * ns) != cudaSuccess) { cudaFree(xr); return -2; }
+    int st = 0;
+    if (cudaMemcpyAsync(xr, xy_rows, sizeof(double) * 2 * nr, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(xs, xy_cols, sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_wscale, wscale, sizeof(double) * nf, 0, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = -3;
+    if (st == 0) {
+        const int64_t total = (int64_t)nr * ns;
+        synth_kernel_rect<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((float2*)G, P, nr, ns, xr, xs);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = -3;
+    }
+    cudaFree(xr);
+    cudaFree(xs);
+    return st;
+}

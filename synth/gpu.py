@@ -30,6 +30,9 @@ def _load():
         L.synth_kernel_c64.restype = ctypes.c_int
         L.synth_kernel_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
+        L.synth_kernel_rect_c64.restype = ctypes.c_int
+        L.synth_kernel_rect_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
+                                            ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -72,3 +75,25 @@ def focusing_inputs_on_device(cfg: synth.Config, points: np.ndarray, device="cud
         q = a2 * arg * arg
         fd[t0:t0 + 64] = ((1.0 - 2.0 * q) * torch.exp(-q)).to(torch.float32)
     return cut, fd
+
+
+def rect_kernel_on_device(cfg: synth.Config, xy_rows: np.ndarray, xy_cols: np.ndarray, d: synth.Draw = None,
+                          device="cuda") -> torch.Tensor:
+    """complex64 G[nf, len(xy_rows), len(xy_cols)] on the device: the formula of ``synth.kernel_between``
+    (the event draws of cfg) between two point sets."""
+    if d is None:
+        d = synth.draw(cfg)
+    L = _load()
+    xr = np.ascontiguousarray(xy_rows, np.float64)
+    xs = np.ascontiguousarray(xy_cols, np.float64)
+    out = torch.empty((cfg.nf, len(xr), len(xs)), dtype=torch.complex64, device=device)
+    ws = np.ascontiguousarray(synth.ricker_spectrum(cfg.freqs) * d.scale, dtype=np.float64)
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (d.t0, d.vel, d.amp)]
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = L.synth_kernel_rect_c64(ctypes.c_void_p(out.data_ptr()), cfg.nf, len(xr), len(xs), dp(xr), dp(xs),
+                                 1.0 / (cfg.nt * cfg.dt), len(arrs[0]), dp(arrs[0]), dp(arrs[1]), dp(arrs[2]),
+                                 dp(ws), stream)
+    if st != 0:
+        raise RuntimeError(f"synth_kernel_rect_c64 failed ({st})")
+    return out

@@ -171,3 +171,33 @@ def test_marchenko_graph_replay_matches_direct_solve():
     m.mdc_set_option(op.h, m.MDC_OPT_GRAPHS, 0)
     op.close()
     ref.close()
+
+
+@pytest.mark.parametrize("niter", [0, 1, 6])
+def test_marchenko_neumann_matches_oracle(niter):
+    """Neumann series of Eq. 5 against the oracle's partial sum; niter = 0 gives the
+    single-scattering Green's functions g0- = R f_d+ (f = 0 in Eq. 6)."""
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(5, 128, 40, 2, 200.0)
+    op_o = omar.Marchenko(G, cfg.dt, cfg.dr, cut, cfg.nt)
+    d = op_o.data(fd)
+    apply_N = lambda x: solvers.lincomb(1.0, x, -1.0, op_o.matvec(x))  # noqa: E731  N = I - M
+    if niter == 0:
+        x = [np.zeros_like(d[0]), np.zeros_like(d[1])]
+    else:
+        x = solvers.neumann(apply_N, d, niter)
+    gm, _, gp = op_o.greens(x[0], x[1], fd)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    out = op.neumann(torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda(), niter)
+    op.close()
+    if niter == 0:
+        assert float(out["f_minus"].abs().max()) == 0.0 and float(out["f_mplus"].abs().max()) == 0.0
+        assert rel(out["g_minus"].cpu().numpy(), op_o.R(fd)) <= TOL
+    else:
+        assert rel(out["f_minus"].cpu().numpy(), x[0]) <= TOL
+        if niter == 1:                  # x = d = [Theta R f_d+; 0]
+            assert float(out["f_mplus"].abs().max()) == 0.0
+        else:
+            assert rel(out["f_mplus"].cpu().numpy(), x[1]) <= TOL
+    assert rel(out["g_minus"].cpu().numpy(), gm) <= TOL
+    assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL

@@ -174,3 +174,83 @@ def test_server_retires_a_non_finite_job_alone(small):
     finally:
         m.srv_destroy(srv)
     op.close()
+
+
+@pytest.mark.parametrize("storage,nref", [("c64", 0), ("c16f", 1)])
+def test_checkpoint_resume_continues_bit_for_bit(small, storage, nref):
+    """A server checkpointed mid-flight (jobs running, one still queued) and resumed on a new
+    server finishes with the same outputs, iteration counts and residuals as the uninterrupted
+    server, bit for bit; resumed jobs wait for srv_bind; a checkpoint does not fit a server of
+    another kernel shape."""
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    jobs = make_jobs(cfg, G, [(3, 12, 0.0), (2, 9, 0.0), (4, 10, 1e-4)], seed=5)
+    Gt = torch.from_numpy(G.astype(np.complex64)).cuda()
+    op = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage=storage)
+    ref = m.MDC(Gt, cfg.nt, cfg.dt, cfg.dr, storage="c64") if nref else None
+    niter_ref = 3 if nref else 0
+    max_cols = 12   # jobs 0 and 1 run together (10 columns); job 2 (8 columns) waits in the queue
+
+    def submit_all(srv):
+        outs, ids = [], []
+        for job in jobs:
+            o = outputs(cfg, job["nv"])
+            outs.append(o)
+            ids.append(m.srv_submit(srv, job["cut"], job["fd"], job["nv"], job["niter"], job["tol"], o))
+        return outs, ids
+
+    def drain(srv, ids):
+        for _ in range(500):
+            if all(m.srv_poll(srv, i)["state"] == m.JOB_DONE for i in ids):
+                return {i: m.srv_poll(srv, i) for i in ids}
+            m.srv_step(srv)
+        raise AssertionError("server did not drain")
+
+    srv = m.srv_create(op.h, ref.h if ref else None, 1 << 34, max_cols, nref, niter_ref)
+    outs_a, ids_a = submit_all(srv)
+    polls_a = drain(srv, ids_a)
+    m.srv_destroy(srv)
+
+    srv = m.srv_create(op.h, ref.h if ref else None, 1 << 34, max_cols, nref, niter_ref)
+    outs_b, ids_b = submit_all(srv)
+    for _ in range(5):
+        m.srv_step(srv)
+    st = m.srv_stats(srv)
+    assert st["running"] == 2 and st["queued"] == 1
+    blob = m.srv_checkpoint(srv)
+    m.srv_destroy(srv)                       # the first server is gone: its host buffers are not reused
+
+    srv = m.srv_create(op.h, ref.h if ref else None, 1 << 34, max_cols, nref, niter_ref)
+    try:
+        got = m.srv_resume(srv, blob)
+        assert got == ids_b
+        with pytest.raises(m.MDCError):
+            m.srv_step(srv)                  # no outputs bound yet
+        outs_c = [outputs(cfg, job["nv"]) for job in jobs]
+        for i, o in zip(got, outs_c):
+            m.srv_bind(srv, i, o)
+        polls_c = drain(srv, got)
+        with pytest.raises(m.MDCError):
+            m.srv_resume(srv, blob)          # ids already known to this server
+    finally:
+        m.srv_destroy(srv)
+    for q, (ia, ic) in enumerate(zip(ids_a, got)):
+        assert polls_c[ic]["iters"] == polls_a[ia]["iters"]
+        assert polls_c[ic]["final_residual"] == polls_a[ia]["final_residual"]
+        for k in range(4):
+            assert np.array_equal(outs_c[q][k], outs_a[q][k]), (q, k)
+
+    other = m.MDC(torch.zeros((cfg.nf, 9, 9), dtype=torch.complex64, device="cuda"), cfg.nt, cfg.dt, cfg.dr,
+                  storage=storage)
+    srv = m.srv_create(other.h, None, 1 << 34, max_cols, 0, 0)
+    try:
+        with pytest.raises(m.MDCError):
+            m.srv_resume(srv, blob)
+        with pytest.raises(m.MDCError):
+            m.srv_resume(srv, b"not a checkpoint" * 4)
+    finally:
+        m.srv_destroy(srv)
+    other.close()
+    op.close()
+    if ref:
+        ref.close()
