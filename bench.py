@@ -55,6 +55,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha(kernel_file):
+    """sha256 of the complex64 GEMV kernels' source text (between their begin/end markers)."""
+    src = open(os.path.join(ROOT, "paper_2011_11120_gb300", "csrc", kernel_file)).read()
+    a = src.index("// ---- complex64 GEMV kernels (begin)")
+    b = src.index("// ---- complex64 GEMV kernels (end)")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
 def profile_traffic(kernel_file):
     """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "product_gemv_c64_3721x3721_nf200_nv1.json")
@@ -62,8 +70,7 @@ def profile_traffic(kernel_file):
         return None
     with open(path) as fh:
         prof = json.load(fh)
-    src = open(os.path.join(ROOT, "paper_2011_11120_gb300", "csrc", kernel_file), "rb").read()
-    if prof.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    if prof.get("source_sha256") != kernel_source_sha(kernel_file):
         return None
     return prof.get("dram_bytes_per_launch")
 
@@ -160,13 +167,42 @@ def cpu_baseline(cfg, nv, min_seconds=10.0, rows=32):
             "seconds": el}
 
 
+def paper_style_cpu(cfg, nv, nslices=4, min_seconds=5.0):
+    """The paper's CPU formulation on the host cores: NumPy complex64 matmul per frequency slice
+    (forward G x and adjoint G^H y) with NumPy real FFTs of the traces, on `nslices` full
+    frequency slices of the workload's shape (random complex64 values: the timing does not depend
+    on them); context beside the oracle, not a target."""
+    rng = np.random.default_rng(12)
+    G = (rng.standard_normal((nslices, cfg.nr, cfg.ns), dtype=np.float32)
+         + 1j * rng.standard_normal((nslices, cfg.nr, cfg.ns), dtype=np.float32)).astype(np.complex64)
+    x = rng.standard_normal((cfg.nt, cfg.ns, nv), dtype=np.float32)
+    y = rng.standard_normal((cfg.nt, cfg.nr, nv), dtype=np.float32)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        X = np.fft.rfft(x, axis=0)[:nslices].astype(np.complex64)
+        Y = np.fft.rfft(y, axis=0)[:nslices].astype(np.complex64)
+        yo = np.matmul(G, X)
+        xo = np.matmul(np.conj(np.swapaxes(G, 1, 2)), Y)
+        np.fft.irfft(yo, n=cfg.nt, axis=0)
+        np.fft.irfft(xo, n=cfg.nt, axis=0)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    bytes_per_rep = 2 * nslices * cfg.nr * cfg.ns * 8
+    return {"value": bytes_per_rep * reps / el / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "paper-style NumPy (complex64 matmul per frequency + NumPy FFT)",
+            "sample": f"{nslices} of {cfg.nf} frequency slices ({cfg.nr}x{cfg.ns}, nv={nv}), forward and "
+                      f"adjoint, {reps} repetitions in {el:.1f} s; bytes = complex64 kernel bytes of the slices"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     cfg = synth.config(args.config, nv=args.nv)
     if args.nf:
-        cfg = cfg.with_(nf=args.nf)
+        cfg = cfg.with_(nf=args.nf, normalise=False)   # profiling case: normalisation not needed
     from oracle import mdc as omdc
     d = synth.draw(cfg)
     rows = 8
@@ -264,8 +300,9 @@ def run_redatum(args, dev):
 def run_mdd(args, dev):
     """Multi-dimensional deconvolution (Eq. 8): a stand-in down-going Green's function G+ between
     the 61 x 61 surface grid and a 29 x 29 lattice of focusing points (nt=1024, nfmax=200), one
-    batch of 20 virtual sources per LSQR solve, complex64 (FP32 SIMT products) and FP16 (tensor
-    cores) kernel copies; the FP16 result is compared with the complex64 one."""
+    batch of 20 virtual sources per LSQR solve, with complex64 (FP32 SIMT products), split FP16
+    (float32-accurate tensor-core products) and FP16 (tensor cores) kernel copies; the tensor-core
+    results are compared with the complex64 one."""
     import torch
     import paper_2011_11120_gb300 as mdc
     from synth import gpu as sgpu
@@ -279,7 +316,7 @@ def run_mdd(args, dev):
     g = torch.randn((cfg.nt, cfg.nr, nv), generator=gen, device=dev, dtype=torch.float32)
     out = {}
     sol = {}
-    for storage in ("c64", "c16f"):
+    for storage in ("c64", "c32s", "c16f"):
         op = mdc.MDC(Gp, cfg.nt, cfg.dt, cfg.dr, storage=storage)
         r = op.mdd(g, niter)                               # warm-up
         torch.cuda.synchronize()
@@ -298,8 +335,9 @@ def run_mdd(args, dev):
                         "tflops_products": 8.0 * cfg.nf * cfg.nr * len(xs) * nv * n_mdc / med / 1e12}
     del Gp
     torch.cuda.empty_cache()
-    a, b = sol["c16f"].double(), sol["c64"].double()
-    out["c16f"]["rel_l2_vs_c64"] = float((a - b).norm() / b.norm())
+    b = sol["c64"].double()
+    for storage in ("c32s", "c16f"):
+        out[storage]["rel_l2_vs_c64"] = float((sol[storage].double() - b).norm() / b.norm())
     out["workload"] = (f"MDD (Eq. 8) by LSQR, G+ {cfg.nr} receivers (61x61, 20 m) x {len(xs)} focusing points "
                        f"(29x29, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, {cfg.n_events} hyperbolic events, "
                        f"{nv} virtual sources per batch, {niter} iterations")
@@ -453,7 +491,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     cfg = synth.config(args.config, nv=args.nv)
     if args.nf:
-        cfg = cfg.with_(nf=args.nf)
+        cfg = cfg.with_(nf=args.nf, normalise=False)   # profiling case: normalisation not needed
     nv = args.nv
     d = synth.draw(cfg)
     G = sgpu.kernel_on_device(cfg, d)
@@ -559,6 +597,7 @@ def run_ours(args):
         result["serving"] = run_serving(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
+        result["cpu_baseline"]["paper_style"] = paper_style_cpu(cfg, nv)
     print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -207,6 +207,31 @@ __constant__ float2 kRoot32[16] = {
     MDC_ROOT32(12), MDC_ROOT32(13), MDC_ROOT32(14), MDC_ROOT32(15)};
 #undef MDC_ROOT32
 
+// Complex add and subtract as one packed two-lane float32 instruction (sm_100 and later);
+// each lane rounds to nearest like the scalar operation.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pr, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pr;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pr;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // Length-R DFT (R <= 32) of a register array, forward sign exp(-2 pi i n k / R) or, with INV,
 // the inverse sign (unscaled): decimation in frequency (natural order in, bit-reversed order
 // out), then a compile-time permutation back to natural order.  After unrolling every index
@@ -225,8 +250,8 @@ __device__ __forceinline__ void reg_fft(float2 (&a)[R]) {
 #pragma unroll
             for (int j = 0; j < h; ++j) {
                 const float2 u = a[g + j], v = a[g + j + h];
-                a[g + j] = cadd(u, v);
-                float2 d = csub(u, v);
+                a[g + j] = padd(u, v);
+                float2 d = psub(u, v);
                 const int m = j << st;       // twiddle exp(-+2 pi i m / R)
                 if (m == 0) {
                 } else if (4 * m == R) {
@@ -263,7 +288,9 @@ template <int N1, int N2> struct FourStep {
     static constexpr int RS = P;
     static constexpr int BP = P == 8 ? 8 : 0;
     static constexpr int ZSIZE = NT * RS + N1 * BP;                  // float2 elements
-    static constexpr size_t smem = (size_t)(NT / 2 + ZSIZE) * sizeof(float2) + FFT_THREADS * 32;
+    // twiddle table and tile; the inverse transform's column-sum reduction reuses the tile
+    static constexpr size_t smem = (size_t)(NT / 2 + ZSIZE) * sizeof(float2);
+    static_assert(ZSIZE * sizeof(float2) >= FFT_THREADS * 4 * sizeof(double), "reduction fits the tile");
     __device__ static __forceinline__ int zi(int t, int j) { return t * RS + (t / N2) * BP + j; }
 };
 
@@ -306,7 +333,7 @@ template <int N1, int N2>
 __device__ __forceinline__ int out_row(int q) { return (q % N1) * N2 + q / N1; }
 
 template <int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
+__global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     using F = FourStep<N1, N2>;
     constexpr int NT = F::NT, CT = F::CT;
     if (a.active && *a.active == 0) return;
@@ -326,33 +353,37 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
         reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v * sc;
     };
     if (a.vec4 && c0 + CT <= a.C) {
-        constexpr int Q = CT / 4, PER = NT * Q / FFT_THREADS, B = PER < 16 ? PER : 16;
+        // each thread keeps the same four columns (FFT_THREADS is a multiple of Q) and walks
+        // rows t0, t0 + TSTEP, ...
+        constexpr int Q = CT / 4, TSTEP = FFT_THREADS / Q, PER = NT / TSTEP, B = PER < 16 ? PER : 16;
+        const int cl = 4 * (threadIdx.x % Q), t0 = threadIdx.x / Q;
+        int cut[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+        if (a.cut)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cut[i] = a.cut[c0 + cl + i];
+        const float* xb = a.x + c0 + cl;
+        const float* x2b = a.x2 ? a.x2 + c0 + cl : nullptr;
 #pragma unroll 1
         for (int b0 = 0; b0 < PER; b0 += B) {
             float4 v[B];
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int q = threadIdx.x + (b0 + u) * FFT_THREADS;
-                const size_t off = (size_t)(q / Q) * a.C + c0 + 4 * (q % Q);
-                v[u] = *reinterpret_cast<const float4*>(a.x + off);
-                if (a.x2) {
-                    const float4 w = *reinterpret_cast<const float4*>(a.x2 + off);
+                const size_t off = (size_t)(t0 + (b0 + u) * TSTEP) * a.C;
+                v[u] = *reinterpret_cast<const float4*>(xb + off);
+                if (x2b) {
+                    const float4 w = *reinterpret_cast<const float4*>(x2b + off);
                     v[u].x += w.x; v[u].y += w.y; v[u].z += w.z; v[u].w += w.w;
                 }
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int q = threadIdx.x + (b0 + u) * FFT_THREADS;
-                const int t = q / Q, cl = 4 * (q % Q), c = c0 + cl;
+                const int t = t0 + (b0 + u) * TSTEP;
+                const int tau = t < (NT >> 1) ? t : NT - t;
                 float4 w = v[u];
-                if (a.cut) {
-                    const int tau = t < (NT >> 1) ? t : NT - t;
-                    if (tau >= a.cut[c]) w.x = 0.f;
-                    if (tau >= a.cut[c + 1]) w.y = 0.f;
-                    if (tau >= a.cut[c + 2]) w.z = 0.f;
-                    if (tau >= a.cut[c + 3]) w.w = 0.f;
-                }
-                w.x *= sc; w.y *= sc; w.z *= sc; w.w *= sc;
+                w.x = tau >= cut[0] ? 0.f : w.x * sc;
+                w.y = tau >= cut[1] ? 0.f : w.y * sc;
+                w.z = tau >= cut[2] ? 0.f : w.z * sc;
+                w.w = tau >= cut[3] ? 0.f : w.w * sc;
                 *reinterpret_cast<float4*>(z + F::zi(t, cl >> 1)) = w;
             }
         }
@@ -383,46 +414,51 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft4_kernel(RfftArgs a) {
     }
     __syncthreads();
     four_step<N1, N2, false>(z, tw);
-    // Bins k < nf sit in rows rho = k1 * N2 + k2 (k = k1 + N1 * k2): the first ceil((nf - k1) / N1)
-    // rows of each block k1.  Walk them in storage order so a warp reads consecutive rows.
-    const int qn = a.nf / N1, rn = a.nf % N1;
-    const bool same_s = (a.nv % CT) == 0;
-    const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
-    for (int idx = threadIdx.x; idx < a.nf * CT; idx += FFT_THREADS) {
-        const int ir = idx / CT, cl = idx % CT, c = c0 + cl;
-        if (c >= a.C) continue;
-        int k1, k2;
-        if (ir < rn * (qn + 1)) {
-            k1 = ir / (qn + 1);
-            k2 = ir % (qn + 1);
+    // Bin k = k1 + N1 * k2 sits in row k1 * N2 + k2, its mirror NT - k in row
+    // ((-k1) mod N1) * N2 + (NT/N1 - k2 - [k1 > 0]) (k > 0).  A thread keeps one column and walks
+    // the bins of every G-th block k1; the G threads of a column cover all N1 blocks, and the
+    // CT threads of one row write CT adjacent columns.
+    constexpr int G = FFT_THREADS / CT;
+    const int cl = threadIdx.x % CT, g = threadIdx.x / CT, c = c0 + cl;
+    if (c < a.C) {
+        int s, v;
+        if ((a.nv % CT) == 0) {               // every column of the tile has the same spatial index
+            s = c0 / a.nv;
+            v = c0 - s * a.nv + cl;
         } else {
-            const int i2 = ir - rn * (qn + 1);
-            k1 = rn + i2 / qn;
-            k2 = i2 % qn;
+            s = c / a.nv;
+            v = c - s * a.nv;
         }
-        const int k = k1 + N1 * k2;
+        float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
+        const size_t kstride = (size_t)a.S * a.ldv;
         const int j = cl >> 1;
-        const float2 Z = z[F::zi(k1 * N2 + k2, j)];
-        const float2 Zm = z[F::zi(out_row<N1, N2>((NT - k) & (NT - 1)), j)];
-        float2 r;
-        if ((cl & 1) == 0) r = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
-        else               r = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
-        if (a.conj) r.y = -r.y;
-        // all columns of the tile share the spatial index s0 when nv is a multiple of CT
-        const int s = same_s ? s0 : c / a.nv, v = same_s ? v0 + cl : c - s * a.nv;
-        a.X[((size_t)k * a.S + s) * a.ldv + a.voff + v] = r;
+        const bool odd = (cl & 1) != 0;
+        for (int k1 = g; k1 < N1 && k1 < a.nf; k1 += G) {
+            const int mk1 = (N1 - k1) & (N1 - 1);
+            const float2* zr = z + F::zi(k1 * N2, j);              // rows k1 * N2 + k2
+            const float2* zm = z + F::zi(mk1 * N2, j);             // rows mk1 * N2 + (...)
+            int mrow2 = NT / N1 - (k1 > 0 ? 1 : 0);                // second index of the mirror row
+            for (int k = k1, k2 = 0; k < a.nf; k += N1, ++k2, --mrow2) {
+                const float2 Z = zr[k2 * F::RS];
+                const float2 Zm = k == 0 ? Z : zm[(mrow2 & (N2 - 1)) * F::RS];
+                float2 r = odd ? make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x))
+                               : make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+                if (a.conj) r.y = -r.y;
+                dst[(size_t)k * kstride] = r;
+            }
+        }
     }
 }
 
 template <int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
+__global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     using F = FourStep<N1, N2>;
     constexpr int NT = F::NT, CT = F::CT, P = F::P;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 sm2[];
     float2* tw = sm2;
     float2* z = sm2 + NT / 2;
-    double* red = reinterpret_cast<double*>(z + F::ZSIZE);
+    double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
     const int c0 = blockIdx.x * CT;
     for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = cconj(a.tw[i]);
     // rows no bin reaches are zero
@@ -537,6 +573,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
             }
         }
         if (a.colsum) {
+            __syncthreads();                             // every thread is done reading the tile
 #pragma unroll
             for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = (double)ss[i];
             __syncthreads();
@@ -583,6 +620,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft4_kernel(IrfftArgs a) {
         }
     }
     if (a.colsum) {
+        __syncthreads();                                 // every thread is done reading the tile
         red[threadIdx.x] = (double)ss;
         __syncthreads();
         if (threadIdx.x < CT && c < a.C) {

@@ -97,6 +97,7 @@ __device__ __forceinline__ void cfma_conj(float2& acc, float2 a, float2 b) {
 
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 
+// ---- complex64 GEMV kernels (begin)
 // complex64 specialisations: one warp per row, X(w) interleaved in shared memory (C64 keeps
 // two complex values per vector, so lanes already read distinct words).
 template <int NVC>
@@ -228,6 +229,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
         if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
     }
 }
+
+// ---- complex64 GEMV kernels (end)
 
 // Forward GEMV.  X(w) is staged de-interleaved by vector lane position:
 // xs[(j * nvec + i) * NVC + v] = X[CPV * i + j][v], so the 32 lanes of a warp, which

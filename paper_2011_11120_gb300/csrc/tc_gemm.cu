@@ -135,7 +135,7 @@ struct TcArgs {
     int nout;           // output rows: nr (forward) or ns (adjoint)
     int nr;             // kernel rows (row-scale stride)
     int ncol;           // complex columns
-    const float* sigma; // [nf][ncol] power-of-two column scales of B
+    const float* inv_sigma; // [nf][ncol] reciprocals of the power-of-two column scales of B
     const float* gscale;// [nf][nr] kernel row scales (forward epilogue)
     float2* out;
     int ldo, voff_o;
@@ -151,7 +151,24 @@ template <int BN, bool SPLIT> struct TcStages {
 
 template <int BN, bool SPLIT>
 constexpr size_t tc_smem_bytes() {
-    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512;
+    // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and four
+    // 32 x 20-float output staging tiles
+    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512 + 1024 + 4 * 32 * 20 * 4;
+}
+
+// AND of a flag over the 128 epilogue threads (named barrier 2): a failed bounded wait in one
+// thread makes all of them leave together, so the named barriers below never miss a thread.
+__device__ __forceinline__ bool epilogue_all(bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -178,8 +195,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
-    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot, then the epilogue's
+    // double-buffered column scales of the current tile
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    float* sig_s = reinterpret_cast<float*>(bars + 2 * STAGES + 6);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,46 +305,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int row = q * 32 + lane;
         long i = 0;                     // accumulation chunks consumed
         const int nch = SPLIT ? (a.kstages + TC_KCHUNK - 1) / TC_KCHUNK : 1;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int parity = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, parity ^= 1) {
             const int k = tile / per_freq, rem = tile - k * per_freq;
             const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
-            const float* sig = a.sigma + (size_t)k * a.ncol;
-            // store 16 accumulator columns c0.. of this thread's row
+            // this tile's reciprocal column scales (exact: powers of two) into shared memory; the
+            // buffer alternates with the tile parity so the next tile's copy never races a reader
+            float* sgs = sig_s + parity * 128;
+            {
+                const int e = threadIdx.x - 64;
+                const int n = (n0 >> 1) + e;
+                if (e < BN / 2) sgs[e] = n < a.ncol ? a.inv_sigma[(size_t)k * a.ncol + n] : 0.f;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            }
+            const int r = m0 + row;
+            const float gs = (!ADJ && r < a.nout) ? a.gscale[(size_t)k * a.nr + r] : 1.f;
+            // Store 16 accumulator columns c0.. (8 complex output columns) of this warp's 32 rows:
+            // scaled values go through a per-warp staging tile (rows padded to 20 floats, so both
+            // the row-wise writes and the column-wise reads are conflict-free), then each store
+            // instruction writes 8 output rows x 64 contiguous bytes.
+            float* stg = sig_s + 256 + q * (32 * 20);
             auto emit = [&](int c0, const float* v) {
                 const int nb = (n0 + c0) >> 1;
+                float w[16];
                 if (!ADJ) {
-                    const int r = m0 + row;
-                    if (r < a.nout) {
-                        const float gs = a.gscale[(size_t)k * a.nr + r];
-                        float2* dst = a.out + ((size_t)k * a.nout + r) * a.ldo + a.voff_o;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int n = nb + j;
-                            if (n < a.ncol) {
-                                const float f = gs / sig[n];
-                                dst[n] = make_float2(v[2 * j] * f, v[2 * j + 1] * f);
-                            }
-                        }
+                    for (int j = 0; j < 8; ++j) {
+                        const float f = gs * sgs[(c0 >> 1) + j];
+                        w[2 * j] = v[2 * j] * f;
+                        w[2 * j + 1] = v[2 * j + 1] * f;
                     }
                 } else {
-                    float p[16];
+                    // rows 2s and 2s + 1 of the real product hold the two halves of output row s
+                    float pv[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) p[j] = __shfl_xor_sync(0xffffffffu, v[j], 1);
-                    const int sidx = (m0 + row) >> 1;
-                    if ((lane & 1) == 0 && sidx < a.nout) {
-                        float2* dst = a.out + ((size_t)k * a.nout + sidx) * a.ldo + a.voff_o;
+                    for (int j = 0; j < 16; ++j) pv[j] = __shfl_xor_sync(0xffffffffu, v[j], 1);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int n = nb + j;
-                            if (n < a.ncol) {
-                                const float f = 1.f / sig[n];
-                                const float re = v[2 * j] + p[2 * j + 1];
-                                const float im = v[2 * j + 1] - p[2 * j];
-                                dst[n] = make_float2(re * f, im * f);
-                            }
+                    for (int j = 0; j < 8; ++j) {
+                        const float f = sgs[(c0 >> 1) + j];
+                        w[2 * j] = (v[2 * j] + pv[2 * j + 1]) * f;
+                        w[2 * j + 1] = (v[2 * j + 1] - pv[2 * j]) * f;
+                    }
+                }
+                constexpr int NROWS = ADJ ? 16 : 32;
+                const int orow0 = ADJ ? (m0 + 32 * q) >> 1 : m0 + 32 * q;
+                if (!ADJ || (lane & 1) == 0) {
+                    float* rowp = stg + (ADJ ? lane >> 1 : lane) * 20;
+#pragma unroll
+                    for (int i4 = 0; i4 < 4; ++i4)
+                        *reinterpret_cast<float4*>(rowp + 4 * i4) =
+                            make_float4(w[4 * i4], w[4 * i4 + 1], w[4 * i4 + 2], w[4 * i4 + 3]);
+                }
+                __syncwarp();
+                const int cc = lane >> 3, n = nb + 2 * cc;
+#pragma unroll
+                for (int it = 0; it < NROWS / 8; ++it) {
+                    const int rr = (lane & 7) + 8 * it, orow = orow0 + rr;
+                    const float4 val = *reinterpret_cast<const float4*>(stg + rr * 20 + 4 * cc);
+                    if (orow < a.nout && n < a.ncol) {
+                        float2* dst = a.out + ((size_t)k * a.nout + orow) * a.ldo + a.voff_o + n;
+                        if (n + 1 < a.ncol && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                            *reinterpret_cast<float4*>(dst) = val;
+                        } else {
+                            dst[0] = make_float2(val.x, val.y);
+                            if (n + 1 < a.ncol) dst[1] = make_float2(val.z, val.w);
                         }
                     }
                 }
+                __syncwarp();
             };
             bool ok = true;
             if constexpr (SPLIT) {
@@ -335,7 +382,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int c = 0; c < BN; ++c) acc[c] = 0.f;
                 for (int ch = 0; ch < nch; ++ch, ++i) {
                     const int buf = (int)(i & 1);
-                    if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) {
+                    if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) {
                         ok = false;
                         break;
                     }
@@ -356,7 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int c0 = 0; c0 < BN; c0 += 16) emit(c0, acc + c0);
             } else {
                 const int buf = (int)(i & 1);
-                if (!mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4)) break;
+                if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
@@ -391,6 +438,7 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
     if (!(maxabs > 0.f) || !isfinite(maxabs)) return 1.f;
     int e;
     frexpf(maxabs, &e);           // maxabs < 2^e
+    e = e < -100 ? -100 : e;      // scale and reciprocal stay normal floats
     return ldexpf(1.f, 14 - e);   // maxabs * scale < 2^14
 }
 
@@ -398,7 +446,7 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X, int ldi, int voff, int ns,
                                                    int ncol, int ldg, int rows_pad, T* __restrict__ BT,
-                                                   float* __restrict__ sigma, const int* active, size_t plane) {
+                                                   float* __restrict__ inv_sigma, const int* active, size_t plane) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * 8;
     const float2* Xk = X + (size_t)k * ns * ldi + voff;
@@ -418,7 +466,7 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
         for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
         const float sc = pow2_scale(mm);
         sig[threadIdx.x] = sc;
-        if (n0 + (int)threadIdx.x < ncol) sigma[(size_t)k * ncol + n0 + threadIdx.x] = sc;
+        if (n0 + (int)threadIdx.x < ncol) inv_sigma[(size_t)k * ncol + n0 + threadIdx.x] = 1.f / sc;
     }
     __syncthreads();
     const size_t kp = 2 * (size_t)ldg;
@@ -456,7 +504,7 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y, int ldi, int voff, int nr,
                                                    int ncol, const float* __restrict__ gscale, int kpitch,
-                                                   int rows_pad, T* __restrict__ BT, float* __restrict__ sigma,
+                                                   int rows_pad, T* __restrict__ BT, float* __restrict__ inv_sigma,
                                                    const int* active, size_t plane) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * 8;
@@ -478,7 +526,7 @@ __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y,
         for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
         const float sc = pow2_scale(mm);
         sig[threadIdx.x] = sc;
-        if (n0 + (int)threadIdx.x < ncol) sigma[(size_t)k * ncol + n0 + threadIdx.x] = sc;
+        if (n0 + (int)threadIdx.x < ncol) inv_sigma[(size_t)k * ncol + n0 + threadIdx.x] = 1.f / sc;
     }
     __syncthreads();
     T* Bk = BT + (size_t)k * rows_pad * kpitch;
@@ -654,7 +702,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     a.nout = adjoint ? p->ns : p->nr;
     a.nr = p->nr;
     a.ncol = ncol;
-    a.sigma = p->tcSigma;
+    a.inv_sigma = p->tcSigma;
     a.gscale = p->gscale;
     a.out = out;
     a.ldo = ldo;

@@ -42,7 +42,7 @@ def test_weighted_forward_adjoint(storage, tol):
 def test_marchenko_on_irregular_geometry():
     """Half of an 11 x 11 grid kept at random; each receiver integrates over its Voronoi cell."""
     import paper_2011_11120_gb300 as m
-    cfg = synth.Config(96, "irregular", 11, 256, 0.004, 60, 5, 4, 200.0, point_grid=2)
+    cfg = synth.Config(96, "irregular", 11, 256, 0.004, 60, 5, 4, 500.0, point_grid=2)  # window keeps part of R f_d+
     d = synth.draw(cfg)
     idx = synth.irregular_subset(cfg.n_side, 0.5, seed=2)
     xy = synth.grid_xy(cfg.n_side)[idx]
