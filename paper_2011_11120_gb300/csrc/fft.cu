@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
     {
         const int items = a.nf * P;
-        constexpr int B = 8;
+        constexpr int B = 4;
 #pragma unroll 1
         for (int b0 = 0; b0 < items; b0 += B * FFT_THREADS) {
             float2 A[B], Bv[B];
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
     if (a.vec4) {
         // four adjacent columns per thread: 16-byte loads and stores
-        constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, B = PER < 8 ? PER : 8;
+        constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, B = PER < 4 ? PER : 4;
         const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
         const bool want_ss = a.colsum != nullptr;
         float ss[4] = {0.f, 0.f, 0.f, 0.f};   // per-thread partial sums of squares (<= 16 terms)

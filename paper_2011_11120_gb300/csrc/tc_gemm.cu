@@ -31,7 +31,9 @@
 namespace mdc {
 namespace {
 
-constexpr int TC_THREADS = 192;
+// warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: epilogue (two warps per TMEM lane
+// quarter, each taking half of the accumulator columns)
+constexpr int TC_THREADS = 320;
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
 // Split format: reduction stages per tensor-core accumulation chunk.  Each chunk's partial sum is
@@ -151,19 +153,19 @@ template <int BN, bool SPLIT> struct TcStages {
 
 template <int BN, bool SPLIT>
 constexpr size_t tc_smem_bytes() {
-    // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and four
+    // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and eight
     // 32 x 20-float output staging tiles
-    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512 + 1024 + 4 * 32 * 20 * 4;
+    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512 + 1024 + 8 * 32 * 20 * 4;
 }
 
-// AND of a flag over the 128 epilogue threads (named barrier 2): a failed bounded wait in one
+// AND of a flag over the 256 epilogue threads (named barrier 2): a failed bounded wait in one
 // thread makes all of them leave together, so the named barriers below never miss a thread.
 __device__ __forceinline__ bool epilogue_all(bool ok) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 2, 128, p;\n\t"
+        "bar.red.and.pred q, 2, 256, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"((uint32_t)ok)
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(accf0 + 8 * i, 1);
-            mbar_init(acce0 + 8 * i, 128);
+            mbar_init(acce0 + 8 * i, 256);
         }
         fence_mbar_init();
     }
@@ -301,8 +303,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               }
         }
     } else {
-        const int q = warp & 3;
+        const int q = warp & 3;                  // TMEM lane quarter of this warp
         const int row = q * 32 + lane;
+        constexpr int BH = BN / 2;               // accumulator columns per epilogue warp
+        const int cbeg = ((warp - 2) >> 2) * BH;
         long i = 0;                     // accumulation chunks consumed
         const int nch = SPLIT ? (a.kstages + TC_KCHUNK - 1) / TC_KCHUNK : 1;
         int parity = 0;
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int e = threadIdx.x - 64;
                 const int n = (n0 >> 1) + e;
                 if (e < BN / 2) sgs[e] = n < a.ncol ? a.inv_sigma[(size_t)k * a.ncol + n] : 0.f;
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                asm volatile("bar.sync 1, 256;" ::: "memory");
             }
             const int r = m0 + row;
             const float gs = (!ADJ && r < a.nout) ? a.gscale[(size_t)k * a.nr + r] : 1.f;
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // scaled values go through a per-warp staging tile (rows padded to 20 floats, so both
             // the row-wise writes and the column-wise reads are conflict-free), then each store
             // instruction writes 8 output rows x 64 contiguous bytes.
-            float* stg = sig_s + 256 + q * (32 * 20);
+            float* stg = sig_s + 256 + (warp - 2) * (32 * 20);
             auto emit = [&](int c0, const float* v) {
                 const int nb = (n0 + c0) >> 1;
                 float w[16];
@@ -377,9 +381,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = true;
             if constexpr (SPLIT) {
                 // sum the chunks' partial accumulators in float32 registers, then store
-                float acc[BN];
+                float acc[BH];
 #pragma unroll
-                for (int c = 0; c < BN; ++c) acc[c] = 0.f;
+                for (int c = 0; c < BH; ++c) acc[c] = 0.f;
                 for (int ch = 0; ch < nch; ++ch, ++i) {
                     const int buf = (int)(i & 1);
                     if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) {
@@ -389,9 +393,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll
-                    for (int c0 = 0; c0 < BN; c0 += 16) {
+                    for (int c0 = 0; c0 < BH; c0 += 16) {
                         uint32_t v[16];
-                        tmem_ld16(taddr + c0, v);
+                        tmem_ld16(taddr + cbeg + c0, v);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
                     }
@@ -400,14 +404,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (!ok) break;
 #pragma unroll
-                for (int c0 = 0; c0 < BN; c0 += 16) emit(c0, acc + c0);
+                for (int c0 = 0; c0 < BH; c0 += 16) emit(cbeg + c0, acc + c0);
             } else {
                 const int buf = (int)(i & 1);
                 if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 16) {
+                for (int c0 = cbeg; c0 < cbeg + BH; c0 += 16) {
                     uint32_t v[16];
                     tmem_ld16(taddr + c0, v);
                     float f[16];
