@@ -512,7 +512,10 @@ def run_ours(args):
     del G
     torch.cuda.empty_cache()
     mdc.mdc_reserve(op.h, nv)
-    x_host = torch.from_numpy(synth.ricker_traces(cfg, d)).pin_memory()
+    xr = synth.ricker_traces(cfg, d)
+    if xr.shape[2] != nv:          # configs with a fixed point lattice: repeat its columns up to nv
+        xr = np.ascontiguousarray(np.take(xr, np.arange(nv) % xr.shape[2], axis=2))
+    x_host = torch.from_numpy(xr).pin_memory()
     xd = x_host.to(dev)
     yd = torch.empty((cfg.nt, cfg.nr, nv), device=dev)
     xo = torch.empty((cfg.nt, cfg.ns, nv), device=dev)

@@ -89,6 +89,24 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"((unsigned long long)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
 }
+// Multicast variant: the box lands at the same shared-memory offset in every CTA of ctaMask and
+// signals the mbarrier at the same offset in each of them.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                               int c1, int c2, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -114,6 +132,12 @@ __device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uin
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// Arrive (once the issued MMAs complete) on the mbarrier at this offset in every CTA of ctaMask.
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
                  : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -181,11 +205,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // column tile fastest, then the row tile, then the frequency.  The TMA/MMA stage ring runs
 // continuously across tiles and the accumulator is double-buffered in TMEM (2 x BN columns),
 // so the epilogue of one tile overlaps the main loop of the next.
-template <bool ADJ, int BN, bool SPLIT>
+//
+// PAIR: the grid is launched as clusters of two CTAs that take row tiles 2j and 2j + 1 of the
+// same column tile together; each loads its own A tile and half of the shared B tile, which TMA
+// multicasts into both CTAs' shared memory, so the L2-to-SM traffic for B halves.  A stage is
+// refilled only after both CTAs' MMAs have consumed it (the empty barrier counts the two
+// multicast commits).  n_tiles_m then counts row-tile pairs.
+template <bool ADJ, int BN, bool SPLIT, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a,
                    uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
+    // the early exit is uniform over a cluster (the flag is one device word read by every CTA)
     if (active && *active == 0) return;
     constexpr int STAGES = TcStages<BN, SPLIT>::v;
     constexpr uint32_t A_BYTES = TC_BM * 128;
@@ -204,12 +235,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rank = PAIR ? (int)cluster_rank() : 0;
+    const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int t_stride = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
     if (warp == 0) tmem_alloc(su32(tmem_slot), 2 * BN);
     if (threadIdx.x == 32) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(full0 + 8 * i, 1);
-            mbar_init(empty0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, PAIR ? 2 : 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(accf0 + 8 * i, 1);
@@ -219,17 +253,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();            // the peer's barriers exist before any multicast lands
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int per_freq = n_tiles_n * n_tiles_m;
+    // tile t -> frequency k, first row m0, first column n0
+    auto coords = [&](int t, int& k, int& m0, int& n0) {
+        k = t / per_freq;
+        const int rem = t - k * per_freq;
+        const int mt = rem / n_tiles_n;
+        m0 = (PAIR ? 2 * mt + rank : mt) * TC_BM;
+        n0 = (rem - mt * n_tiles_n) * BN;
+    };
 
     if (warp == 0) {
         if (lane == 0) {
             long g = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-                const int k = tile / per_freq, rem = tile - k * per_freq;
-                const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
+            for (int tile = t_first; tile < n_tiles && ok; tile += t_stride) {
+                int k, m0, n0;
+                coords(tile, k, m0, n0);
                 for (int kb = 0; kb < a.kstages; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t round = (uint32_t)(g / STAGES);
@@ -250,7 +293,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             tma_load_3d(ha, ma, full0 + 8 * s, m0, kb * TC_BK, k);
                             tma_load_3d(ha + A_BYTES / 2, ma, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
                         }
-                        tma_load_3d(hb, mb, full0 + 8 * s, kb * TC_BK, n0, k);
+                        if (PAIR)   // this CTA's half of the B tile, into both CTAs of the pair
+                            tma_load_3d_mc(hb + rank * (B_BYTES / 2), mb, full0 + 8 * s, kb * TC_BK,
+                                           n0 + rank * (BN / 2), k, (uint16_t)0x3);
+                        else
+                            tma_load_3d(hb, mb, full0 + 8 * s, kb * TC_BK, n0, k);
                     }
                 }
             }
@@ -264,7 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             long i = 0;                 // accumulation chunks issued (one per tile unless SPLIT)
             bool ok = true;
             const int kc = SPLIT ? TC_KCHUNK : a.kstages;
-            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
+            for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
               for (int kb0 = 0; kb0 < a.kstages && ok; kb0 += kc, ++i) {
                 const int buf = (int)(i & 1);
                 if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) {
@@ -297,7 +344,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             umma_f16(d, sdesc(sa2 + ao, lbo, 1024), bd, idesc, 1u);
                         }
                     }
-                    umma_commit(empty0 + 8 * s);
+                    if (PAIR) umma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);   // both CTAs refill s
+                    else umma_commit(empty0 + 8 * s);
                 }
                 umma_commit(accf0 + 8 * buf);
               }
@@ -310,9 +358,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         long i = 0;                     // accumulation chunks consumed
         const int nch = SPLIT ? (a.kstages + TC_KCHUNK - 1) / TC_KCHUNK : 1;
         int parity = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, parity ^= 1) {
-            const int k = tile / per_freq, rem = tile - k * per_freq;
-            const int m0 = (rem / n_tiles_n) * TC_BM, n0 = (rem % n_tiles_n) * BN;
+        for (int tile = t_first; tile < n_tiles; tile += t_stride, parity ^= 1) {
+            int k, m0, n0;
+            coords(tile, k, m0, n0);
             // this tile's reciprocal column scales (exact: powers of two) into shared memory; the
             // buffer alternates with the tile parity so the next tile's copy never races a reader
             float* sgs = sig_s + parity * 128;
@@ -427,6 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();            // no CTA leaves while its peer may still multicast into it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -605,19 +654,59 @@ int sm_count() {
     return n;
 }
 
-template <bool ADJ, int BN, bool SPLIT>
-void launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
+// grid: (column tiles, row tiles, frequencies).  PAIR launches clusters of two CTAs over row-tile
+// pairs (an odd last row tile is paired with an empty one whose rows fall outside the output).
+bool g_pair_off = false;   // set when a cluster launch is refused: later products use single CTAs
+
+template <bool ADJ, int BN, bool SPLIT, bool PAIR>
+bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
                const int* active) {
     static bool attr = false;
     const size_t smem = tc_smem_bytes<BN, SPLIT>();
+    auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, PAIR>;
     if (!attr) {
-        cudaFuncSetAttribute(tc_gemm_kernel<ADJ, BN, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    const int n_tiles = (int)(grid.x * grid.y * grid.z);
-    const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
-    tc_gemm_kernel<ADJ, BN, SPLIT><<<ctas, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc,
-                                                                  active, (int)grid.x, (int)grid.y, n_tiles);
+    const int rows = PAIR ? (int)(grid.y + 1) / 2 : (int)grid.y;
+    const int n_tiles = (int)grid.x * rows * (int)grid.z;
+    if (!PAIR) {
+        const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
+        kern<<<ctas, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
+                                            n_tiles);
+        return true;
+    }
+    const int pairs = n_tiles < sm_count() / 2 ? n_tiles : sm_count() / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
+                           n_tiles) != cudaSuccess) {
+        cudaGetLastError();
+        g_pair_off = true;
+        return false;
+    }
+    return true;
+}
+
+// Paired CTAs (B multicast) for wide column tiles with at least two row tiles; MDC_TC_PAIR=0 in
+// the environment turns it off.
+bool use_pair(int bn, int row_tiles) {
+    static int env = -1;
+    if (env < 0) {
+        const char* e = getenv("MDC_TC_PAIR");
+        env = (e && e[0] == '0') ? 0 : 1;
+    }
+    return env == 1 && !g_pair_off && bn >= 128 && row_tiles >= 2;
 }
 
 }  // namespace
@@ -684,17 +773,21 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const unsigned char* Bp = static_cast<const unsigned char*>(p->tcB);
     const size_t glo = split ? (size_t)p->nf * p->nr * p->ldg * 4 : 0;   // lo plane of the kernel
     const size_t blo = plane * 2;                                          // lo plane of B (bytes)
+    // row tiles of the product (kernel rows forward; 2 * ldg interleaved reals adjoint)
+    const int mrows = adjoint ? (int)(kp / TC_BM) : (p->nr + TC_BM - 1) / TC_BM;
+    const bool pair = use_pair(bn, mrows);
+    const int bbox = pair ? bn / 2 : bn;      // paired CTAs each load half of the B tile
     bool ok = true;
     for (int h = 0; h < (split ? 2 : 1) && ok; ++h) {
         const void* ga = G + h * glo;
         const void* gb = Bp + h * blo;
         if (!adjoint)
             ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 128) &&
-                 make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bn);
+                 make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bbox);
         else
             ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 64) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
-                             (uint64_t)kpitch * 2 * rows_pad, 64, bn);
+                             (uint64_t)kpitch * 2 * rows_pad, 64, bbox);
     }
     if (!ok) return false;
     if (!split) {
@@ -715,19 +808,22 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const uint32_t fmt = bf16 ? 1u : 0u;
     const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((adjoint ? 1u : 0u) << 15) |
                            ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-    const int mrows = adjoint ? (int)(kp / TC_BM) : (p->nr + TC_BM - 1) / TC_BM;
     dim3 grid((unsigned)(rows_pad / bn), (unsigned)mrows, (unsigned)p->nf);
+#define MDC_TC_LAUNCH(ADJV, BV, SPV)                                                       \
+    launched = pair ? launch_tc<ADJV, BV, SPV, true>(maps, a, idesc, grid, s, active)     \
+                    : launch_tc<ADJV, BV, SPV, false>(maps, a, idesc, grid, s, active);
 #define MDC_TC_CASE(BNV)                                                                   \
     case BNV:                                                                              \
         if (split) {                                                                       \
             constexpr int BS = BNV > 128 ? 128 : BNV;                                      \
-            if (adjoint) launch_tc<true, BS, true>(maps, a, idesc, grid, s, active);       \
-            else launch_tc<false, BS, true>(maps, a, idesc, grid, s, active);              \
+            if (adjoint) { MDC_TC_LAUNCH(true, BS, true) }                                 \
+            else { MDC_TC_LAUNCH(false, BS, true) }                                        \
         } else {                                                                           \
-            if (adjoint) launch_tc<true, BNV, false>(maps, a, idesc, grid, s, active);     \
-            else launch_tc<false, BNV, false>(maps, a, idesc, grid, s, active);            \
+            if (adjoint) { MDC_TC_LAUNCH(true, BNV, false) }                               \
+            else { MDC_TC_LAUNCH(false, BNV, false) }                                      \
         }                                                                                  \
         break;
+    bool launched = false;
     switch (bn) {
         MDC_TC_CASE(32)
         MDC_TC_CASE(64)
@@ -735,7 +831,8 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         MDC_TC_CASE(256)
     }
 #undef MDC_TC_CASE
-    return true;
+#undef MDC_TC_LAUNCH
+    return launched;
 }
 
 }  // namespace mdc
