@@ -80,10 +80,10 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, tag=""):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}{tag}.csv")
 
     def start(self):
         try:
@@ -101,7 +101,7 @@ class ClockSampler:
         self.proc.terminate()
         self.proc.wait()
         self.fh.close()
-        sms, maxs, reasons = [], [], set()
+        sms, maxs, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -110,6 +110,7 @@ class ClockSampler:
             try:
                 sms.append(float(f[1]))
                 maxs.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -117,7 +118,8 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sms) if sms else None,
                 "sm_max_mhz": max(maxs) if maxs else None,
-                "reasons": sorted(reasons), "samples": len(sms)}
+                "reasons": sorted(reasons), "samples": len(sms),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 def max_over_ranks(values, device):
@@ -272,10 +274,13 @@ def run_redatum(args, dev):
     out = solve()                                      # warm-up (allocations, tensor maps)
     torch.cuda.synchronize()
     times = []
+    sampler = ClockSampler(dev.index if dev.index is not None else 0, "_redatum")
+    sampler.start()
     for _ in range(args.redatum_solves):
         t0 = time.perf_counter()
         out = solve()
         times.append(time.perf_counter() - t0)
+    clocks = sampler.stop()
     # device time per kernel class in one more solve (CUDA events around every launch)
     breakdown = {}
     for name, h in (("fp16_kernel", lo.h), ("reference_kernel", ref.h)):
@@ -306,6 +311,7 @@ def run_redatum(args, dev):
             "iterations": out["iters"], "final_residual": out["final_residual"],
             "rel_l2_vs_fp32_solve": err,
             "device_ms_per_kernel_class": breakdown,
+            "clocks": clocks,
             "fp32_one_job": {"solves_per_s": 1.0 / t_plain, "ms_per_solve": 1e3 * t_plain,
                              "iterations": plain["iters"], "storage": "c64"}}
 
@@ -354,6 +360,69 @@ def run_mdd(args, dev):
     out["workload"] = (f"MDD (Eq. 8) by LSQR, G+ {cfg.nr} receivers (61x61, 20 m) x {len(xs)} focusing points "
                        f"(29x29, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, {cfg.n_events} hyperbolic events, "
                        f"{nv} virtual sources per batch, {niter} iterations")
+    return out
+
+
+def run_precision(args, dev):
+    """Precision sweep on the 8281-trace kernel (nfmax=160): forward and adjoint MDC per storage
+    format at nv = 1 (GEMV, streaming the kernel) and nv = 128 (tensor cores for the 16-bit copies),
+    with the relative L2 error of 8 sampled output rows (forward) and columns (adjoint) against the
+    FP64 oracle at nv = 16."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from oracle import mdc as omdc
+    from synth import gpu as sgpu
+    cfg = synth.config(3)
+    d = synth.draw(cfg)
+    G = sgpu.kernel_on_device(cfg, d)
+    rng = np.random.default_rng(31)
+    rows = np.sort(rng.choice(cfg.nr, size=8, replace=False))
+    cols = np.sort(rng.choice(cfg.ns, size=8, replace=False))
+    Gr = synth.kernel(cfg, d, rows=rows)
+    Gc = synth.kernel(cfg, d, cols=cols)
+    x16 = synth.random_traces(cfg, 16, seed_offset=7)
+    y16 = synth.random_traces(cfg, 16, seed_offset=8, nspace=cfg.nr)
+    ref_f = omdc.forward_rows(Gr, x16, cfg.dt, cfg.dr)
+    ref_a = omdc.adjoint_cols(Gc, y16, cfg.dt, cfg.dr)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg.seed)
+    out = {"workload": f"MDC fwd+adj, nr=ns={cfg.nr} (91x91, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
+                       f"{cfg.n_events} hyperbolic events; rel L2 on 8 sampled rows/columns at nv=16 vs the FP64 oracle"}
+
+    def timed(fn, cls, h):
+        fn()
+        torch.cuda.synchronize()
+        mdc.mdc_timing(h, True)
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ms, n = mdc.mdc_timing_read(h, cls)
+        mdc.mdc_timing(h, False)
+        return ms / max(n, 1)
+
+    for fmt in ("c64", "c32s", "c16f", "cbf16", "ce4m3"):
+        op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=fmt)
+        kb = cfg.nf * cfg.nr * cfg.ns * BYTES_PER_COMPLEX[fmt]     # algorithmic kernel bytes per pass
+        res = {"kernel_gb": kb / 1e9}
+        for nv in (1, 128):
+            x = torch.randn((cfg.nt, cfg.ns, nv), generator=gen, device=dev)
+            y = torch.randn((cfg.nt, cfg.nr, nv), generator=gen, device=dev)
+            tf = timed(lambda: op.forward(x), "product_fwd", op.h)
+            ta = timed(lambda: op.adjoint(y), "product_adj", op.h)
+            flops = 8.0 * cfg.nf * cfg.nr * cfg.ns * nv
+            res[f"nv{nv}"] = {"product_fwd_ms": tf, "product_adj_ms": ta,
+                              "kernel_gbs": kb / (0.5 * (tf + ta)) / 1e6,
+                              "tflops": flops / (0.5 * (tf + ta)) / 1e9}
+            del x, y
+        yg = op.forward(torch.from_numpy(x16).to(dev)).cpu().numpy()[:, rows]
+        xg = op.adjoint(torch.from_numpy(y16).to(dev)).cpu().numpy()[:, cols]
+        res["rel_l2_forward"] = float(np.linalg.norm(yg - ref_f) / np.linalg.norm(ref_f))
+        res["rel_l2_adjoint"] = float(np.linalg.norm(xg - ref_a) / np.linalg.norm(ref_a))
+        op.close()
+        torch.cuda.empty_cache()
+        out[fmt] = res
+    del G
+    torch.cuda.empty_cache()
     return out
 
 
@@ -611,6 +680,8 @@ def run_ours(args):
         result["redatum"] = run_redatum(args, dev)
     if world == 1 and not args.no_mdd:
         result["mdd"] = run_mdd(args, dev)
+    if world == 1 and not args.no_precision:
+        result["precision"] = run_precision(args, dev)
     if world == 1 and not args.no_serving:
         result["serving"] = run_serving(args, dev)
     if world == 1 and not args.no_cpu_baseline:
@@ -636,6 +707,7 @@ def main():
     ap.add_argument("--no-redatum", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mdd", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--mdd-iters", type=int, default=10)
     ap.add_argument("--serving-config", type=int, default=5)
     ap.add_argument("--serving-rate", type=float, default=50.0)
