@@ -495,115 +495,153 @@ __device__ __forceinline__ float pow2_scale(float maxabs) {
     return ldexpf(1.f, 14 - e);   // maxabs * scale < 2^14
 }
 
-// forward: X[k][s][ldi] (voff, ncol columns) -> BT[k][n'][2*ldg], sigma[k][n]
+// Packed pair of 16-bit values (lo element first in memory).
+template <typename T> struct Pair2;
+template <> struct Pair2<__half> {
+    using type = __half2;
+    static __device__ __forceinline__ __half2 make(__half a, __half b) { return __halves2half2(a, b); }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    using type = __nv_bfloat162;
+    static __device__ __forceinline__ __nv_bfloat162 make(__nv_bfloat16 a, __nv_bfloat16 b) {
+        return __halves2bfloat162(a, b);
+    }
+};
+
+constexpr int PREP_COLS = 8;      // complex columns per CTA
+constexpr int PREP_ROWS = 256;    // spatial rows per staged block (one per thread)
+
+// Column maxima of |Re|, |Im| over the rows of a [rows][ldi] complex block (8 columns per CTA,
+// each warp reading 4 rows x 64 contiguous bytes), optionally weighted per row; writes the
+// power-of-two scale of each column to sig[] and its reciprocal to inv_sigma.
+__device__ __forceinline__ void prep_scales(const float2* __restrict__ Xk, int ldi, int nrows, int n0, int ncol,
+                                            const float* __restrict__ rw, float* red, float* sig,
+                                            float* __restrict__ inv_sigma_k) {
+    const int j0 = threadIdx.x & 7;
+    float m = 0.f;
+    if (n0 + j0 < ncol)
+        for (int s = threadIdx.x >> 3; s < nrows; s += 32) {
+            const float2 v = Xk[(size_t)s * ldi + n0 + j0];
+            const float w = rw ? rw[s] : 1.f;
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * w);
+        }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x < PREP_COLS) {
+        float mm = 0.f;
+        for (int i = threadIdx.x; i < 256; i += PREP_COLS) mm = fmaxf(mm, red[i]);
+        const float sc = pow2_scale(mm);
+        sig[threadIdx.x] = sc;
+        if (n0 + (int)threadIdx.x < ncol) inv_sigma_k[n0 + threadIdx.x] = 1.f / sc;
+    }
+    __syncthreads();
+}
+
+// Stage rows [s0, s0 + 256) x 8 columns of a complex block in shared memory (coalesced reads),
+// scaled by sig[column] (and by rw[row] if given); rows or columns outside the block are zero.
+__device__ __forceinline__ void prep_stage(const float2* __restrict__ Xk, int ldi, int nrows, int s0, int n0,
+                                           int ncol, const float* __restrict__ rw, const float* sig,
+                                           float2 (*tile)[PREP_COLS + 1]) {
+#pragma unroll
+    for (int u = 0; u < PREP_ROWS * PREP_COLS / 256; ++u) {
+        const int idx = threadIdx.x + 256 * u;
+        const int rr = idx >> 3, j = idx & 7, s = s0 + rr;
+        float2 v = make_float2(0.f, 0.f);
+        if (s < nrows && n0 + j < ncol) {
+            v = Xk[(size_t)s * ldi + n0 + j];
+            const float f = sig[j] * (rw ? rw[s] : 1.f);
+            v.x *= f;
+            v.y *= f;
+        }
+        tile[rr][j] = v;
+    }
+}
+
+// forward: X[k][s][ldi] (voff, ncol columns) -> BT[k][n'][2*ldg], inv_sigma[k][n].  Real rows
+// 2n and 2n + 1 of B hold (Re, -Im) and (Im, Re) pairs of column n along s, so the real GEMM
+// over K = 2 * ldg gives the real and imaginary parts of the complex product.
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X, int ldi, int voff, int ns,
                                                    int ncol, int ldg, int rows_pad, T* __restrict__ BT,
                                                    float* __restrict__ inv_sigma, const int* active, size_t plane) {
     if (active && *active == 0) return;
-    const int k = blockIdx.y, n0 = blockIdx.x * 8;
+    using P2 = typename Pair2<T>::type;
+    const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
     const float2* Xk = X + (size_t)k * ns * ldi + voff;
     __shared__ float red[256];
-    __shared__ float sig[8];
-    const int j0 = threadIdx.x & 7;
-    float m = 0.f;
-    if (n0 + j0 < ncol)
-        for (int s = threadIdx.x >> 3; s < ns; s += 32) {
-            const float2 v = Xk[(size_t)s * ldi + n0 + j0];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-        }
-    red[threadIdx.x] = m;
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        float mm = 0.f;
-        for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
-        const float sc = pow2_scale(mm);
-        sig[threadIdx.x] = sc;
-        if (n0 + (int)threadIdx.x < ncol) inv_sigma[(size_t)k * ncol + n0 + threadIdx.x] = 1.f / sc;
-    }
-    __syncthreads();
+    __shared__ float sig[PREP_COLS];
+    __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    prep_scales(Xk, ldi, ns, n0, ncol, nullptr, red, sig, inv_sigma + (size_t)k * ncol);
     const size_t kp = 2 * (size_t)ldg;
-    T* Bk = BT + (size_t)k * rows_pad * kp;
-    for (int s = threadIdx.x; s < ldg; s += 256) {
+    P2* Bk = reinterpret_cast<P2*>(BT + (size_t)k * rows_pad * kp);      // one pair per s
+    const size_t kp2 = kp / 2, plane2 = plane / 2;
+    for (int s0 = 0; s0 < ldg; s0 += PREP_ROWS) {
+        prep_stage(Xk, ldi, ns, s0, n0, ncol, nullptr, sig, tile);
+        __syncthreads();
+        const int s = s0 + threadIdx.x;
+        if (s < ldg) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int n = n0 + j;
-            if (2 * n >= rows_pad) break;
-            float2 v = make_float2(0.f, 0.f);
-            if (n < ncol && s < ns) {
-                v = Xk[(size_t)s * ldi + n];
-                v.x *= sig[j];
-                v.y *= sig[j];
-            }
-            T* r0 = Bk + (size_t)(2 * n) * kp + 2 * (size_t)s;
-            T* r1 = r0 + kp;
-            const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
-            r0[0] = hx;
-            r0[1] = cvt<T>(-v.y);
-            r1[0] = hy;
-            r1[1] = hx;
-            if (SPLIT) {
-                const float lx = v.x - (float)hx, ly = v.y - (float)hy;
-                r0[plane] = cvt<T>(lx);
-                r0[plane + 1] = cvt<T>(-ly);
-                r1[plane] = cvt<T>(ly);
-                r1[plane + 1] = cvt<T>(lx);
+            for (int j = 0; j < PREP_COLS; ++j) {
+                const int n = n0 + j;
+                if (2 * n >= rows_pad) break;
+                const float2 v = tile[threadIdx.x][j];
+                const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
+                P2* r0 = Bk + (size_t)(2 * n) * kp2 + s;
+                r0[0] = Pair2<T>::make(hx, cvt<T>(-v.y));
+                r0[kp2] = Pair2<T>::make(hy, hx);
+                if (SPLIT) {
+                    const float lx = v.x - (float)hx, ly = v.y - (float)hy;
+                    const T tlx = cvt<T>(lx), tly = cvt<T>(ly);
+                    r0[plane2] = Pair2<T>::make(tlx, cvt<T>(-ly));
+                    r0[plane2 + kp2] = Pair2<T>::make(tly, tlx);
+                }
             }
         }
+        __syncthreads();
     }
 }
 
-// adjoint: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] -> BT[k][n''][kpitch], sigma[k][n]
+// adjoint: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] -> BT[k][n''][kpitch], inv_sigma[k][n].
+// Real rows 2n and 2n + 1 hold Re and Im of column n along r; each thread writes two adjacent r.
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y, int ldi, int voff, int nr,
                                                    int ncol, const float* __restrict__ gscale, int kpitch,
                                                    int rows_pad, T* __restrict__ BT, float* __restrict__ inv_sigma,
                                                    const int* active, size_t plane) {
     if (active && *active == 0) return;
-    const int k = blockIdx.y, n0 = blockIdx.x * 8;
+    using P2 = typename Pair2<T>::type;
+    const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
     const float2* Yk = Y + (size_t)k * nr * ldi + voff;
     const float* gs = gscale + (size_t)k * nr;
     __shared__ float red[256];
-    __shared__ float sig[8];
-    const int j0 = threadIdx.x & 7;
-    float m = 0.f;
-    if (n0 + j0 < ncol)
-        for (int r = threadIdx.x >> 3; r < nr; r += 32) {
-            const float2 v = Yk[(size_t)r * ldi + n0 + j0];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * gs[r]);
-        }
-    red[threadIdx.x] = m;
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        float mm = 0.f;
-        for (int i = threadIdx.x; i < 256; i += 8) mm = fmaxf(mm, red[i]);
-        const float sc = pow2_scale(mm);
-        sig[threadIdx.x] = sc;
-        if (n0 + (int)threadIdx.x < ncol) inv_sigma[(size_t)k * ncol + n0 + threadIdx.x] = 1.f / sc;
-    }
-    __syncthreads();
-    T* Bk = BT + (size_t)k * rows_pad * kpitch;
-    for (int r = threadIdx.x; r < kpitch; r += 256) {
-        const float g = r < nr ? gs[r] : 0.f;
+    __shared__ float sig[PREP_COLS];
+    __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    prep_scales(Yk, ldi, nr, n0, ncol, gs, red, sig, inv_sigma + (size_t)k * ncol);
+    P2* Bk = reinterpret_cast<P2*>(BT + (size_t)k * rows_pad * kpitch);  // kpitch is a multiple of 8
+    const size_t kq = (size_t)kpitch / 2, plane2 = plane / 2;
+    for (int r0 = 0; r0 < kpitch; r0 += PREP_ROWS) {
+        prep_stage(Yk, ldi, nr, r0, n0, ncol, gs, sig, tile);
+        __syncthreads();
+        // threads 0..127 each take rows r0 + 2t, r0 + 2t + 1 for columns 0..3, threads 128..255 columns 4..7
+        const int t = threadIdx.x & 127, jb = (threadIdx.x >> 7) * (PREP_COLS / 2);
+        const int r = r0 + 2 * t;
+        if (r < kpitch) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int n = n0 + j;
-            if (2 * n >= rows_pad) break;
-            float2 v = make_float2(0.f, 0.f);
-            if (n < ncol && r < nr) {
-                v = Yk[(size_t)r * ldi + n];
-                const float f = g * sig[j];
-                v.x *= f;
-                v.y *= f;
-            }
-            const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
-            Bk[(size_t)(2 * n) * kpitch + r] = hx;
-            Bk[(size_t)(2 * n + 1) * kpitch + r] = hy;
-            if (SPLIT) {
-                Bk[plane + (size_t)(2 * n) * kpitch + r] = cvt<T>(v.x - (float)hx);
-                Bk[plane + (size_t)(2 * n + 1) * kpitch + r] = cvt<T>(v.y - (float)hy);
+            for (int jj = 0; jj < PREP_COLS / 2; ++jj) {
+                const int j = jb + jj, n = n0 + j;
+                if (2 * n >= rows_pad) continue;
+                const float2 a = tile[2 * t][j], b = tile[2 * t + 1][j];
+                const T ax = cvt<T>(a.x), bx = cvt<T>(b.x), ay = cvt<T>(a.y), by = cvt<T>(b.y);
+                P2* q0 = Bk + (size_t)(2 * n) * kq + (r >> 1);
+                q0[0] = Pair2<T>::make(ax, bx);
+                q0[kq] = Pair2<T>::make(ay, by);
+                if (SPLIT) {
+                    q0[plane2] = Pair2<T>::make(cvt<T>(a.x - (float)ax), cvt<T>(b.x - (float)bx));
+                    q0[plane2 + kq] = Pair2<T>::make(cvt<T>(a.y - (float)ay), cvt<T>(b.y - (float)by));
+                }
             }
         }
+        __syncthreads();
     }
 }
 
