@@ -290,6 +290,7 @@ template <int N1, int N2> struct FourStep {
     static constexpr int ZSIZE = NT * RS + N1 * BP;                  // float2 elements
     // twiddle table and tile; the inverse transform's column-sum reduction reuses the tile
     static constexpr size_t smem = (size_t)(NT / 2 + ZSIZE) * sizeof(float2);
+    static constexpr size_t smem_full = (size_t)(NT + ZSIZE) * sizeof(float2);   // full-period twiddles
     static_assert(ZSIZE * sizeof(float2) >= FFT_THREADS * 4 * sizeof(double), "reduction fits the tile");
     __device__ static __forceinline__ int zi(int t, int j) { return t * RS + (t / N2) * BP + j; }
 };
@@ -298,8 +299,9 @@ __device__ __forceinline__ float2 tw_full(const float2* tw, int m, int nt) {
     return m < (nt >> 1) ? tw[m] : make_float2(-tw[m - (nt >> 1)].x, -tw[m - (nt >> 1)].y);
 }
 
-// tw: the twiddle table W_NT^m, m < NT/2, of the transform's sign (conjugated for INV).
-template <int N1, int N2, bool INV>
+// tw: the twiddle table W_NT^m of the transform's sign (conjugated for INV), m < NT/2, or with
+// FULL the whole period m < NT (no sign select per twiddle).
+template <int N1, int N2, bool INV, bool FULL = false>
 __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
     using F = FourStep<N1, N2>;
     constexpr int P = F::P;
@@ -311,7 +313,7 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
         reg_fft<N1, INV>(r);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
-            const float2 v = k1 == 0 ? r[0] : cmul(r[k1], tw_full(tw, n2 * k1, F::NT));
+            const float2 v = k1 == 0 ? r[0] : cmul(r[k1], FULL ? tw[n2 * k1] : tw_full(tw, n2 * k1, F::NT));
             z[F::zi(k1 * N2 + n2, j)] = v;
         }
     }
@@ -338,10 +340,14 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     constexpr int NT = F::NT, CT = F::CT;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 sm2[];
-    float2* tw = sm2;
-    float2* z = sm2 + NT / 2;
+    float2* tw = sm2;                  // W_NT^m for the whole period m < NT
+    float2* z = sm2 + NT;
     const int c0 = blockIdx.x * CT;
-    for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) {
+        const float2 w = a.tw[i];
+        tw[i] = w;
+        tw[i + NT / 2] = make_float2(-w.x, -w.y);
+    }
     const float sc = coef(a.scale);
     // Load the [NT][CT] tile with many independent loads in flight per thread.
     auto put = [&](int t, int cl, float v) {
@@ -413,7 +419,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         }
     }
     __syncthreads();
-    four_step<N1, N2, false>(z, tw);
+    four_step<N1, N2, false, true>(z, tw);
     // Bin k = k1 + N1 * k2 sits in row k1 * N2 + k2, its mirror NT - k in row
     // ((-k1) mod N1) * N2 + (NT/N1 - k2 - [k1 > 0]) (k > 0).  A thread keeps one column and walks
     // the bins of every G-th block k1; the G threads of a column cover all N1 blocks, and the
@@ -638,11 +644,11 @@ void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     a.vec4 = (a.C % 4 == 0) && ((uintptr_t)a.x % 16 == 0) && (!a.x2 || (uintptr_t)a.x2 % 16 == 0);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(rfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem);
+        cudaFuncSetAttribute(rfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_full);
         attr = true;
     }
     LaunchScope ls(p, s, MDC_KC_RFFT);
-    rfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+    rfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
 }
 
 template <int N1, int N2>
