@@ -256,9 +256,10 @@ int srv_create(mdc_server_handle* out, mdc_handle R, mdc_handle R_ref, int64_t h
  * memory, of which the first nv columns are the job's (ld >= nv; pinned memory copies fastest).
  * The buffers are NOT copied at submission: they are read when the job is admitted, so the
  * caller keeps them unchanged until the job completes.  niter LSQR iterations (tol > 0: stop
- * earlier at tol * ||d||).  The four host output buffers [nt][ns][nv] (each may be NULL) are
- * written when the job completes.  MDC_ERR_BUDGET if the job can never fit the budget or the
- * column capacity.  *job_id receives the job's id. */
+ * earlier at tol * ||d||).  The four host output buffers [nt][ns][nv] are written when the job
+ * completes; any of them may be NULL (that result is dropped, or kept for srv_result after
+ * srv_keep_results(s, 1)).  MDC_ERR_BUDGET if the job can never fit the budget or the column
+ * capacity.  *job_id receives the job's id. */
 int srv_submit(mdc_server_handle s, const int* window_host, const float* fd_plus_host, int nv, int ld,
                int niter, double tol, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
                float* g_plus_host, int64_t* job_id);
@@ -270,6 +271,16 @@ int srv_step(mdc_server_handle s, int* completed);
  * Returns the job's error status if it failed. */
 int srv_poll(mdc_server_handle s, int64_t job_id, int* state, int* iters, double* final_residual,
              double* latency_s, double* queue_s);
+/* srv_keep_results -- keep = 1: jobs submitted from now on keep the results whose output
+ * buffers are given as NULL in server-owned host memory until srv_release, for srv_result;
+ * keep = 0 (the default): such results are dropped. */
+int srv_keep_results(mdc_server_handle s, int keep);
+/* srv_result -- copy a completed job's outputs [nt][ns][nv] into the given host buffers (each may
+ * be NULL), from the buffers given at submission or from the server's kept copy.
+ * MDC_ERR_STATE while the job is queued or running or if a requested result was neither given a
+ * buffer nor kept; the job's error status if it failed. */
+int srv_result(mdc_server_handle s, int64_t job_id, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+               float* g_plus_host);
 /* srv_release -- forget a completed or failed job (MDC_ERR_STATE while queued/running). */
 int srv_release(mdc_server_handle s, int64_t job_id);
 /* srv_stats -- queued and running job counts, bytes and columns in use. */

@@ -56,6 +56,8 @@ SIGNATURES = {
     "srv_step": (_i, [_vp, ctypes.POINTER(_i)]),
     "srv_poll": (_i, [_vp, _i64, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d),
                       ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "srv_result": (_i, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "srv_keep_results": (_i, [_vp, _i]),
     "srv_release": (_i, [_vp, _i64]),
     "srv_stats": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i)]),
     "srv_checkpoint": (_i, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
@@ -383,6 +385,16 @@ def srv_poll(v, job_id: int) -> dict:
                         ctypes.byref(qs))
     return {"state": st.value, "iters": it.value, "final_residual": fr.value, "latency_s": lat.value,
             "queue_s": qs.value, "status": rc}
+
+
+def srv_keep_results(v, keep: bool = True) -> None:
+    _check(lib().srv_keep_results(v, 1 if keep else 0), "srv_keep_results")
+
+
+def srv_result(v, job_id: int, outputs=(None, None, None, None)) -> None:
+    """Copy a completed job's f-, f_m+, g-, g+ (float32 [nt][ns][nv] numpy arrays, may be None)."""
+    o = [_hptr(a) for a in outputs]
+    _check(lib().srv_result(v, job_id, o[0], o[1], o[2], o[3]), "srv_result")
 
 
 def srv_release(v, job_id: int) -> None:

@@ -520,6 +520,8 @@ struct ServeJob {
     bool bound = true;           // false for a resumed job until srv_bind gives its outputs
     std::vector<int> cut_own;    // inputs held by the server (resumed queued jobs)
     std::vector<float> fd_own;
+    std::vector<float> res_own[4];  // results kept by the server for outputs given as NULL
+    bool keep = false;              // keep NULL outputs (server setting at submission)
 };
 
 }  // namespace
@@ -540,6 +542,7 @@ struct mdc_server {
     std::unordered_map<int64_t, ServeJob*> jobs;
     int* flags_h = nullptr;      // pinned
     int flags_cap = 0;
+    bool keep_results = false;   // keep outputs given as NULL for srv_result
 };
 
 namespace mdc {
@@ -735,8 +738,15 @@ void finish_job(mdc_server* v, ServeJob* j) {
     }
     S->greens(j->fd_d, j->x[0], j->x[1], j->x[2], j->x[3]);
     const size_t bytes = (size_t)S->B * sizeof(float);
-    for (int i = 0; i < 4; ++i)
-        if (j->out[i]) cudaMemcpyAsync(j->out[i], j->x[i], bytes, cudaMemcpyDeviceToHost, v->s);
+    for (int i = 0; i < 4; ++i) {
+        float* dst = j->out[i];
+        if (!dst && !j->keep) continue;           // not wanted
+        if (!dst) {                               // no caller buffer: keep it for srv_result
+            j->res_own[i].resize((size_t)S->B);
+            dst = j->res_own[i].data();
+        }
+        cudaMemcpyAsync(dst, j->x[i], bytes, cudaMemcpyDeviceToHost, v->s);
+    }
 }
 
 }  // namespace
@@ -797,6 +807,7 @@ extern "C" int srv_submit(mdc_server* v, const int* window_host, const float* fd
     j->out[3] = g_plus_host;
     j->bytes = job_bytes(v->p, nv);
     j->t_submit = now_s();
+    j->keep = v->keep_results;
     v->queue.push_back(j);
     v->jobs[j->id] = j;
     *job_id = j->id;
@@ -948,6 +959,31 @@ extern "C" int srv_poll(mdc_server* v, int64_t id, int* state, int* iters, doubl
     if (latency_s) *latency_s = j->state >= JOB_DONE ? j->t_done - j->t_submit : -1.0;
     if (queue_s) *queue_s = j->state >= JOB_RUNNING ? j->t_start - j->t_submit : -1.0;
     return j->state == JOB_FAILED ? j->status : MDC_OK;
+}
+
+extern "C" int srv_result(mdc_server* v, int64_t id, float* f_minus_host, float* f_mplus_host, float* g_minus_host,
+                          float* g_plus_host) {
+    if (!v) return MDC_ERR_ARG;
+    auto it = v->jobs.find(id);
+    if (it == v->jobs.end()) return MDC_ERR_ARG;
+    ServeJob* j = it->second;
+    if (j->state == JOB_FAILED) return j->status;
+    if (j->state != JOB_DONE) return MDC_ERR_STATE;
+    float* dst[4] = {f_minus_host, f_mplus_host, g_minus_host, g_plus_host};
+    const size_t n = (size_t)v->p->nt * v->p->ns * j->nv;
+    for (int i = 0; i < 4; ++i) {
+        if (!dst[i]) continue;
+        const float* src = j->out[i] ? j->out[i] : j->res_own[i].data();
+        if (!j->out[i] && j->res_own[i].size() < n) return MDC_ERR_STATE;   // not kept
+        if (src != dst[i]) std::memcpy(dst[i], src, n * sizeof(float));
+    }
+    return MDC_OK;
+}
+
+extern "C" int srv_keep_results(mdc_server* v, int keep) {
+    if (!v) return MDC_ERR_ARG;
+    v->keep_results = keep != 0;
+    return MDC_OK;
 }
 
 extern "C" int srv_release(mdc_server* v, int64_t id) {

@@ -201,3 +201,37 @@ def test_marchenko_neumann_matches_oracle(niter):
             assert rel(out["f_mplus"].cpu().numpy(), x[1]) <= TOL
     assert rel(out["g_minus"].cpu().numpy(), gm) <= TOL
     assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL
+
+
+def test_redatuming_workload_full_size_two_points():
+    """The bench's redatuming workload at full size (1681 x 1681 kernel, nt = 512, nfmax = 150,
+    ||R|| = 0.5), sampled to two of its 256 focusing points: the complex64 LSQR solve and the
+    FP16 solve refined against the split-FP16 reference (the bench's configuration) both match the
+    FP64 oracle's converged solution."""
+    import paper_2011_11120_gb300 as m
+    from synth import gpu as sgpu
+    cfg = synth.config(4)
+    d = synth.draw(cfg)
+    pick = [0, 137]
+    cut = np.ascontiguousarray(synth.window_cutoffs(cfg, d)[:, pick])
+    fd = np.ascontiguousarray(synth.direct_focusing(cfg, d)[:, :, pick])
+    Gd = sgpu.kernel_on_device(cfg, d)
+    G = Gd.cpu().numpy().astype(np.complex128)            # the workload's kernel, for the oracle
+    op_o = omar.Marchenko(G, cfg.dt, cfg.dr, cut, cfg.nt)
+    res = solvers.lsqr(op_o.matvec, op_o.rmatvec, op_o.data(fd), niter=30)
+    del G, op_o
+    cut_t, fd_t = torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda()
+    plain = m.MDC(Gd, cfg.nt, cfg.dt, cfg.dr, storage="c64")
+    out = plain.marchenko(cut_t, fd_t, 20, greens=False)
+    plain.close()
+    lo = m.MDC(Gd, cfg.nt, cfg.dt, cfg.dr, storage="c16f")
+    ref = m.MDC(Gd, cfg.nt, cfg.dt, cfg.dr, storage="c32s")
+    del Gd
+    outr = lo.marchenko_refined(ref, cut_t, fd_t, 20, nrefine=1, niter_refine=5, greens=False)
+    lo.close()
+    ref.close()
+    e_plain = max(rel(out["f_minus"].cpu().numpy(), res.x[0]), rel(out["f_mplus"].cpu().numpy(), res.x[1]))
+    e_ref = max(rel(outr["f_minus"].cpu().numpy(), res.x[0]), rel(outr["f_mplus"].cpu().numpy(), res.x[1]))
+    print(f"full-size redatuming, 2 points: complex64 {e_plain:.2e}, FP16 + refinement {e_ref:.2e}")
+    assert e_plain <= TOL
+    assert e_ref <= TOL

@@ -254,3 +254,34 @@ def test_checkpoint_resume_continues_bit_for_bit(small, storage, nref):
     op.close()
     if ref:
         ref.close()
+
+
+def test_kept_results_match_submitted_buffers(small):
+    """srv_result returns, for a job submitted without output buffers (results kept by the
+    server), exactly what a job with buffers received; without keep_results it is refused."""
+    import paper_2011_11120_gb300 as m
+    cfg, G = small
+    job = make_jobs(cfg, G, [(2, 6, 0.0)], seed=9)[0]
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    srv = m.srv_create(op.h, None, 1 << 34, 64)
+    try:
+        o_a = outputs(cfg, 2)
+        ja = m.srv_submit(srv, job["cut"], job["fd"], 2, job["niter"], 0.0, o_a)
+        jb = m.srv_submit(srv, job["cut"], job["fd"], 2, job["niter"], 0.0)         # dropped results
+        m.srv_keep_results(srv, True)
+        jc = m.srv_submit(srv, job["cut"], job["fd"], 2, job["niter"], 0.0)         # kept results
+        with pytest.raises(m.MDCError):
+            m.srv_result(srv, jc, outputs(cfg, 2))                                   # still queued
+        while any(m.srv_poll(srv, j)["state"] < m.JOB_DONE for j in (ja, jb, jc)):
+            m.srv_step(srv)
+        o_c = outputs(cfg, 2)
+        m.srv_result(srv, jc, o_c)
+        o_a2 = outputs(cfg, 2)
+        m.srv_result(srv, ja, o_a2)
+        for k in range(4):
+            assert np.array_equal(o_c[k], o_a[k]) and np.array_equal(o_a2[k], o_a[k])
+        with pytest.raises(m.MDCError):
+            m.srv_result(srv, jb, outputs(cfg, 2))                                   # was dropped
+    finally:
+        m.srv_destroy(srv)
+    op.close()
