@@ -299,6 +299,24 @@ __device__ __forceinline__ float2 tw_full(const float2* tw, int m, int nt) {
     return m < (nt >> 1) ? tw[m] : make_float2(-tw[m - (nt >> 1)].x, -tw[m - (nt >> 1)].y);
 }
 
+// Second pass of the four-step transform: the length-N2 DFTs over n2 of every block k1, in
+// place; ends with a barrier.
+template <int N1, int N2, bool INV>
+__device__ __forceinline__ void four_step_pass_b(float2* z) {
+    using F = FourStep<N1, N2>;
+    constexpr int P = F::P;
+    for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
+        const int j = task % P, k1 = task / P;
+        float2 r[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) r[n2] = z[F::zi(k1 * N2 + n2, j)];
+        reg_fft<N2, INV>(r);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) z[F::zi(k1 * N2 + k2, j)] = r[k2];
+    }
+    __syncthreads();
+}
+
 // tw: the twiddle table W_NT^m of the transform's sign (conjugated for INV), m < NT/2, or with
 // FULL the whole period m < NT (no sign select per twiddle).
 template <int N1, int N2, bool INV, bool FULL = false>
@@ -318,16 +336,7 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
         }
     }
     __syncthreads();
-    for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
-        const int j = task % P, k1 = task / P;
-        float2 r[N2];
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) r[n2] = z[F::zi(k1 * N2 + n2, j)];
-        reg_fft<N2, INV>(r);
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) z[F::zi(k1 * N2 + k2, j)] = r[k2];
-    }
-    __syncthreads();
+    four_step_pass_b<N1, N2, INV>(z);
 }
 
 // Row holding bin (or time sample) q after four_step.
@@ -359,40 +368,43 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v * sc;
     };
     if (a.vec4 && c0 + CT <= a.C) {
-        // each thread keeps the same four columns (FFT_THREADS is a multiple of Q) and walks
-        // rows t0, t0 + TSTEP, ...
-        constexpr int Q = CT / 4, TSTEP = FFT_THREADS / Q, PER = NT / TSTEP, B = PER < 16 ? PER : 16;
-        const int cl = 4 * (threadIdx.x % Q), t0 = threadIdx.x / Q;
-        int cut[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-        if (a.cut)
+        // First pass straight from global memory: task (j, n2) loads the column pair
+        // (c0 + 2j, c0 + 2j + 1) at rows n1 * N2 + n2 (a warp reads whole 64- or 128-byte row
+        // segments), applies window and scale, transforms over n1 in registers, twiddles, and
+        // writes the tile; only the second pass goes through shared memory.
+        __syncthreads();                                  // twiddle table
+        constexpr int P = F::P;
+        for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
+            const int j = task % P, n2 = task / P, c = c0 + 2 * j;
+            const int cut0 = a.cut ? a.cut[c] : 0x7fffffff, cut1 = a.cut ? a.cut[c + 1] : 0x7fffffff;
+            const float* xb = a.x + c;
+            float2 r[N1];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cut[i] = a.cut[c0 + cl + i];
-        const float* xb = a.x + c0 + cl;
-        const float* x2b = a.x2 ? a.x2 + c0 + cl : nullptr;
-#pragma unroll 1
-        for (int b0 = 0; b0 < PER; b0 += B) {
-            float4 v[B];
+            for (int n1 = 0; n1 < N1; ++n1)
+                r[n1] = *reinterpret_cast<const float2*>(xb + (size_t)(n1 * N2 + n2) * a.C);
+            if (a.x2) {
+                const float* x2b = a.x2 + c;
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
-                const size_t off = (size_t)(t0 + (b0 + u) * TSTEP) * a.C;
-                v[u] = *reinterpret_cast<const float4*>(xb + off);
-                if (x2b) {
-                    const float4 w = *reinterpret_cast<const float4*>(x2b + off);
-                    v[u].x += w.x; v[u].y += w.y; v[u].z += w.z; v[u].w += w.w;
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    const float2 w = *reinterpret_cast<const float2*>(x2b + (size_t)(n1 * N2 + n2) * a.C);
+                    r[n1].x += w.x;
+                    r[n1].y += w.y;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
-                const int t = t0 + (b0 + u) * TSTEP;
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int t = n1 * N2 + n2;
                 const int tau = t < (NT >> 1) ? t : NT - t;
-                float4 w = v[u];
-                w.x = tau >= cut[0] ? 0.f : w.x * sc;
-                w.y = tau >= cut[1] ? 0.f : w.y * sc;
-                w.z = tau >= cut[2] ? 0.f : w.z * sc;
-                w.w = tau >= cut[3] ? 0.f : w.w * sc;
-                *reinterpret_cast<float4*>(z + F::zi(t, cl >> 1)) = w;
+                r[n1].x = tau >= cut0 ? 0.f : r[n1].x * sc;
+                r[n1].y = tau >= cut1 ? 0.f : r[n1].y * sc;
             }
+            reg_fft<N1, false>(r);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                z[F::zi(k1 * N2 + n2, j)] = k1 == 0 ? r[0] : cmul(r[k1], tw[n2 * k1]);
         }
+        __syncthreads();
+        four_step_pass_b<N1, N2, false>(z);
     } else {
         constexpr int PER = NT * CT / FFT_THREADS, B = PER < 16 ? PER : 16;
 #pragma unroll 1
@@ -417,9 +429,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 else reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = 0.f;
             }
         }
+        __syncthreads();
+        four_step<N1, N2, false, true>(z, tw);
     }
-    __syncthreads();
-    four_step<N1, N2, false, true>(z, tw);
     // Bin k = k1 + N1 * k2 sits in row k1 * N2 + k2, its mirror NT - k in row
     // ((-k1) mod N1) * N2 + (NT/N1 - k2 - [k1 > 0]) (k > 0).  A thread keeps one column and walks
     // the bins of every G-th block k1; the G threads of a column cover all N1 blocks, and the
