@@ -426,6 +426,98 @@ def run_precision(args, dev):
     return out
 
 
+PAPER_FULL = synth.Config(80, "paper-full-9801x9801-nt2048-nf300", 99, 2048, 0.004, 300, 20, 1, 600.0)
+
+
+def run_paper_full(args, dev):
+    """The paper's Full geometry (Table 1) on one GPU: 99 x 99 = 9801 co-located sources and
+    receivers, 300 frequencies (nt = 2048, dt = 4 ms), 20 hyperbolic events.  The complex64 kernel
+    (232 GB) and then an FP16 copy (116 GB) are filled slab by slab (20 frequencies at a time,
+    generated on the device), then timed: one forward+adjoint MDC at one virtual point, and
+    Marchenko LSQR solves of 10 iterations for 1 and 20 focusing points (z = 600 m).  The paper's
+    16-node CPU figures for the same geometry are quoted beside them as context."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from synth import gpu as sgpu
+    cfg = PAPER_FULL
+    d = synth.draw(cfg)
+    ldg = -(-cfg.ns // 64) * 64
+    slab, niter = 20, 10
+    extent = synth.GRID_DX * (cfg.n_side - 1)
+    pts20 = np.random.default_rng(cfg.seed).uniform(0.25 * extent, 0.75 * extent, size=(20, 2))
+    x = torch.from_numpy(np.ascontiguousarray(synth.ricker_traces(cfg, d), np.float32)).to(dev)
+    yo = torch.empty((cfg.nt, cfg.nr, 1), device=dev)
+    xo = torch.empty((cfg.nt, cfg.ns, 1), device=dev)
+    peak, _ = peaks()
+    out = {"workload": f"paper Full geometry: nr=ns={cfg.nr} (99x99, 20 m), nt={cfg.nt}, dt={cfg.dt}, "
+                       f"nfmax={cfg.nf}, {cfg.n_events} hyperbolic events; MDC fwd+adj at nv=1; Marchenko LSQR "
+                       f"({niter} iterations) for 1 and 20 focusing points at z={cfg.z_point:.0f} m",
+           "paper_context": {"hardware": "16 nodes x 2 octa-core Xeon @ 2.90 GHz, 128 GB each (Dask)",
+                             "setup_s": 180, "one_point_inversion_s": 260, "twenty_point_inversion_s": 1760,
+                             "ms_per_mdc_derived": 6000, "solver": "10 CGLS iterations",
+                             "kernel": "300 x 9801 x 9801 complex64, 230 GB"}}
+    fm_c64 = None
+    for storage in ("c64", "c16f"):
+        torch.cuda.empty_cache()
+        need = cfg.nf * cfg.nr * ldg * BYTES_PER_COMPLEX[storage] + slab * cfg.nr * cfg.ns * 8 + (8 << 30)
+        free, _ = torch.cuda.mem_get_info()
+        if free < need:
+            out[storage] = {"skipped": f"needs {need / 1e9:.0f} GB free on the device, {free / 1e9:.0f} GB free"}
+            continue
+        t0 = time.perf_counter()
+        op = mdc.MDC.empty(cfg.nf, cfg.nr, cfg.ns, cfg.nt, cfg.dt, cfg.dr, storage=storage)
+        buf = torch.empty((slab, cfg.nr, cfg.ns), dtype=torch.complex64, device=dev)
+        for k0 in range(0, cfg.nf, slab):
+            nk = min(slab, cfg.nf - k0)
+            sgpu.kernel_slab_on_device(cfg, k0, nk, d, out=buf[:nk])
+            op.load_slab(buf[:nk], k0)
+        del buf
+        torch.cuda.empty_cache()
+        res = {"kernel_gb": cfg.nf * cfg.nr * cfg.ns * BYTES_PER_COMPLEX[storage] / 1e9,
+               "setup_s": time.perf_counter() - t0}
+        for _ in range(3):
+            op.forward(x, out=yo)
+            op.adjoint(yo, out=xo)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        for _ in range(5):
+            op.forward(x, out=yo)
+            op.adjoint(yo, out=xo)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        bytes_pair, _ = algorithmic_bytes(cfg, 1, storage)
+        res.update({"ms_per_mdc_pair": ms, "gbs": bytes_pair / ms / 1e6,
+                    "frac_of_measured_hbm": bytes_pair / ms / 1e6 / peak})
+        for nv, pts in ((1, d.points), (20, pts20)):
+            cut, fd = sgpu.focusing_inputs_on_device(cfg, pts, device=dev)
+            sol = op.marchenko(cut, fd, niter)                       # warm-up (workspace, tensor maps)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(2):
+                t1 = time.perf_counter()
+                sol = op.marchenko(cut, fd, niter)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t1)
+            r = {"s_per_solve": min(times), "iterations": sol["iters"],
+                 "final_residual": sol["resid"][sol["iters"]]}
+            if nv == 1 and storage == "c64":
+                fm_c64 = sol["f_minus"].double()
+            elif nv == 1 and fm_c64 is not None:
+                r["rel_l2_f_minus_vs_c64"] = float((sol["f_minus"].double() - fm_c64).norm() / fm_c64.norm())
+            res[f"marchenko_nv{nv}"] = r
+            del cut, fd, sol
+            if storage == "c64":
+                break          # 20 points on complex64 run on the SIMT product (minutes); FP16 only
+        op.close()
+        out[storage] = res
+    del x, yo, xo, fm_c64
+    torch.cuda.empty_cache()
+    return out
+
+
 def serve_loop(mdc, srv, arrivals, pool, horizon, drain):
     """Submit arrivals (t, nv, niter, tol, entry) as their time comes, step the server, and
     collect completed jobs; returns (completed records, jobs still queued or running)."""
@@ -684,6 +776,8 @@ def run_ours(args):
         result["precision"] = run_precision(args, dev)
     if world == 1 and not args.no_serving:
         result["serving"] = run_serving(args, dev)
+    if world == 1 and not args.no_paper_full:
+        result["paper_full"] = run_paper_full(args, dev)
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
         result["cpu_baseline"]["paper_style"] = paper_style_cpu(cfg, nv)
@@ -708,6 +802,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mdd", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-paper-full", action="store_true")
     ap.add_argument("--mdd-iters", type=int, default=10)
     ap.add_argument("--serving-config", type=int, default=5)
     ap.add_argument("--serving-rate", type=float, default=50.0)

@@ -99,6 +99,32 @@ int mdc_create_weighted(mdc_handle* out, const void* G, const double* weights, i
                         double dt, double dr, int storage, void* stream);
 
 /*
+ * mdc_create_empty -- as mdc_create, but the library-owned kernel copy starts as zeros and
+ * is filled one frequency slab at a time with mdc_load_slab.  This is for kernels larger
+ * than the free device memory left beside a full complex64 staging copy (the paper's Full
+ * geometry, Table 1: 300 frequencies of a 9801 x 9801 kernel, 230 GB in complex64, which
+ * the paper keeps partitioned by frequency over its nodes, Section "Implementing the batch
+ * matrix multiplication operator").  Same arguments and
+ * errors as mdc_create without G; blocking.
+ */
+int mdc_create_empty(mdc_handle* out, int nfmax, int nr, int ns, int nt, double dt, double dr,
+                     int storage, void* stream);
+
+/*
+ * mdc_load_slab -- copy (complex64 storage) or quantise (reduced storage, with the same
+ * per-row scales mdc_create computes) frequencies k0 .. k0+nk-1 of the kernel into the
+ * handle's copy.
+ *   G_slab  device pointer, complex64 interleaved [nk][nr][ns]: kernel frequencies k0..k0+nk-1.
+ *           Read only; the call synchronises `stream` before returning, so the caller may
+ *           reuse or free the buffer afterwards.
+ *   k0, nk  0 <= k0, nk >= 1, k0 + nk <= nfmax (MDC_ERR_ARG otherwise).
+ * Loading every frequency once gives the same operator, bit for bit, as mdc_create on the
+ * whole kernel; frequencies never loaded stay zero.  Not to be called while a product on
+ * this handle is in flight on another stream.
+ */
+int mdc_load_slab(mdc_handle h, const void* G_slab, int k0, int nk, void* stream);
+
+/*
  * mdc_forward -- y = C x (Eq. 3, left), or y = R* x with MDC_CONJ_KERNEL (Eq. 5).
  *   x  device float32 [nt][ns][nv] (input function f, integration axis ns).
  *   y  device float32 [nt][nr][nv] (output function g), fully overwritten.

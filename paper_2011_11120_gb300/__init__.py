@@ -30,6 +30,8 @@ _vp, _i, _d, _u, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c
 SIGNATURES = {
     "mdc_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i, _i, _d, _d, _i, _vp]),
     "mdc_create_weighted": (_i, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(_d), _i, _i, _i, _i, _d, _d, _i, _vp]),
+    "mdc_create_empty": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _d, _d, _i, _vp]),
+    "mdc_load_slab": (_i, [_vp, _vp, _i, _i, _vp]),
     "mdc_forward": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_adjoint": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_reserve": (_i, [_vp, _i]),
@@ -138,6 +140,24 @@ def mdc_create(G: torch.Tensor, nt: int, dt: float, dr: float, storage="c64", st
                                          w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nf, nr, ns, nt, dt, dr,
                                          st, _stream(stream)), "mdc_create_weighted")
     return h
+
+
+def mdc_create_empty(nfmax: int, nr: int, ns: int, nt: int, dt: float, dr: float, storage="c64",
+                     stream=None) -> ctypes.c_void_p:
+    """An MDC handle whose kernel copy is zero until filled by ``mdc_load_slab``."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    h = ctypes.c_void_p()
+    _check(lib().mdc_create_empty(ctypes.byref(h), nfmax, nr, ns, nt, dt, dr, st, _stream(stream)),
+           "mdc_create_empty")
+    return h
+
+
+def mdc_load_slab(h, G_slab: torch.Tensor, k0: int, stream=None) -> None:
+    """Load kernel frequencies k0 .. k0+nk-1 from a complex64 CUDA tensor G_slab[nk, nr, ns]."""
+    if G_slab.dtype != torch.complex64 or G_slab.dim() != 3:
+        raise ValueError("G_slab must be complex64 [nk, nr, ns]")
+    _check(lib().mdc_load_slab(h, _ptr(G_slab, name="G_slab"), k0, G_slab.shape[0], _stream(stream)),
+           "mdc_load_slab")
 
 
 def mdc_forward(h, x: torch.Tensor, y: torch.Tensor, nv: int, flags: int = 0, stream=None) -> None:
@@ -269,6 +289,18 @@ class MDC:
         self.nf, self.nr, self.ns = G.shape
         self.nt, self.dt, self.dr = nt, dt, dr
         self.h = mdc_create(G, nt, dt, dr, storage, stream, weights)
+
+    @classmethod
+    def empty(cls, nfmax: int, nr: int, ns: int, nt: int, dt: float, dr: float, storage="c64", stream=None):
+        """An operator with a zero kernel, to be filled frequency slab by slab with ``load_slab``."""
+        op = cls.__new__(cls)
+        op.nf, op.nr, op.ns = nfmax, nr, ns
+        op.nt, op.dt, op.dr = nt, dt, dr
+        op.h = mdc_create_empty(nfmax, nr, ns, nt, dt, dr, storage, stream)
+        return op
+
+    def load_slab(self, G_slab: torch.Tensor, k0: int, stream=None) -> None:
+        mdc_load_slab(self.h, G_slab, k0, stream)
 
     def forward(self, x: torch.Tensor, out: Optional[torch.Tensor] = None, conj=False, stream=None):
         nv = x.shape[2]

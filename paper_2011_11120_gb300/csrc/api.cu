@@ -108,7 +108,8 @@ static int create_plan(mdc_handle* out, const void* G, const double* weights, in
                        double dt, double dr, int storage, void* stream) {
     if (!out) return MDC_ERR_ARG;
     *out = nullptr;
-    if (!G || nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
+    // G == nullptr: an empty (zero) kernel copy, filled later by mdc_load_slab
+    if (nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
     if (!(dt > 0.0) || !(dr > 0.0) || !std::isfinite(dt) || !std::isfinite(dr)) return MDC_ERR_ARG;
     if (storage < MDC_C64 || storage > MDC_C32S) return MDC_ERR_ARG;
     if ((int64_t)nr * nfmax > (int64_t)1 << 31) return MDC_ERR_ARG;
@@ -128,7 +129,12 @@ static int create_plan(mdc_handle* out, const void* G, const double* weights, in
         if (e == cudaSuccess) e = cudaMemcpyAsync(w_d, wf.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // wf is a host temporary
     }
-    if (storage == MDC_C64) {
+    if (!G) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->G, 0, rowbytes * nr * nfmax, s);
+        if (e == cudaSuccess && storage != MDC_C64) e = cudaMalloc(&p->gscale, sizeof(float) * (size_t)nr * nfmax);
+        if (e == cudaSuccess && storage != MDC_C64)
+            e = cudaMemsetAsync(p->gscale, 0, sizeof(float) * (size_t)nr * nfmax, s);
+    } else if (storage == MDC_C64) {
         if (e == cudaSuccess) e = cudaMemcpy2DAsync(p->G, rowbytes, G, (size_t)ns * sizeof(float2),
                                                     (size_t)ns * sizeof(float2), (size_t)nr * nfmax,
                                                     cudaMemcpyDeviceToDevice, s);
@@ -172,12 +178,41 @@ static int create_plan(mdc_handle* out, const void* G, const double* weights, in
 
 extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int ns, int nt,
                           double dt, double dr, int storage, void* stream) {
+    if (!G) return MDC_ERR_ARG;
     return create_plan(out, G, nullptr, nfmax, nr, ns, nt, dt, dr, storage, stream);
+}
+
+extern "C" int mdc_create_empty(mdc_handle* out, int nfmax, int nr, int ns, int nt, double dt, double dr,
+                                int storage, void* stream) {
+    return create_plan(out, nullptr, nullptr, nfmax, nr, ns, nt, dt, dr, storage, stream);
+}
+
+extern "C" int mdc_load_slab(mdc_handle h, const void* G_slab, int k0, int nk, void* stream) {
+    if (!h || !G_slab || k0 < 0 || nk < 1 || k0 + nk > h->nf) return MDC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mdc_plan* p = h;
+    const int64_t row0 = (int64_t)k0 * p->nr, nrows = (int64_t)nk * p->nr;
+    cudaError_t e = cudaSuccess;
+    if (p->storage == MDC_C64) {
+        const size_t rowbytes = (size_t)p->ldg * sizeof(float2);
+        char* dst = static_cast<char*>(p->G) + (size_t)row0 * rowbytes;
+        e = cudaMemcpy2DAsync(dst, rowbytes, G_slab, (size_t)p->ns * sizeof(float2), (size_t)p->ns * sizeof(float2),
+                              (size_t)nrows, cudaMemcpyDeviceToDevice, s);
+    } else {
+        launch_quantize_rows(p, static_cast<const float2*>(G_slab), nullptr, row0, nrows, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);       // the caller may reuse the slab buffer
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return MDC_ERR_CUDA;
+    }
+    return MDC_OK;
 }
 
 extern "C" int mdc_create_weighted(mdc_handle* out, const void* G, const double* weights, int nfmax, int nr,
                                    int ns, int nt, double dt, double dr, int storage, void* stream) {
-    if (!weights) return MDC_ERR_ARG;
+    if (!G || !weights) return MDC_ERR_ARG;
     for (int i = 0; i < ns; ++i)
         if (!std::isfinite(weights[i]) || weights[i] < 0.0) return MDC_ERR_ARG;
     return create_plan(out, G, weights, nfmax, nr, ns, nt, dt, dr, storage, stream);

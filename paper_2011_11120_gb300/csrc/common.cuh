@@ -148,6 +148,7 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol);
 
 // Quantise a complex64 kernel [nf][nr][ns] into the plan's reduced-storage copy and row scales.
 void launch_quantize(mdc_plan* p, const float2* G, const float* w, cudaStream_t s);
+void launch_quantize_rows(mdc_plan* p, const float2* G, const float* w, int64_t row0, int64_t nrows, cudaStream_t s);
 
 // Bytes of one stored complex value (MDC_C32S: 4 in each of its two planes).
 inline int storage_bytes(int storage) {

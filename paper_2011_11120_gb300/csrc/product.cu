@@ -14,6 +14,7 @@
 // Many columns (GEMM regime): a tiled FP32 complex GEMM (64x64 complex tile per
 // CTA, 4x4 per thread), the adjoint tile loader conjugating and transposing.
 #include "common.cuh"
+#include <cstdlib>
 
 namespace mdc {
 
@@ -377,6 +378,207 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     }
 }
 
+// ---- chunked GEMV for long rows or columns
+// When X(w) (forward) or Y(w) (adjoint) would take more than GEMV_STAGE_MAX bytes of shared
+// memory -- e.g. 9801 x 9801 kernels, where a whole complex row is 78 KB per column and only one
+// or two CTAs would fit on an SM, too few loads in flight to stream HBM -- it is staged in
+// chunks of GEMV_CHUNK_BYTES instead.  Each lane still visits its vectors (forward) or rows
+// (adjoint) in ascending order and the warp and CTA reductions are unchanged, so the chunked
+// kernels give the same bits as the kernels above.
+constexpr int GEMV_STAGE_MAX = 48 * 1024;
+constexpr int GEMV_CHUNK_BYTES = 32 * 1024;
+constexpr int FWD_CHUNK_ROWS = 32;     // rows per CTA of the chunked forward (4 per warp, in registers)
+
+// Forward chunk: CHV vectors of every row (a multiple of 128, the 4-way unrolled lane stride).
+template <int FMT, int NVC>
+struct FwdChunk {
+    static constexpr int CHV = ((GEMV_CHUNK_BYTES / (8 * NVC * Fmt<FMT>::CPV)) / 128) * 128;
+    static_assert(CHV >= 128, "forward chunk too small");
+};
+// Adjoint chunk: CHR rows (a multiple of 4 * 8 warps, the unrolled row stride).
+template <int NVC>
+struct AdjChunk {
+    static constexpr int CHR = ((GEMV_CHUNK_BYTES / (8 * NVC)) / 32) * 32;
+};
+
+// Forward: the CTA's 32 rows, warp w owning rows r0 + w + 8 q (q < 4) with their partial sums
+// held in registers across chunks.
+template <int FMT, int NVC>
+__global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_chunked(
+    const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
+    const float2* __restrict__ X, int ldi, int voff_i,
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo) {
+    constexpr int CPV = Fmt<FMT>::CPV;
+    constexpr int CHV = FwdChunk<FMT, NVC>::CHV;
+    constexpr int W = GEMV_THREADS / 32;
+    constexpr int RPW = FWD_CHUNK_ROWS / W;
+    if (active && *active == 0) return;
+    extern __shared__ __align__(16) float2 xs[];   // [CPV][CHV][NVC]
+    const int k = blockIdx.y;
+    const int nvec = ldg / CPV;
+    const float2* Xk = X + (size_t)k * ns * ldi + voff_i;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rw = blockIdx.x * FWD_CHUNK_ROWS + warp;
+    float2 acc[RPW][NVC];
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) acc[q][v] = make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < nvec; c0 += CHV) {
+        const int c1 = min(c0 + CHV, nvec);
+        __syncthreads();                               // the previous chunk has been consumed
+        for (int e = threadIdx.x; e < (c1 - c0) * CPV * NVC; e += GEMV_THREADS) {
+            const int sl = e / NVC, v = e - sl * NVC;
+            const int i = sl / CPV, j = sl - i * CPV;
+            const int s = c0 * CPV + sl;
+            xs[(j * CHV + i) * NVC + v] = s < ns ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int r = rw + W * q;
+            if (r >= nr) break;                        // warp-uniform
+            const uint4* g = G + ((size_t)k * nr + r) * nvec;
+            int i = c0 + lane;
+            for (; i + 96 < c1; i += 128) {
+                float2 c4[4][CPV];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) load_decode<FMT>(g, i + 32 * u, lo, c4[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int j = 0; j < CPV; ++j)
+#pragma unroll
+                        for (int v = 0; v < NVC; ++v)
+                            cfma(acc[q][v], c4[u][j], xs[(j * CHV + i - c0 + 32 * u) * NVC + v]);
+                }
+            }
+            for (; i < c1; i += 32) {
+                float2 c[CPV];
+                load_decode<FMT>(g, i, lo, c);
+#pragma unroll
+                for (int j = 0; j < CPV; ++j)
+#pragma unroll
+                    for (int v = 0; v < NVC; ++v) cfma(acc[q][v], c[j], xs[(j * CHV + i - c0) * NVC + v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+        const int r = rw + W * q;
+        if (r >= nr) break;
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                acc[q][v].x += __shfl_xor_sync(0xffffffffu, acc[q][v].x, off);
+                acc[q][v].y += __shfl_xor_sync(0xffffffffu, acc[q][v].y, off);
+            }
+        }
+        if (lane == 0) {
+            const float sc = (FMT == MDC_C64) ? 1.f : gscale[(size_t)k * nr + r];
+            float2* y = Y + ((size_t)k * nr + r) * ldo + voff_o;
+#pragma unroll
+            for (int v = 0; v < NVC; ++v) y[v] = make_float2(acc[q][v].x * sc, acc[q][v].y * sc);
+        }
+    }
+}
+
+// Adjoint: Y(w) (row scales folded in) staged CHR rows at a time; per-lane column sums persist
+// across chunks.
+template <int FMT, int NVC>
+__global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_chunked(
+    const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
+    const float2* __restrict__ Yin, int ldi, int voff_i,
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo) {
+    constexpr int CPV = Fmt<FMT>::CPV;
+    constexpr int TILE = 32 * CPV;
+    constexpr int W = GEMV_THREADS / 32;
+    constexpr int CHR = AdjChunk<NVC>::CHR;
+    if (active && *active == 0) return;
+    extern __shared__ __align__(16) float2 ys[];   // [CHR][NVC], then reduction space
+    const int k = blockIdx.y;
+    const int s0 = blockIdx.x * TILE;
+    const float2* Yk = Yin + (size_t)k * nr * ldi + voff_i;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvec = ldg / CPV;
+    const bool live = s0 + CPV * lane < ldg;
+    const uint4* g = G + (size_t)k * nr * nvec + (s0 / CPV) + lane;
+    float2 acc[CPV][NVC];
+#pragma unroll
+    for (int j = 0; j < CPV; ++j)
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) acc[j][v] = make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < nr; c0 += CHR) {
+        const int c1 = min(c0 + CHR, nr);
+        __syncthreads();                               // the previous chunk has been consumed
+        for (int e = threadIdx.x; e < (c1 - c0) * NVC; e += GEMV_THREADS) {
+            const int rl = e / NVC, v = e - rl * NVC;
+            const int r = c0 + rl;
+            float2 y = Yk[(size_t)r * ldi + v];
+            if (FMT != MDC_C64) {
+                const float sc = gscale[(size_t)k * nr + r];
+                y.x *= sc;
+                y.y *= sc;
+            }
+            ys[e] = y;
+        }
+        __syncthreads();
+        if (live) {
+            int r = c0 + warp;
+            for (; r + 3 * W < c1; r += 4 * W) {
+                float2 c4[4][CPV];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) load_decode<FMT>(g, (size_t)(r + u * W) * nvec, lo, c4[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int v = 0; v < NVC; ++v) {
+                        const float2 y = ys[(r - c0 + u * W) * NVC + v];
+#pragma unroll
+                        for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c4[u][j], y);
+                    }
+                }
+            }
+            for (; r < c1; r += W) {
+                float2 c[CPV];
+                load_decode<FMT>(g, (size_t)r * nvec, lo, c);
+#pragma unroll
+                for (int v = 0; v < NVC; ++v) {
+                    const float2 y = ys[(r - c0) * NVC + v];
+#pragma unroll
+                    for (int j = 0; j < CPV; ++j) cfma_conj(acc[j][v], c[j], y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float2* red = ys;   // reuse: W * TILE * NVC float2 (the launcher sizes shared memory for it)
+#pragma unroll
+    for (int j = 0; j < CPV; ++j)
+#pragma unroll
+        for (int v = 0; v < NVC; ++v) red[(warp * TILE + CPV * lane + j) * NVC + v] = acc[j][v];
+    __syncthreads();
+    for (int e = threadIdx.x; e < TILE * NVC; e += GEMV_THREADS) {
+        const int sl = e / NVC, v = e - sl * NVC;
+        const int s = s0 + sl;
+        float2 tot = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < W; ++w) tot = cadd(tot, red[(w * TILE + sl) * NVC + v]);
+        if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
+    }
+}
+
+// MDC_GEMV_CHUNK=0 in the environment stages whole rows whenever they fit (for comparisons).
+bool gemv_chunk_allowed() {
+    static int env = -1;
+    if (env < 0) {
+        const char* e = getenv("MDC_GEMV_CHUNK");
+        env = (e && e[0] == '0') ? 0 : 1;
+    }
+    return env == 1;
+}
+
 // ------------------------------------------------------------------ SIMT complex GEMM
 constexpr int GBM = 64, GBN = 64, GBK = 8;
 
@@ -502,6 +704,14 @@ template <int FMT, int NVC>
 void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                      int voff_o, cudaStream_t s, const int* active) {
     const size_t smem = (size_t)p->ldg * NVC * sizeof(float2);
+    if (smem > (size_t)GEMV_STAGE_MAX && gemv_chunk_allowed()) {
+        constexpr size_t csmem = (size_t)Fmt<FMT>::CPV * FwdChunk<FMT, NVC>::CHV * NVC * sizeof(float2);
+        dim3 grid((p->nr + FWD_CHUNK_ROWS - 1) / FWD_CHUNK_ROWS, p->nf);
+        gemv_fwd_chunked<FMT, NVC><<<grid, GEMV_THREADS, csmem, s>>>(
+            reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
+            ldo, voff_o, active, lo_plane_vec(p));
+        return;
+    }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(gemv_fwd<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -530,6 +740,21 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
     constexpr int TILE = 32 * Fmt<FMT>::CPV;
     size_t smem = (size_t)p->nr * NVC * sizeof(float2);
     const size_t red = (size_t)(GEMV_THREADS / 32) * TILE * NVC * sizeof(float2);
+    if (smem > (size_t)GEMV_STAGE_MAX && gemv_chunk_allowed()) {
+        size_t csmem = (size_t)AdjChunk<NVC>::CHR * NVC * sizeof(float2);
+        if (csmem < red) csmem = red;
+        static bool cattr = false;
+        if (!cattr) {
+            cudaFuncSetAttribute(gemv_adj_chunked<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 220 * 1024);
+            cattr = true;
+        }
+        dim3 grid((unsigned)((p->ldg + TILE - 1) / TILE), p->nf);
+        gemv_adj_chunked<FMT, NVC><<<grid, GEMV_THREADS, csmem, s>>>(
+            reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
+            ldo, voff_o, active, lo_plane_vec(p));
+        return;
+    }
     if (smem < red) smem = red;
     static bool attr = false;
     if (!attr) {
@@ -556,7 +781,8 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
 bool gemv_fits(const mdc_plan* p, bool adjoint, int ncol, int cpv) {
     const int64_t stage = (int64_t)(adjoint ? p->nr : p->ldg) * ncol * (int64_t)sizeof(float2);
     const int64_t red = (int64_t)(GEMV_THREADS / 32) * 32 * cpv * ncol * (int64_t)sizeof(float2);
-    return ncol <= gemv_max_columns() && stage <= 200 * 1024 && red <= 200 * 1024;
+    const bool staged = stage <= 200 * 1024 || (stage > GEMV_STAGE_MAX && gemv_chunk_allowed());
+    return ncol <= gemv_max_columns() && staged && red <= 200 * 1024;
 }
 
 // path: PATH_GEMV or PATH_SIMT (PATH_AUTO: GEMV when it fits, else SIMT)
@@ -644,7 +870,7 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
 template <int FMT>
 __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ G, int ns, int ldg,
                                                      unsigned char* __restrict__ Q, float* __restrict__ scale,
-                                                     const float* __restrict__ w) {
+                                                     const float* __restrict__ w, size_t lo_plane) {
     constexpr float QMAX = (FMT == MDC_C16F || FMT == MDC_C32S) ? 32768.f : (FMT == MDC_CBF16 ? 1.f : 448.f);
     const size_t row = blockIdx.x;
     const float2* g = G + row * ns;
@@ -680,8 +906,7 @@ __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ 
             const __half2 hi = __floats2half2_rn(v.x, v.y);
             const float2 h = __half22float2(hi);
             reinterpret_cast<__half2*>(Q)[row * ldg + s] = hi;
-            reinterpret_cast<__half2*>(Q)[(size_t)gridDim.x * ldg + row * ldg + s] =
-                __floats2half2_rn(v.x - h.x, v.y - h.y);
+            reinterpret_cast<__half2*>(Q)[lo_plane + row * ldg + s] = __floats2half2_rn(v.x - h.x, v.y - h.y);
         } else if constexpr (FMT == MDC_CBF16) {
             reinterpret_cast<__nv_bfloat162*>(Q)[row * ldg + s] = __floats2bfloat162_rn(v.x, v.y);
         } else {
@@ -691,16 +916,25 @@ __global__ void __launch_bounds__(256) quantize_rows(const float2* __restrict__ 
     }
 }
 
-void launch_quantize(mdc_plan* p, const float2* G, const float* w, cudaStream_t s) {
-    const unsigned rows = (unsigned)((int64_t)p->nf * p->nr);
-    unsigned char* Q = reinterpret_cast<unsigned char*>(p->G);
+// Quantise kernel rows [row0, row0 + nrows) of the [nf * nr] rows from G (which holds exactly
+// those rows); the split format's lo plane sits one full plane (nf * nr * ldg values) above hi.
+void launch_quantize_rows(mdc_plan* p, const float2* G, const float* w, int64_t row0, int64_t nrows, cudaStream_t s) {
+    const size_t vb = p->storage == MDC_CE4M3 ? 2 : 4;        // bytes per stored complex value (one plane)
+    unsigned char* Q = reinterpret_cast<unsigned char*>(p->G) + (size_t)row0 * p->ldg * vb;
+    float* sc = p->gscale + row0;
+    const size_t lo = (size_t)p->nf * p->nr * p->ldg;
+    const unsigned rows = (unsigned)nrows;
     switch (p->storage) {
-        case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
-        case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
-        case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
-        case MDC_C32S: quantize_rows<MDC_C32S><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, p->gscale, w); break;
+        case MDC_C16F: quantize_rows<MDC_C16F><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, sc, w, lo); break;
+        case MDC_CBF16: quantize_rows<MDC_CBF16><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, sc, w, lo); break;
+        case MDC_CE4M3: quantize_rows<MDC_CE4M3><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, sc, w, lo); break;
+        case MDC_C32S: quantize_rows<MDC_C32S><<<rows, 256, 0, s>>>(G, p->ns, (int)p->ldg, Q, sc, w, lo); break;
         default: break;
     }
+}
+
+void launch_quantize(mdc_plan* p, const float2* G, const float* w, cudaStream_t s) {
+    launch_quantize_rows(p, G, w, 0, (int64_t)p->nf * p->nr, s);
 }
 
 }  // namespace mdc

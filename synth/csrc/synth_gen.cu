@@ -3,9 +3,9 @@
 //     G[k][r][s] = scale * sum_e a_e W(f_k) exp(-i 2 pi f_k tau_e(r, s)),
 //     tau_e = sqrt(t0_e^2 + |x_r - x_s|^2 / v_e^2),  f_k = k df,
 // on a co-located square grid (flat index iy * n_side + ix, spacing dx).
-// The phase in cycles, k * df * tau_e, is carried as an exact-as-possible float64
-// fraction (incremented by frac(df * tau_e) per bin), so the float32 sine/cosine
-// of the reduced argument leaves only float32 rounding in G.  W(f_k) * scale is
+// The phase in cycles, k * df * tau_e, is reduced in float64 (to frac(k * frac(df * tau_e)),
+// or, in the rectangular variant, incremented by frac(df * tau_e) per bin), so the float32
+// sine/cosine of the reduced argument leaves only float32 rounding in G.  W(f_k) * scale is
 // supplied by the caller as a float64 table.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,7 +21,10 @@ struct SynthParams {
 
 __constant__ double c_wscale[SYNTH_MAX_NF];
 
-__global__ void synth_kernel(float2* __restrict__ G, SynthParams P) {
+// Frequencies k0 .. k0+P.nf-1 (c_wscale holds their weights from index 0).  The phase of
+// bin k is frac(k * frac(df * tau)), evaluated per bin in float64, so a slab is
+// bit-identical to the same frequencies of the whole kernel.
+__global__ void synth_kernel(float2* __restrict__ G, SynthParams P, int k0) {
     const int64_t n = (int64_t)P.n_side * P.n_side;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n * n) return;
@@ -29,33 +32,33 @@ __global__ void synth_kernel(float2* __restrict__ G, SynthParams P) {
     const double ddx = P.dx * (double)((r % P.n_side) - (s % P.n_side));
     const double ddy = P.dx * (double)((r / P.n_side) - (s / P.n_side));
     const double d2 = ddx * ddx + ddy * ddy;
-    double step[SYNTH_MAX_EVENTS], cur[SYNTH_MAX_EVENTS];
+    double step[SYNTH_MAX_EVENTS];
     for (int e = 0; e < P.E; ++e) {
         const double tau = sqrt(P.t0[e] * P.t0[e] + d2 / (P.vel[e] * P.vel[e]));
         const double ph = P.df * tau;
         step[e] = ph - floor(ph);
-        cur[e] = 0.0;
     }
     for (int k = 0; k < P.nf; ++k) {
+        const double kk = (double)(k0 + k);
         double re = 0.0, im = 0.0;
         for (int e = 0; e < P.E; ++e) {
             float sn, cs;
-            const double c = cur[e] - rint(cur[e]);
+            const double cyc = kk * step[e];
+            const double c = cyc - rint(cyc);
             sincospif((float)(2.0 * c), &sn, &cs);
             re += P.amp[e] * (double)cs;
             im -= P.amp[e] * (double)sn;
-            double nx = cur[e] + step[e];
-            cur[e] = nx >= 1.0 ? nx - 1.0 : nx;
         }
         const double w = c_wscale[k];
         G[((int64_t)k * n + r) * n + s] = make_float2((float)(w * re), (float)(w * im));
     }
 }
 
-extern "C" int synth_kernel_c64(void* G, int nf, int n_side, double dx, double df, int E,
-                                const double* t0, const double* vel, const double* amp,
-                                const double* wscale, void* stream) {
-    if (!G || nf < 1 || nf > SYNTH_MAX_NF || n_side < 1 || E < 1 || E > SYNTH_MAX_EVENTS) return -1;
+// G [nf][n][n] receives frequencies k0 .. k0+nf-1; wscale[nf] their weights.
+extern "C" int synth_kernel_slab_c64(void* G, int k0, int nf, int n_side, double dx, double df, int E,
+                                     const double* t0, const double* vel, const double* amp,
+                                     const double* wscale, void* stream) {
+    if (!G || k0 < 0 || nf < 1 || nf > SYNTH_MAX_NF || n_side < 1 || E < 1 || E > SYNTH_MAX_EVENTS) return -1;
     SynthParams P{};
     P.nf = nf; P.n_side = n_side; P.E = E; P.dx = dx; P.df = df;
     for (int e = 0; e < E; ++e) { P.t0[e] = t0[e]; P.vel[e] = vel[e]; P.amp[e] = amp[e]; }
@@ -66,10 +69,16 @@ extern "C" int synth_kernel_c64(void* G, int nf, int n_side, double dx, double d
     const int64_t n = (int64_t)n_side * n_side;
     const int64_t total = n * n;
     const int threads = 256;
-    synth_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>((float2*)G, P);
+    synth_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>((float2*)G, P, k0);
     if (cudaGetLastError() != cudaSuccess) return -3;
     if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
     return 0;
+}
+
+extern "C" int synth_kernel_c64(void* G, int nf, int n_side, double dx, double df, int E,
+                                const double* t0, const double* vel, const double* amp,
+                                const double* wscale, void* stream) {
+    return synth_kernel_slab_c64(G, 0, nf, n_side, dx, df, E, t0, vel, amp, wscale, stream);
 }
 
 // Rectangular variant: rows and columns are arbitrary point sets (x, y in m), e.g. surface

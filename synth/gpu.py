@@ -30,6 +30,10 @@ def _load():
         L.synth_kernel_c64.restype = ctypes.c_int
         L.synth_kernel_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
+        L.synth_kernel_slab_c64.restype = ctypes.c_int
+        L.synth_kernel_slab_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp,
+                                            ctypes.c_void_p]
         L.synth_kernel_rect_c64.restype = ctypes.c_int
         L.synth_kernel_rect_c64.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
                                             ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, ctypes.c_void_p]
@@ -55,6 +59,30 @@ def kernel_on_device(cfg: synth.Config, d: synth.Draw = None, device="cuda", out
                             1.0 / (cfg.nt * cfg.dt), len(t0), dp(t0), dp(vel), dp(amp), dp(ws), stream)
     if st != 0:
         raise RuntimeError(f"synth_kernel_c64 failed ({st})")
+    return out
+
+
+def kernel_slab_on_device(cfg: synth.Config, k0: int, nk: int, d: synth.Draw = None, device="cuda",
+                          out=None) -> torch.Tensor:
+    """complex64 G[nk, nr, ns]: frequencies k0 .. k0+nk-1 of ``kernel_on_device(cfg)``, bit for bit,
+    for kernels too large to generate whole (the complex64 copy is assembled slab by slab)."""
+    if d is None:
+        d = synth.draw(cfg)
+    if k0 < 0 or nk < 1 or k0 + nk > cfg.nf:
+        raise ValueError("slab outside the kernel's frequencies")
+    L = _load()
+    if out is None:
+        out = torch.empty((nk, cfg.nr, cfg.ns), dtype=torch.complex64, device=device)
+    ws = np.ascontiguousarray((synth.ricker_spectrum(cfg.freqs) * d.scale)[k0:k0 + nk], dtype=np.float64)
+    t0 = np.ascontiguousarray(d.t0, np.float64)
+    vel = np.ascontiguousarray(d.vel, np.float64)
+    amp = np.ascontiguousarray(d.amp, np.float64)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = L.synth_kernel_slab_c64(ctypes.c_void_p(out.data_ptr()), k0, nk, cfg.n_side, synth.GRID_DX,
+                                 1.0 / (cfg.nt * cfg.dt), len(t0), dp(t0), dp(vel), dp(amp), dp(ws), stream)
+    if st != 0:
+        raise RuntimeError(f"synth_kernel_slab_c64 failed ({st})")
     return out
 
 
