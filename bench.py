@@ -501,8 +501,16 @@ def run_paper_full(args, dev):
                 sol = op.marchenko(cut, fd, niter)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t1)
+            mdc.mdc_timing(op.h, True)                              # device time per kernel class, one more solve
+            op.marchenko(cut, fd, niter)
+            torch.cuda.synchronize()
+            split = {}
+            for cls in ("rfft", "product_fwd", "product_adj", "irfft", "solver"):
+                t, n = mdc.mdc_timing_read(op.h, cls)
+                split[cls] = {"ms": t, "launches": n}
+            mdc.mdc_timing(op.h, False)
             r = {"s_per_solve": min(times), "iterations": sol["iters"],
-                 "final_residual": sol["resid"][sol["iters"]]}
+                 "final_residual": sol["resid"][sol["iters"]], "device_ms_per_kernel_class": split}
             if nv == 1 and storage == "c64":
                 fm_c64 = sol["f_minus"].double()
             elif nv == 1 and fm_c64 is not None:

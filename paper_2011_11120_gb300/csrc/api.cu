@@ -155,13 +155,18 @@ static int create_plan(mdc_handle* out, const void* G, const double* weights, in
     if (e == cudaSuccess) e = cudaMalloc(&p->err_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->err_flag, 0, sizeof(int), s);
     if (e == cudaSuccess) {
-        std::vector<float2> tw(nt / 2);
-        for (int j = 0; j < nt / 2; ++j) {
+        // W_nt^j for j < nt/2, then W_{nt/2}^m and its conjugate for m < nt/2 (half-length transforms)
+        const int h = nt / 2;
+        std::vector<float2> tw(3 * (size_t)h);
+        for (int j = 0; j < h; ++j) {
             const double ang = -2.0 * M_PI * (double)j / (double)nt;
             tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            const double angh = -2.0 * M_PI * (double)j / (double)h;
+            tw[h + j] = make_float2((float)std::cos(angh), (float)std::sin(angh));
+            tw[2 * h + j] = make_float2((float)std::cos(angh), -(float)std::sin(angh));
         }
-        e = cudaMalloc(&p->tw, sizeof(float2) * (nt / 2));
-        if (e == cudaSuccess) e = cudaMemcpyAsync(p->tw, tw.data(), sizeof(float2) * (nt / 2),
+        e = cudaMalloc(&p->tw, sizeof(float2) * tw.size());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->tw, tw.data(), sizeof(float2) * tw.size(),
                                                   cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }

@@ -65,7 +65,8 @@ struct mdc_plan {
     int64_t ldg;                // row pitch of the kernel copy, in complex elements
     void* G = nullptr;          // library-owned kernel [nf][nr][ldg] in `storage` format
     float* gscale = nullptr;    // [nf][nr] per-row scales (reduced storage), else null
-    float2* tw = nullptr;       // [nt/2] e^{-2 pi i j/nt}, from host float64
+    float2* tw = nullptr;       // [nt/2] e^{-2 pi i j/nt}, then [nt/2] e^{-2 pi i m/(nt/2)} and [nt/2] its
+                                // conjugate (half-length transforms), from host float64
     // scratch spectra, sized for nv_cap columns
     int nv_cap = 0;
     float2* specA = nullptr;    // [nf][max(nr,ns)][nv_cap]

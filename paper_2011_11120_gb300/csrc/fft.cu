@@ -649,6 +649,305 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ half-length real transforms
+// nt = 2 * N1 * N2 (2048 with N1 = N2 = 32): one real column x per complex sequence
+// z[n] = x[2n] + i x[2n+1] of length NC = nt / 2, transformed by the four-step DFT above.
+// With E and O the spectra of the even and odd samples (period NC),
+//   Z[k] = E[k] + i O[k],  E[k] = (Z[k] + conj Z[NC-k]) / 2,  O[k] = (Z[k] - conj Z[NC-k]) / (2i),
+//   X[k] = E[k] + W_nt^k O[k]  (k < NC),   X[NC] = E[0] - O[0];
+// the inverse builds Z[k] = (X[k] + conj X[NC-k]) + i (X[k] - conj X[NC-k]) W_nt^-k and takes the
+// unnormalised inverse DFT of length NC, whose real and imaginary parts are nt times the even and
+// odd samples.  A CTA holds P columns; the tile is the same as the nt = NC four-step kernels'.
+
+template <int N1, int N2>
+struct HalfStep {
+    using F = FourStep<N1, N2>;
+    static constexpr int NC = F::NT;               // complex length
+    static constexpr int NT = 2 * NC;              // real length
+    static constexpr int P = F::P;                 // columns per CTA
+    // the tile only: the twiddles W_NC^m come from the plan's table (a.tw + NC, conjugates at
+    // a.tw + 2 NC), read through L1
+    static constexpr size_t smem = (size_t)F::ZSIZE * sizeof(float2);
+};
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
+    using H = HalfStep<N1, N2>;
+    using F = typename H::F;
+    constexpr int NC = H::NC, NT = H::NT, P = H::P;
+    if (a.active && *a.active == 0) return;
+    extern __shared__ __align__(16) float2 z[];
+    const float2* __restrict__ twc = a.tw + NC;       // W_NC^m, m < NC
+    const int c0 = blockIdx.x * P;
+    const float sc = coef(a.scale);
+    // Pass A straight from global memory: task (j, n2) reads samples 2n and 2n + 1 of column
+    // c0 + j for n = n1 * N2 + n2, applies window and scale, and transforms over n1.
+    for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
+        const int j = task % P, n2 = task / P, c = c0 + j;
+        float2 r[N1];
+        if (c < a.C) {
+            const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+            const float* xb = a.x + c;
+            const float* x2b = a.x2 ? a.x2 + c : nullptr;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int t = 2 * (n1 * N2 + n2);
+                r[n1] = make_float2(xb[(size_t)t * a.C], xb[(size_t)(t + 1) * a.C]);
+            }
+            if (x2b) {
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    const int t = 2 * (n1 * N2 + n2);
+                    r[n1].x += x2b[(size_t)t * a.C];
+                    r[n1].y += x2b[(size_t)(t + 1) * a.C];
+                }
+            }
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int t = 2 * (n1 * N2 + n2);
+                const int tau0 = t < NC ? t : NT - t, tau1 = t + 1 < NC ? t + 1 : NT - t - 1;
+                r[n1].x = tau0 >= cut ? 0.f : r[n1].x * sc;
+                r[n1].y = tau1 >= cut ? 0.f : r[n1].y * sc;
+            }
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) r[n1] = make_float2(0.f, 0.f);
+        }
+        reg_fft<N1, false>(r);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) z[F::zi(k1 * N2 + n2, j)] = k1 == 0 ? r[0] : cmul(r[k1], twc[n2 * k1]);
+    }
+    __syncthreads();
+    four_step_pass_b<N1, N2, false>(z);
+    // Z[k] sits in row (k % N1) * N2 + k / N1.  Thread (cl, g) writes the bins k = k1 + N1 * k2 of
+    // column c0 + cl for k1 = g, g + G, ...
+    constexpr int G = FFT_THREADS / P;
+    const int cl = threadIdx.x % P, g = threadIdx.x / P, c = c0 + cl;
+    if (c >= a.C) return;
+    const int s = c / a.nv, v = c - s * a.nv;
+    float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
+    const size_t kstride = (size_t)a.S * a.ldv;
+    for (int k1 = g; k1 < N1 && k1 < a.nf; k1 += G) {
+        for (int k = k1, k2 = 0; k < a.nf; k += N1, ++k2) {
+            float2 X;
+            if (k >= NC) {                                     // Nyquist bin k = NC
+                const float2 Z0 = z[F::zi(0, cl)];
+                X = make_float2(Z0.x - Z0.y, 0.f);
+            } else {
+                const float2 Z = z[F::zi(k1 * N2 + k2, cl)];
+                const int km = (NC - k) & (NC - 1);
+                const float2 Zm = z[F::zi((km % N1) * N2 + km / N1, cl)];
+                const float2 E = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+                const float2 O = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
+                X = cadd(E, cmul(O, a.tw[k]));
+            }
+            if (a.conj) X.y = -X.y;
+            dst[(size_t)k * kstride] = X;
+        }
+    }
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a) {
+    using H = HalfStep<N1, N2>;
+    using F = typename H::F;
+    constexpr int NC = H::NC, NT = H::NT, P = H::P;
+    if (a.active && *a.active == 0) return;
+    extern __shared__ __align__(16) float2 z[];
+    double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
+    const float2* __restrict__ twc = a.tw + 2 * NC;   // conj W_NC^m, m < NC
+    const int c0 = blockIdx.x * P;
+    // Item (kk, j), kk <= NC / 2, reads X[kk] and X[NC - kk] of column c0 + j and writes Z[kk]
+    // and Z[NC - kk]; bins >= nf are zero, DC and Nyquist lose their imaginary parts.
+    {
+        constexpr int ITEMS = (NC / 2 + 1) * P, BL = 4;
+        const size_t kstride = (size_t)a.S * a.ldv;
+#pragma unroll 1
+        for (int b0 = 0; b0 < ITEMS; b0 += BL * FFT_THREADS) {
+          float2 Al[BL], Bl[BL];
+#pragma unroll
+          for (int u = 0; u < BL; ++u) {                 // loads first, BL items in flight
+            const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+            Al[u] = make_float2(0.f, 0.f);
+            Bl[u] = Al[u];
+            const int j = idx % P, kk = idx / P, c = c0 + j;
+            if (idx < ITEMS && c < a.C) {
+                const int sp = c / a.nv, vp = c - sp * a.nv;
+                const float2* col = a.Y + (size_t)sp * a.ldv + a.voff + vp;
+                if (kk < a.nf) Al[u] = col[(size_t)kk * kstride];
+                if (NC - kk < a.nf) Bl[u] = col[(size_t)(NC - kk) * kstride];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < BL; ++u) {
+            const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+            if (idx >= ITEMS) continue;
+            const int j = idx % P, kk = idx / P;
+            float2 A = Al[u], B = Bl[u];
+            if (a.conj_in) { A.y = -A.y; B.y = -B.y; }
+            if (kk == 0) { A.y = 0.f; B.y = 0.f; }
+            // E = A + conj B, O = (A - conj B) W_nt^-kk; the mirror NC - kk has E' = conj E and
+            // O' = (conj A - B) W_nt^-(NC-kk) = (A - conj B)^* W_nt^kk.  Z goes in natural order.
+            const float2 w = a.tw[kk < NC ? kk : 0];
+            const float2 E = make_float2(A.x + B.x, A.y - B.y);
+            const float2 D = make_float2(A.x - B.x, A.y + B.y);
+            const float2 O = cmul(D, cconj(w));
+            z[F::zi(kk, j)] = make_float2(E.x - O.y, E.y + O.x);
+            if (kk > 0 && 2 * kk < NC) {
+                const float2 Om = cmul(make_float2(D.x, -D.y), w);
+                z[F::zi(NC - kk, j)] = make_float2(E.x - Om.y, -E.y + Om.x);
+            }
+          }
+        }
+    }
+    __syncthreads();
+    four_step<N1, N2, true, true>(z, twc);
+
+    // Row rho holds complex sample n = (rho % N2) * N1 + rho / N2, i.e. real samples 2n (real
+    // part) and 2n + 1 (imaginary part).
+    const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
+    const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
+    const bool want_ss = a.colsum != nullptr;
+    if (a.vec4) {
+        // four adjacent columns per thread (16-byte loads and stores), BQ rows of samples in flight
+        constexpr int Q = P / 4, TSQ = FFT_THREADS / Q, PERQ = NC / TSQ, BQ = PERQ < 4 ? PERQ : 4;
+        const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
+        float ss[4] = {0.f, 0.f, 0.f, 0.f};
+        if (cq < a.C) {
+            int cut[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+#pragma unroll 1
+            for (int b0 = 0; b0 < PERQ; b0 += BQ) {
+                float4 bv[BQ][2], pv[BQ][2];
+#pragma unroll
+                for (int u = 0; u < BQ; ++u) {
+                    const int rho = t0 + (b0 + u) * TSQ;
+                    const int n = (rho % N2) * N1 + rho / N2;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const size_t o = (size_t)(2 * n + h) * a.C + cq;
+                        bv[u][h] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        pv[u][h] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < BQ; ++u) {
+                    const int rho = t0 + (b0 + u) * TSQ;
+                    const int n = (rho % N2) * N1 + rho / N2;
+                    const float4 z01 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q));
+                    const float4 z23 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q + 2));
+                    const float re[4] = {z01.x, z01.z, z23.x, z23.z}, im[4] = {z01.y, z01.w, z23.y, z23.w};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = 2 * n + h;
+                        const int tau = t < NC ? t : NT - t;
+                        const float bb[4] = {bv[u][h].x, bv[u][h].y, bv[u][h].z, bv[u][h].w};
+                        const float pp[4] = {pv[u][h].x, pv[u][h].y, pv[u][h].z, pv[u][h].w};
+                        float v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float val = tau >= cut[i] ? 0.f : (h ? im[i] : re[i]) * a.scale;
+                            v[i] = am * val + ab * bb[i] + ap * pp[i];
+                            if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
+                        }
+                        *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                }
+            }
+        }
+        if (a.colsum) {
+            __syncthreads();                             // every thread is done reading the tile
+#pragma unroll
+            for (int i = 0; i < 4; ++i) red[4 * threadIdx.x + i] = (double)ss[i];
+            __syncthreads();
+            if (threadIdx.x < P && c0 + (int)threadIdx.x < a.C) {
+                const int qq = threadIdx.x / 4, ii = threadIdx.x % 4;
+                double tot = 0.0;
+                for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
+                a.colsum[c0 + threadIdx.x] = tot;
+            }
+        }
+        return;
+    }
+    constexpr int TS = FFT_THREADS / P, PER = NC / TS, BS = PER < 8 ? PER : 8;
+    const int cl = threadIdx.x % P, t0 = threadIdx.x / P, c = c0 + cl;
+    float ss = 0.f;
+    if (c < a.C) {
+        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+#pragma unroll 1
+        for (int b0 = 0; b0 < PER; b0 += BS) {
+            float bv[BS][2], pv[BS][2];
+#pragma unroll
+            for (int u = 0; u < BS; ++u) {
+                const int rho = t0 + (b0 + u) * TS;
+                const int n = (rho % N2) * N1 + rho / N2;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t = 2 * n + h;
+                    const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
+                    bv[u][h] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
+                    pv[u][h] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BS; ++u) {
+                const int rho = t0 + (b0 + u) * TS;
+                const int n = (rho % N2) * N1 + rho / N2;
+                const float2 zz = z[F::zi(rho, cl)];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t = 2 * n + h;
+                    const int tau = t < NC ? t : NT - t;
+                    float val = (h ? zz.y : zz.x) * a.scale;
+                    if (tau >= cut) val = 0.f;
+                    const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
+                    const float r = am * val + ab * bv[u][h] + ap * pv[u][h];
+                    a.out[(size_t)to * a.C + c] = r;
+                    if (want_ss) ss = fmaf(r, r, ss);
+                }
+            }
+        }
+    }
+    if (a.colsum) {
+        __syncthreads();                                 // every thread is done reading the tile
+        red[threadIdx.x] = (double)ss;
+        __syncthreads();
+        if (threadIdx.x < P && c < a.C) {
+            double tot = 0.0;
+            for (int i = threadIdx.x; i < FFT_THREADS; i += P) tot += red[i];
+            a.colsum[c] = tot;
+        }
+    }
+}
+
+template <int N1, int N2>
+void rfft_half_launch(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+    using H = HalfStep<N1, N2>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(rfft_half_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H::smem);
+        attr = true;
+    }
+    LaunchScope ls(p, s, MDC_KC_RFFT);
+    rfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+}
+
+template <int N1, int N2>
+void irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
+    using H = HalfStep<N1, N2>;
+    IrfftArgs a = a0;
+    a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
+             (!a.base || (uintptr_t)a.base % 16 == 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(irfft_half_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H::smem);
+        attr = true;
+    }
+    LaunchScope ls(p, s, MDC_KC_IRFFT);
+    irfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+}
+
 template <int N1, int N2>
 void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     using F = FourStep<N1, N2>;
@@ -698,6 +997,7 @@ void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
         case 256: rfft4_launch<16, 16>(p, a, s); return;
         case 512: rfft4_launch<32, 16>(p, a, s); return;
         case 1024: rfft4_launch<32, 32>(p, a, s); return;
+        case 2048: rfft_half_launch<32, 32>(p, a, s); return;
         default: break;
     }
     const int logCT = tile_log_columns(a.nt);
@@ -719,6 +1019,7 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
         case 256: irfft4_launch<16, 16>(p, a, s); return;
         case 512: irfft4_launch<32, 16>(p, a, s); return;
         case 1024: irfft4_launch<32, 32>(p, a, s); return;
+        case 2048: irfft_half_launch<32, 32>(p, a, s); return;
         default: break;
     }
     const int logCT = tile_log_columns(a.nt);

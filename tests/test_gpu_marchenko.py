@@ -46,6 +46,8 @@ def oracle_solve(cfg, G, cut, fd, niter, tol=0.0):
     (3, 64, 20, 1, 120.0, 6),       # nv = 1: 2 columns per pass (GEMV)
     (5, 128, 40, 2, 200.0, 10),     # nv = 4: 8 columns per pass (GEMM)
     (21, 512, 150, 2, 800.0, 20),   # redatuming shapes at reduced aperture
+    (3, 2048, 300, 1, 600.0, 6),    # nt = 2048 (half-length real transforms), GEMV
+    (5, 2048, 301, 2, 600.0, 6),    # nt = 2048, GEMM, odd nf
 ])
 def test_marchenko_lsqr_matches_oracle(n_side, nt, nf, nvg, z, niter):
     import paper_2011_11120_gb300 as m
@@ -199,6 +201,24 @@ def test_marchenko_neumann_matches_oracle(niter):
             assert float(out["f_mplus"].abs().max()) == 0.0
         else:
             assert rel(out["f_mplus"].cpu().numpy(), x[1]) <= TOL
+    assert rel(out["g_minus"].cpu().numpy(), gm) <= TOL
+    assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL
+
+
+def test_marchenko_neumann_nt2048_matches_oracle():
+    """Neumann series at nt = 2048: the half-length transforms with every fused epilogue term."""
+    import paper_2011_11120_gb300 as m
+    cfg, G, cut, fd = problem(3, 2048, 300, 2, 600.0)
+    op_o = omar.Marchenko(G, cfg.dt, cfg.dr, cut, cfg.nt)
+    d = op_o.data(fd)
+    apply_N = lambda x: solvers.lincomb(1.0, x, -1.0, op_o.matvec(x))  # noqa: E731  N = I - M
+    x = solvers.neumann(apply_N, d, 4)
+    gm, _, gp = op_o.greens(x[0], x[1], fd)
+    op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), cfg.nt, cfg.dt, cfg.dr)
+    out = op.neumann(torch.from_numpy(cut).cuda(), torch.from_numpy(fd).cuda(), 4)
+    op.close()
+    assert rel(out["f_minus"].cpu().numpy(), x[0]) <= TOL
+    assert rel(out["f_mplus"].cpu().numpy(), x[1]) <= TOL
     assert rel(out["g_minus"].cpu().numpy(), gm) <= TOL
     assert rel(out["g_plus"].cpu().numpy(), gp) <= TOL
 
