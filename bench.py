@@ -365,7 +365,8 @@ def run_mdd(args, dev):
 
 def run_precision(args, dev):
     """Precision sweep on the 8281-trace kernel (nfmax=160): forward and adjoint MDC per storage
-    format at nv = 1 (GEMV, streaming the kernel) and nv = 128 (tensor cores for the 16-bit copies),
+    format at nv = 1 (GEMV, streaming the kernel), 16 and 128 (tensor cores for the FP16, BF16, split
+    FP16 and E4M3 copies),
     with the relative L2 error of 8 sampled output rows (forward) and columns (adjoint) against the
     FP64 oracle at nv = 16."""
     import torch
@@ -404,7 +405,7 @@ def run_precision(args, dev):
         op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=fmt)
         kb = cfg.nf * cfg.nr * cfg.ns * BYTES_PER_COMPLEX[fmt]     # algorithmic kernel bytes per pass
         res = {"kernel_gb": kb / 1e9}
-        for nv in (1, 128):
+        for nv in (1, 16, 128):
             x = torch.randn((cfg.nt, cfg.ns, nv), generator=gen, device=dev)
             y = torch.randn((cfg.nt, cfg.nr, nv), generator=gen, device=dev)
             tf = timed(lambda: op.forward(x), "product_fwd", op.h)

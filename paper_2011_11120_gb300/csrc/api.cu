@@ -241,8 +241,8 @@ int mdc::ensure_scratch(mdc_plan* p, int ncols) {
         p->specB = b;
         p->nv_cap = ncols;
     }
-    // tensor-core operand for the FP16/BF16 copies (used from 8 columns on)
-    if (storage_16bit(p->storage) && ncols > p->tc_cap) {
+    // tensor-core operand for the FP16/BF16/E4M3 copies (used from 8 columns on)
+    if (storage_tc(p->storage) && ncols > p->tc_cap) {
         void* b = nullptr;
         float* sg = nullptr;
         cudaError_t e = cudaMalloc(&b, tc_scratch_elems(p, ncols) * 2 * (p->storage == MDC_C32S ? 2 : 1));

@@ -155,9 +155,10 @@ void launch_quantize_rows(mdc_plan* p, const float2* G, const float* w, int64_t 
 inline int storage_bytes(int storage) {
     return (storage == MDC_C64 || storage == MDC_C32S) ? 8 : (storage == MDC_CE4M3 ? 2 : 4);
 }
-// Storage held in 16-bit halves that the tensor-core path can consume.
-inline bool storage_16bit(int storage) {
-    return storage == MDC_C16F || storage == MDC_CBF16 || storage == MDC_C32S;
+// Storage the tensor-core path can consume: 16-bit halves, or E4M3 bytes that the GEMM widens to
+// FP16 in shared memory.
+inline bool storage_tc(int storage) {
+    return storage == MDC_C16F || storage == MDC_CBF16 || storage == MDC_C32S || storage == MDC_CE4M3;
 }
 
 void set_cuda_error(cudaError_t e);

@@ -774,7 +774,7 @@ extern "C" int srv_create(mdc_server** out, mdc_handle R, mdc_handle R_ref, int6
     v->s = (cudaStream_t)stream;
     // one product path for every batch composition: a job's columns see the same arithmetic
     // alone or in a mix
-    R->force_tc = (R->storage == MDC_C16F || R->storage == MDC_CBF16);
+    R->force_tc = (R->storage == MDC_C16F || R->storage == MDC_CBF16 || R->storage == MDC_CE4M3);
     int st = ensure_scratch(R, max_cols);
     if (st == MDC_OK && v->pr != R) st = ensure_scratch(v->pr, max_cols);
     if (st != MDC_OK) {

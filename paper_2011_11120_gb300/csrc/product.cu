@@ -834,7 +834,7 @@ bool product_simt_or_gemv(mdc_plan* p, bool adjoint, const float2* in, int ldi, 
 bool launch_product_variant(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out,
                             int ldo, int voff_o, int ncol, cudaStream_t s, int path, int bn) {
     if (path == PATH_TC)
-        return storage_16bit(p->storage) && p->tcB && ncol <= p->tc_cap &&
+        return storage_tc(p->storage) && p->tcB && ncol <= p->tc_cap &&
                launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, nullptr, bn);
     return product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, nullptr, path);
 }
@@ -854,7 +854,7 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
             }
     }
     if (path == PATH_TC || (path == PATH_AUTO && tc_supported(p, ncol))) {
-        if (storage_16bit(p->storage) && p->tcB && ncol <= p->tc_cap &&
+        if (storage_tc(p->storage) && p->tcB && ncol <= p->tc_cap &&
             launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, bn))
             return;
         path = PATH_AUTO;
@@ -1037,7 +1037,7 @@ int autotune(mdc_plan* p, int ncol_max, cudaStream_t s) {
             std::vector<Cand> cands;
             if (ncol <= gemv_max_columns()) cands.push_back({PATH_GEMV, 0});
             cands.push_back({PATH_SIMT, 0});
-            if (storage_16bit(p->storage) && p->tcB)
+            if (storage_tc(p->storage) && p->tcB)
                 for (int bn = 32; bn <= 256; bn *= 2)
                     if (bn / 2 <= 2 * ncol || bn == 32) cands.push_back({PATH_TC, bn});
             float best = 1e30f;

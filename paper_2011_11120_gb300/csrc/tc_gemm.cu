@@ -32,8 +32,11 @@ namespace mdc {
 namespace {
 
 // warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: epilogue (two warps per TMEM lane
-// quarter, each taking half of the accumulator columns)
+// quarter, each taking half of the accumulator columns); for the E4M3 kernel copy warps
+// 10..13 widen each stage's A tile to FP16
 constexpr int TC_THREADS = 320;
+constexpr int TC_CVT_THREADS = 128;
+constexpr uint32_t TC_STG_BYTES = 128 * 64;     // E4M3 A tile: 128 rows x 64 one-byte reals
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
 // Split format: reduction stages per tensor-core accumulation chunk.  Each chunk's partial sum is
@@ -168,18 +171,26 @@ struct TcArgs {
     int* err;
 };
 
-// Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies.
-template <int BN, bool SPLIT> struct TcStages {
-    static constexpr int bytes = (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
+// Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies,
+// the E4M3 path a byte tile beside the widened A tile.
+template <int BN, bool SPLIT, bool CVT = false> struct TcStages {
+    static constexpr int bytes = (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128) + (CVT ? (int)TC_STG_BYTES : 0);
     static constexpr int fit = (198 * 1024) / bytes;
     static constexpr int v = fit > 8 ? 8 : fit;
 };
 
-template <int BN, bool SPLIT>
+template <int BN, bool SPLIT, bool CVT = false>
 constexpr size_t tc_smem_bytes() {
     // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and eight
     // 32 x 20-float output staging tiles
-    return (size_t)TcStages<BN, SPLIT>::v * TcStages<BN, SPLIT>::bytes + 1024 + 512 + 1024 + 8 * 32 * 20 * 4;
+    return (size_t)TcStages<BN, SPLIT, CVT>::v * TcStages<BN, SPLIT, CVT>::bytes + 1024 + 512 + 1024 +
+           8 * 32 * 20 * 4;
+}
+
+// Two E4M3 values (low byte first) to a packed pair of FP16 (exact: E4M3 is a subset of FP16).
+__device__ __forceinline__ uint32_t e4m3x2_to_h2(uint32_t w) {
+    const __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu), __NV_E4M3);
+    return (uint32_t)r.x | ((uint32_t)r.y << 16);
 }
 
 // AND of a flag over the 256 epilogue threads (named barrier 2): a failed bounded wait in one
@@ -211,29 +222,38 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // multicasts into both CTAs' shared memory, so the L2-to-SM traffic for B halves.  A stage is
 // refilled only after both CTAs' MMAs have consumed it (the empty barrier counts the two
 // multicast commits).  n_tiles_m then counts row-tile pairs.
-template <bool ADJ, int BN, bool SPLIT, bool PAIR>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+//
+// CVT (E4M3 kernel copy): TMA brings each stage's A tile as bytes (128 rows x 64 B, unswizzled)
+// into a staging area; warps 10..13 widen it to FP16 and write it where a 16-bit TMA load would
+// have put it (128-byte swizzle), then arrive on the stage's conv barrier, which the MMA issuer
+// waits on instead of the TMA barrier.  The MMA is the ordinary kind::f16 with FP16 operands.
+template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
+__global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a,
                    uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
+    static_assert(!(CVT && SPLIT), "E4M3 widening has no split form");
     // the early exit is uniform over a cluster (the flag is one device word read by every CTA)
     if (active && *active == 0) return;
-    constexpr int STAGES = TcStages<BN, SPLIT>::v;
+    constexpr int STAGES = TcStages<BN, SPLIT, CVT>::v;
     constexpr uint32_t A_BYTES = TC_BM * 128;
     constexpr uint32_t B_BYTES = BN * 128;
-    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo
-    constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
+    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo, or (CVT) the byte tile of A
+    constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES) + (CVT ? TC_STG_BYTES : 0);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
-    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot, then the epilogue's
-    // double-buffered column scales of the current tile
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot (two words), (CVT)
+    // conv[STAGES] rounded up to an even count, then the epilogue's double-buffered column
+    // scales of the current tile (16-byte aligned)
+    constexpr int SIG_OFF = 2 * STAGES + 6 + (CVT ? (STAGES + 1) & ~1 : 0);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
-    float* sig_s = reinterpret_cast<float*>(bars + 2 * STAGES + 6);
+    float* sig_s = reinterpret_cast<float*>(bars + SIG_OFF);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
+    const uint32_t conv0 = su32(bars + 2 * STAGES + 6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = PAIR ? (int)cluster_rank() : 0;
     const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
@@ -249,6 +269,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(accf0 + 8 * i, 1);
             mbar_init(acce0 + 8 * i, 256);
         }
+        if (CVT)
+            for (int i = 0; i < STAGES; ++i) mbar_init(conv0 + 8 * i, TC_CVT_THREADS / 32);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -281,6 +303,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         break;
                     }
                     const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                    if constexpr (CVT) {
+                        // A as bytes into the staging tile, B as usual
+                        const uint32_t st = sb + B_BYTES;
+                        mbar_expect_tx(full0 + 8 * s, TC_STG_BYTES + B_BYTES);
+                        if (!ADJ) {
+                            tma_load_3d(st, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
+                        } else {
+                            tma_load_3d(st, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
+                            tma_load_3d(st + TC_STG_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+                        }
+                        if (PAIR)
+                            tma_load_3d_mc(sb + rank * (B_BYTES / 2), &tmB, full0 + 8 * s, kb * TC_BK,
+                                           n0 + rank * (BN / 2), k, (uint16_t)0x3);
+                        else
+                            tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
+                        continue;
+                    }
                     mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
 #pragma unroll
                     for (int h = 0; h < (SPLIT ? 2 : 1); ++h) {
@@ -323,7 +362,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int kb1 = kb0 + kc < a.kstages ? kb0 + kc : a.kstages;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
-                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
+                    // CVT: the widened A tile (and, before it, the TMA copies) of this stage
+                    if (!mbar_wait((CVT ? conv0 : full0) + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
                         ok = false;
                         break;
                     }
@@ -350,6 +390,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 umma_commit(accf0 + 8 * buf);
               }
         }
+    } else if (CVT && warp >= TC_THREADS / 32) {
+        // widen each stage's byte tile: item (row R, 8-byte chunk j) -> 16 bytes at row R, chunk
+        // j ^ (R % 8) of the 128-byte-swizzled A tile
+        const int ct = threadIdx.x - TC_THREADS;
+        long g = 0;
+        bool ok = true;
+        for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
+            for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 6)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* stg = gbase + (size_t)s * STAGE_BYTES + A_BYTES + B_BYTES;
+                unsigned char* at = gbase + (size_t)s * STAGE_BYTES;
+#pragma unroll
+                for (int u = 0; u < (int)(TC_STG_BYTES / 8) / TC_CVT_THREADS; ++u) {
+                    const int idx = ct + TC_CVT_THREADS * u;
+                    const int R = idx >> 3, j = idx & 7;
+                    const uint2 w = *reinterpret_cast<const uint2*>(stg + R * 64 + j * 8);
+                    uint4 h;
+                    h.x = e4m3x2_to_h2(w.x);
+                    h.y = e4m3x2_to_h2(w.x >> 16);
+                    h.z = e4m3x2_to_h2(w.y);
+                    h.w = e4m3x2_to_h2(w.y >> 16);
+                    *reinterpret_cast<uint4*>(at + R * 128 + ((j ^ (R & 7)) << 4)) = h;
+                }
+                // the tensor core reads the tile through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(conv0 + 8 * s);
+            }
     } else {
         const int q = warp & 3;                  // TMEM lane quarter of this warp
         const int row = q * 32 + lane;
@@ -660,17 +732,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map_3d(CUtensorMap* m, const void* ptr, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
-                 uint64_t pitch1_bytes, uint64_t pitch2_bytes, uint32_t b0, uint32_t b1) {
+                 uint64_t pitch1_bytes, uint64_t pitch2_bytes, uint32_t b0, uint32_t b1, bool bytes = false) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[3] = {d0, d1, d2};
     cuuint64_t strides[2] = {pitch1_bytes, pitch2_bytes};
     cuuint32_t box[3] = {b0, b1, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                     const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // 16-bit operands land 128-byte swizzled for the MMA; E4M3 bytes land unswizzled for widening
+    const CUtensorMapDataType dt = bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                         : (bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    CUresult r = enc(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     bytes ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -696,12 +770,13 @@ int sm_count() {
 // pairs (an odd last row tile is paired with an empty one whose rows fall outside the output).
 bool g_pair_off = false;   // set when a cluster launch is refused: later products use single CTAs
 
-template <bool ADJ, int BN, bool SPLIT, bool PAIR>
+template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
 bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
                const int* active) {
     static bool attr = false;
-    const size_t smem = tc_smem_bytes<BN, SPLIT>();
-    auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, PAIR>;
+    const size_t smem = tc_smem_bytes<BN, SPLIT, CVT>();
+    constexpr int THREADS = CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS;
+    auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, PAIR, CVT>;
     if (!attr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
@@ -710,14 +785,14 @@ bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 gr
     const int n_tiles = (int)grid.x * rows * (int)grid.z;
     if (!PAIR) {
         const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
-        kern<<<ctas, TC_THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
-                                            n_tiles);
+        kern<<<ctas, THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
+                                         n_tiles);
         return true;
     }
     const int pairs = n_tiles < sm_count() / 2 ? n_tiles : sm_count() / 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(2 * pairs));
-    cfg.blockDim = dim3(TC_THREADS);
+    cfg.blockDim = dim3(THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -763,7 +838,7 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
 }
 
 bool tc_supported(const mdc_plan* p, int ncol) {
-    return storage_16bit(p->storage) && (ncol >= 8 || p->force_tc) && p->tcB != nullptr && ncol <= p->tc_cap &&
+    return storage_tc(p->storage) && (ncol >= 8 || p->force_tc) && p->tcB != nullptr && ncol <= p->tc_cap &&
            encode_fn() != nullptr;
 }
 
@@ -772,6 +847,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
                        int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override) {
     const bool bf16 = p->storage == MDC_CBF16;
     const bool split = p->storage == MDC_C32S;
+    const bool e4m3 = p->storage == MDC_CE4M3;      // bytes widened to FP16 in shared memory
     int bn = bn_override ? bn_override : pick_bn(2 * ncol);
     if (split && bn > 128) bn = 128;   // the split epilogue keeps a BN-wide float32 row in registers
     if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return false;
@@ -816,14 +892,15 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const bool pair = use_pair(bn, mrows);
     const int bbox = pair ? bn / 2 : bn;      // paired CTAs each load half of the B tile
     bool ok = true;
+    const uint64_t ab = e4m3 ? 1 : 2;         // bytes per real of the kernel copy
     for (int h = 0; h < (split ? 2 : 1) && ok; ++h) {
         const void* ga = G + h * glo;
         const void* gb = Bp + h * blo;
         if (!adjoint)
-            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 128) &&
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, 64, 128, e4m3) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bbox);
         else
-            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * 2, kp * 2 * p->nr, 64, 64) &&
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, 64, 64, e4m3) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
                              (uint64_t)kpitch * 2 * rows_pad, 64, bbox);
     }
@@ -847,9 +924,13 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((adjoint ? 1u : 0u) << 15) |
                            ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     dim3 grid((unsigned)(rows_pad / bn), (unsigned)mrows, (unsigned)p->nf);
-#define MDC_TC_LAUNCH(ADJV, BV, SPV)                                                       \
-    launched = pair ? launch_tc<ADJV, BV, SPV, true>(maps, a, idesc, grid, s, active)     \
-                    : launch_tc<ADJV, BV, SPV, false>(maps, a, idesc, grid, s, active);
+#define MDC_TC_LAUNCH(ADJV, BV, SPV)                                                             \
+    if (e4m3)                                                                                    \
+        launched = pair ? launch_tc<ADJV, BV, false, true, true>(maps, a, idesc, grid, s, active)   \
+                        : launch_tc<ADJV, BV, false, false, true>(maps, a, idesc, grid, s, active); \
+    else                                                                                         \
+        launched = pair ? launch_tc<ADJV, BV, SPV, true>(maps, a, idesc, grid, s, active)           \
+                        : launch_tc<ADJV, BV, SPV, false>(maps, a, idesc, grid, s, active);
 #define MDC_TC_CASE(BNV)                                                                   \
     case BNV:                                                                              \
         if (split) {                                                                       \

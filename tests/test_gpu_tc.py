@@ -1,4 +1,4 @@
-"""GPU parity of the tcgen05 tensor-core products (FP16/BF16 kernel copies, >= 8 columns).
+"""GPU parity of the tcgen05 tensor-core products (FP16/BF16/E4M3 kernel copies, >= 8 columns).
 
 The tensor-core path also rounds the spectra (B operand) to the 16-bit type, after a
 power-of-two column scaling, so its error against the FP64 oracle on the dequantised
@@ -66,6 +66,26 @@ def test_tc_matches_oracle(storage, nt, nr, ns, nf, nv):
     assert abs(lhs - rhs) <= 8 * u * np.linalg.norm(yg) * np.linalg.norm(y)
 
 
+U16 = 2.0 ** -11     # FP16 unit roundoff
+
+
+@pytest.mark.parametrize("nt,nr,ns,nf,nv", CASES)
+def test_tc_e4m3_widened_matches_oracle(nt, nr, ns, nf, nv):
+    """E4M3 kernel copy on tensor cores: TMA brings the kernel as bytes and the GEMM widens them to
+    FP16 in shared memory (exactly: E4M3 is a subset of FP16), so against the FP64 oracle on the
+    dequantised E4M3 kernel the only error is the FP16 rounding of the spectra (tolerance 4 u16),
+    like the FP16 copy's."""
+    G, x, y, yg, xg = run("ce4m3", nt, nr, ns, nf, nv)
+    Gq = dequantised(G, "ce4m3")
+    ef = rel(yg, omdc.forward(Gq, x, 0.004, 400.0))
+    ea = rel(xg, omdc.adjoint(Gq, y, 0.004, 400.0))
+    print(f"tc ce4m3 nr={nr} ns={ns} nv={nv}: vs dequantised kernel fwd {ef:.2e} adj {ea:.2e}")
+    assert ef <= 4 * U16 and ea <= 4 * U16
+    lhs = np.vdot(yg.astype(np.float64), y)
+    rhs = np.vdot(x.astype(np.float64), xg)
+    assert abs(lhs - rhs) <= 8 * U16 * np.linalg.norm(yg) * np.linalg.norm(y)
+
+
 _PAIR_SCRIPT = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, {root!r})
@@ -84,7 +104,7 @@ np.save({out!r}, np.concatenate([yg.ravel(), xg.ravel()]))
 """
 
 
-@pytest.mark.parametrize("storage", ["c16f", "c32s"])
+@pytest.mark.parametrize("storage", ["c16f", "c32s", "ce4m3"])
 def test_paired_and_single_cta_products_agree(tmp_path, storage):
     """The two-CTA clusters sharing B by multicast (default for wide column tiles) and the
     single-CTA kernel (MDC_TC_PAIR=0) give bit-identical products: pairing only changes which SM
