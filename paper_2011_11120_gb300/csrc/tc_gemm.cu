@@ -171,20 +171,29 @@ struct TcArgs {
     int* err;
 };
 
-// Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies,
-// the E4M3 path a byte tile beside the widened A tile.
-template <int BN, bool SPLIT, bool CVT = false> struct TcStages {
-    static constexpr int bytes = (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128) + (CVT ? (int)TC_STG_BYTES : 0);
-    static constexpr int fit = (198 * 1024) / bytes;
-    static constexpr int v = fit > 8 ? 8 : fit;
+// Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies.
+// The E4M3 path (CVT) streams stages of [B slices | A byte tile] (at most 16) and widens A into a
+// separate ring of WBUF FP16 tiles.  Its byte tiles have 128-byte rows, as many bytes per TMA row
+// as the 16-bit tiles (adjoint: one box covers both 64-element halves of the 128 output rows), and
+// for narrow B tiles a stage spans KSUB = 2 reduction slices (the widened tile is two slices, each
+// laid out as a 16-bit TMA load of one slice would be), halving the hand-offs per kernel byte.
+template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false> struct TcStages {
+    static constexpr int KSUB = (CVT && BN <= 64) ? 2 : 1;
+    static constexpr int WBUF = CVT ? (KSUB == 2 || BN >= 256 ? 2 : 3) : 0;
+    static constexpr int WA = TC_BM * 128 * KSUB;                      // one widened A tile
+    static constexpr int bytes = CVT ? KSUB * (BN * 128 + (int)TC_STG_BYTES)
+                                     : (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
+    static constexpr int fit = (198 * 1024 - WBUF * WA) / bytes;
+    static constexpr int cap = CVT ? 16 : 8;
+    static constexpr int v = fit > cap ? cap : fit;
 };
 
-template <int BN, bool SPLIT, bool CVT = false>
+template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false>
 constexpr size_t tc_smem_bytes() {
     // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and eight
     // 32 x 20-float output staging tiles
-    return (size_t)TcStages<BN, SPLIT, CVT>::v * TcStages<BN, SPLIT, CVT>::bytes + 1024 + 512 + 1024 +
-           8 * 32 * 20 * 4;
+    using S = TcStages<BN, SPLIT, CVT, ADJ>;
+    return (size_t)S::v * S::bytes + (size_t)S::WBUF * S::WA + 1024 + 512 + 1024 + 8 * 32 * 20 * 4;
 }
 
 // Two E4M3 values (low byte first) to a packed pair of FP16 (exact: E4M3 is a subset of FP16).
@@ -224,9 +233,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // multicast commits).  n_tiles_m then counts row-tile pairs.
 //
 // CVT (E4M3 kernel copy): TMA brings each stage's A tile as bytes (128 rows x 64 B, unswizzled)
-// into a staging area; warps 10..13 widen it to FP16 and write it where a 16-bit TMA load would
-// have put it (128-byte swizzle), then arrive on the stage's conv barrier, which the MMA issuer
-// waits on instead of the TMA barrier.  The MMA is the ordinary kind::f16 with FP16 operands.
+// beside its B tile; warps 10..13 widen it to FP16 into the next free tile w of a small ring,
+// laid out as a 16-bit TMA load would have put it (128-byte swizzle), and arrive on conv[w]; the
+// MMA issuer waits for the stage (B) and conv[w] (A), and its commit frees both.  The MMA is
+// the ordinary kind::f16 with FP16 operands.
 template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
 __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -235,25 +245,33 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     static_assert(!(CVT && SPLIT), "E4M3 widening has no split form");
     // the early exit is uniform over a cluster (the flag is one device word read by every CTA)
     if (active && *active == 0) return;
-    constexpr int STAGES = TcStages<BN, SPLIT, CVT>::v;
+    using SC = TcStages<BN, SPLIT, CVT, ADJ>;
+    constexpr int STAGES = SC::v;
+    constexpr int WBUF = SC::WBUF;
+    constexpr int KSUB = SC::KSUB;
     constexpr uint32_t A_BYTES = TC_BM * 128;
     constexpr uint32_t B_BYTES = BN * 128;
-    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo, or (CVT) the byte tile of A
-    constexpr uint32_t STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES) + (CVT ? TC_STG_BYTES : 0);
+    constexpr uint32_t WA_BYTES = SC::WA;
+    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo; or (CVT) KSUB B slices, then the
+    // byte tile of A (KSUB * 8 KB)
+    constexpr uint32_t STAGE_BYTES = SC::bytes;
+    // KSUB divides the forward kstages; an adjoint tail slice reads rows past nr (zero filled)
+    const int ksteps = (a.kstages + KSUB - 1) / KSUB;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES);
+    const uint32_t wbase = base + STAGES * STAGE_BYTES;          // (CVT) widened A tiles
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES + WBUF * WA_BYTES);
     // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot (two words), (CVT)
-    // conv[STAGES] rounded up to an even count, then the epilogue's double-buffered column
-    // scales of the current tile (16-byte aligned)
-    constexpr int SIG_OFF = 2 * STAGES + 6 + (CVT ? (STAGES + 1) & ~1 : 0);
+    // conv[WBUF], wfree[WBUF], then the epilogue's double-buffered column scales of the current
+    // tile (16-byte aligned)
+    constexpr int SIG_OFF = 2 * STAGES + 6 + 2 * WBUF;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
     float* sig_s = reinterpret_cast<float*>(bars + SIG_OFF);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
-    const uint32_t conv0 = su32(bars + 2 * STAGES + 6);
+    const uint32_t conv0 = su32(bars + 2 * STAGES + 6), wfree0 = conv0 + 8 * WBUF;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rank = PAIR ? (int)cluster_rank() : 0;
     const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
@@ -269,8 +287,10 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             mbar_init(accf0 + 8 * i, 1);
             mbar_init(acce0 + 8 * i, 256);
         }
-        if (CVT)
-            for (int i = 0; i < STAGES; ++i) mbar_init(conv0 + 8 * i, TC_CVT_THREADS / 32);
+        for (int i = 0; i < WBUF; ++i) {
+            mbar_init(conv0 + 8 * i, TC_CVT_THREADS / 32);
+            mbar_init(wfree0 + 8 * i, 1);
+        }
         fence_mbar_init();
     }
     tc_fence_before();
@@ -295,29 +315,32 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             for (int tile = t_first; tile < n_tiles && ok; tile += t_stride) {
                 int k, m0, n0;
                 coords(tile, k, m0, n0);
-                for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+                for (int kb = 0; kb < ksteps; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t round = (uint32_t)(g / STAGES);
                     if (g >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                    const uint32_t sa = base + s * STAGE_BYTES;
                     if constexpr (CVT) {
-                        // A as bytes into the staging tile, B as usual
-                        const uint32_t st = sb + B_BYTES;
-                        mbar_expect_tx(full0 + 8 * s, TC_STG_BYTES + B_BYTES);
-                        if (!ADJ) {
-                            tma_load_3d(st, &tmA, full0 + 8 * s, kb * TC_BK, m0, k);
-                        } else {
-                            tma_load_3d(st, &tmA, full0 + 8 * s, m0, kb * TC_BK, k);
-                            tma_load_3d(st + TC_STG_BYTES / 2, &tmA, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
+                        // B as usual at the stage start, A as bytes after it
+                        // B slices at the stage start, A as bytes after them: forward one box of
+                        // 128 rows x KSUB * 64 bytes, adjoint one box of KSUB * 64 rows x 128 bytes
+                        const uint32_t st = sa + KSUB * B_BYTES;
+                        mbar_expect_tx(full0 + 8 * s, KSUB * (TC_STG_BYTES + B_BYTES));
+                        if (!ADJ) tma_load_3d(st, &tmA, full0 + 8 * s, kb * KSUB * TC_BK, m0, k);
+                        else tma_load_3d(st, &tmA, full0 + 8 * s, m0, kb * KSUB * TC_BK, k);
+#pragma unroll
+                        for (int h = 0; h < KSUB; ++h) {
+                            const uint32_t bt = sa + h * B_BYTES;
+                            const int kx = (kb * KSUB + h) * TC_BK;
+                            if (PAIR)
+                                tma_load_3d_mc(bt + rank * (B_BYTES / 2), &tmB, full0 + 8 * s, kx,
+                                               n0 + rank * (BN / 2), k, (uint16_t)0x3);
+                            else
+                                tma_load_3d(bt, &tmB, full0 + 8 * s, kx, n0, k);
                         }
-                        if (PAIR)
-                            tma_load_3d_mc(sb + rank * (B_BYTES / 2), &tmB, full0 + 8 * s, kb * TC_BK,
-                                           n0 + rank * (BN / 2), k, (uint16_t)0x3);
-                        else
-                            tma_load_3d(sb, &tmB, full0 + 8 * s, kb * TC_BK, n0, k);
                         continue;
                     }
                     mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
@@ -349,9 +372,9 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             long g = 0;
             long i = 0;                 // accumulation chunks issued (one per tile unless SPLIT)
             bool ok = true;
-            const int kc = SPLIT ? TC_KCHUNK : a.kstages;
+            const int kc = SPLIT ? TC_KCHUNK : ksteps;
             for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
-              for (int kb0 = 0; kb0 < a.kstages && ok; kb0 += kc, ++i) {
+              for (int kb0 = 0; kb0 < ksteps && ok; kb0 += kc, ++i) {
                 const int buf = (int)(i & 1);
                 if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) {
                     ok = false;
@@ -359,25 +382,33 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * BN);
-                const int kb1 = kb0 + kc < a.kstages ? kb0 + kc : a.kstages;
+                const int kb1 = kb0 + kc < ksteps ? kb0 + kc : ksteps;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
-                    // CVT: the widened A tile (and, before it, the TMA copies) of this stage
-                    if (!mbar_wait((CVT ? conv0 : full0) + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    const int w = CVT ? (int)(g % WBUF) : 0;
+                    // CVT: the widened A tile of this step
+                    if (CVT && !mbar_wait(conv0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1)) & 1, a.err, 7)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                    const uint32_t sa = CVT ? wbase + w * WA_BYTES : base + s * STAGE_BYTES;
+                    const uint32_t sb = CVT ? base + s * STAGE_BYTES : sa + A_BYTES;
                     const uint32_t sa2 = sb + B_BYTES, sb2 = sa2 + A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        // K-major: +32 bytes per 16 elements inside the swizzled row; MN-major: +16 rows
-                        const uint32_t ao = ADJ ? kk * 2048 : kk * 32;
+                    for (int kq = 0; kq < KSUB * (TC_BK / 16); ++kq) {
+                        // K-major: +32 bytes per 16 elements inside the swizzled row (next 64-element
+                        // slice: next A tile and B slice); MN-major: +16 rows
+                        const int kk = kq % (TC_BK / 16), ks = kq / (TC_BK / 16);
+                        const uint32_t ao = ks * A_BYTES + (ADJ ? kk * 2048 : kk * 32);
                         const uint32_t lbo = ADJ ? A_BYTES / 2 : 16;
                         const uint64_t ad = sdesc(sa + ao, lbo, 1024);
-                        const uint64_t bd = sdesc(sb + kk * 32, 16, 1024);
-                        umma_f16(d, ad, bd, idesc, ((kb - kb0) | kk) != 0 ? 1u : 0u);
+                        const uint64_t bd = sdesc(sb + ks * B_BYTES + kk * 32, 16, 1024);
+                        umma_f16(d, ad, bd, idesc, ((kb - kb0) | kq) != 0 ? 1u : 0u);
                         if (SPLIT) {
                             // hi*lo + lo*hi: the dropped lo*lo term is below 2^-22 relative
                             umma_f16(d, ad, sdesc(sb2 + kk * 32, 16, 1024), idesc, 1u);
@@ -386,6 +417,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     }
                     if (PAIR) umma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);   // both CTAs refill s
                     else umma_commit(empty0 + 8 * s);
+                    if (CVT) umma_commit(wfree0 + 8 * w);                     // the widened tile is free
                 }
                 umma_commit(accf0 + 8 * buf);
               }
@@ -397,30 +429,44 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
         long g = 0;
         bool ok = true;
         for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
-            for (int kb = 0; kb < a.kstages; ++kb, ++g) {
+            for (int kb = 0; kb < ksteps; ++kb, ++g) {
                 const int s = (int)(g % STAGES);
+                const int w = (int)(g % (CVT ? WBUF : 1));
                 if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 6)) {
                     ok = false;
                     break;
                 }
-                const unsigned char* stg = gbase + (size_t)s * STAGE_BYTES + A_BYTES + B_BYTES;
-                unsigned char* at = gbase + (size_t)s * STAGE_BYTES;
+                // the MMAs that read this widened tile last time round are complete
+                if (g >= WBUF && !mbar_wait(wfree0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1) - 1) & 1, a.err, 8)) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* stg = gbase + (size_t)s * STAGE_BYTES + KSUB * B_BYTES;
+                unsigned char* at = gbase + (size_t)STAGES * STAGE_BYTES + (size_t)w * WA_BYTES;
+                // byte tile rows of RB bytes (64 forward with KSUB = 1, else 128).  Forward: chunk j of
+                // row R goes to slice j / 8, row R; adjoint: row R is reduction row R % 64 of slice
+                // R / 64, and chunk j goes to output-row half j / 8 (8 KB apart); in both the
+                // 16-byte chunk lands swizzled at (j % 8) ^ (R % 8)
+                constexpr int RB = (!ADJ && KSUB == 1) ? 64 : 128;
+                constexpr int ITEMS = (int)(KSUB * TC_STG_BYTES) / 8;
 #pragma unroll
-                for (int u = 0; u < (int)(TC_STG_BYTES / 8) / TC_CVT_THREADS; ++u) {
+                for (int u = 0; u < ITEMS / TC_CVT_THREADS; ++u) {
                     const int idx = ct + TC_CVT_THREADS * u;
-                    const int R = idx >> 3, j = idx & 7;
-                    const uint2 w = *reinterpret_cast<const uint2*>(stg + R * 64 + j * 8);
+                    const int R = idx / (RB / 8), j = idx % (RB / 8);
+                    const int off = ADJ ? (R >> 6) * (int)A_BYTES + (j >> 3) * (int)(A_BYTES / 2) + (R & 63) * 128
+                                        : (j >> 3) * (int)A_BYTES + R * 128;
+                    const uint2 w = *reinterpret_cast<const uint2*>(stg + R * RB + j * 8);
                     uint4 h;
                     h.x = e4m3x2_to_h2(w.x);
                     h.y = e4m3x2_to_h2(w.x >> 16);
                     h.z = e4m3x2_to_h2(w.y);
                     h.w = e4m3x2_to_h2(w.y >> 16);
-                    *reinterpret_cast<uint4*>(at + R * 128 + ((j ^ (R & 7)) << 4)) = h;
+                    *reinterpret_cast<uint4*>(at + off + (((j & 7) ^ (R & 7)) << 4)) = h;
                 }
                 // the tensor core reads the tile through the async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(conv0 + 8 * s);
+                if (lane == 0) mbar_arrive(conv0 + 8 * w);
             }
     } else {
         const int q = warp & 3;                  // TMEM lane quarter of this warp
@@ -774,7 +820,7 @@ template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
 bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
                const int* active) {
     static bool attr = false;
-    const size_t smem = tc_smem_bytes<BN, SPLIT, CVT>();
+    const size_t smem = tc_smem_bytes<BN, SPLIT, CVT, ADJ>();
     constexpr int THREADS = CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS;
     auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, PAIR, CVT>;
     if (!attr) {
@@ -893,14 +939,18 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const int bbox = pair ? bn / 2 : bn;      // paired CTAs each load half of the B tile
     bool ok = true;
     const uint64_t ab = e4m3 ? 1 : 2;         // bytes per real of the kernel copy
+    // E4M3 byte tiles: forward 128 rows x 128 bytes for B tiles of <= 64 columns (two reduction
+    // slices per stage), else 128 x 64; adjoint 128 (<= 64 columns) or 64 reduction rows x 128
+    // bytes (both output-row halves)
+    const uint32_t fa0 = e4m3 && bn <= 64 ? 128 : 64, aa0 = e4m3 ? 128 : 64, aa1 = e4m3 && bn <= 64 ? 128 : 64;
     for (int h = 0; h < (split ? 2 : 1) && ok; ++h) {
         const void* ga = G + h * glo;
         const void* gb = Bp + h * blo;
         if (!adjoint)
-            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, 64, 128, e4m3) &&
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, fa0, 128, e4m3) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bbox);
         else
-            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, 64, 64, e4m3) &&
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, aa0, aa1, e4m3) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, p->nr, rows_pad, p->nf, (uint64_t)kpitch * 2,
                              (uint64_t)kpitch * 2 * rows_pad, 64, bbox);
     }
