@@ -427,7 +427,7 @@ def run_precision(args, dev):
     return out
 
 
-PAPER_FULL = synth.Config(80, "paper-full-9801x9801-nt2048-nf300", 99, 2048, 0.004, 300, 20, 1, 600.0)
+PAPER_FULL = synth.config(6)
 
 
 def run_paper_full(args, dev):

@@ -141,6 +141,9 @@ CONFIGS = {
     # kernel; virtual points, nv and iterations are drawn per job by the serving workload
     5: Config(3, "serving-8281x8281-nt1024-nf160", 91, 1024, 0.004, 160, 20, 1, 800.0,
               normalise=True, niter=20),
+    # the paper's Full geometry (Table 1): 9801 co-located sources and receivers, 300 frequencies;
+    # the 1201-sample traces padded to nt = 2048
+    6: Config(80, "paper-full-9801x9801-nt2048-nf300", 99, 2048, 0.004, 300, 20, 1, 600.0),
 }
 
 

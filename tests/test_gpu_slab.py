@@ -88,7 +88,7 @@ def test_paper_full_size_sampled_rows():
     import paper_2011_11120_gb300 as m
     from synth import gpu as sgpu
     torch.cuda.empty_cache()
-    cfg = synth.Config(80, "paper-full-9801x9801-nt2048-nf300", 99, 2048, 0.004, 300, 20, 1, 600.0)
+    cfg = synth.config(6)
     ldg = -(-cfg.ns // 64) * 64
     need = cfg.nf * cfg.nr * ldg * 8 + 20 * cfg.nr * cfg.ns * 8 + (4 << 30)
     free, _ = torch.cuda.mem_get_info()
