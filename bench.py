@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -83,7 +84,13 @@ class ClockSampler:
     def __init__(self, gpu_index, tag=""):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}{tag}.csv")
+        # the raw samples are kept in MDC_CLOCK_LOG_DIR when it is set, else in a temporary file
+        log_dir = os.environ.get("MDC_CLOCK_LOG_DIR")
+        if log_dir:
+            self.path = os.path.join(log_dir, f"clocks_rank{gpu_index}{tag}.csv")
+        else:
+            fd, self.path = tempfile.mkstemp(prefix=f"clocks_rank{gpu_index}{tag}_", suffix=".csv")
+            os.close(fd)
 
     def start(self):
         try:
