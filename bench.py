@@ -798,6 +798,9 @@ def run_ours(args):
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
         result["cpu_baseline"]["paper_style"] = paper_style_cpu(cfg, nv)
     print(json.dumps(result), flush=True)
+    if args.metrics_jsonl:
+        with open(args.metrics_jsonl, "a") as fh:
+            fh.write(json.dumps(result) + "\n")
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -819,6 +822,7 @@ def main():
     ap.add_argument("--no-mdd", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-paper-full", action="store_true")
+    ap.add_argument("--metrics-jsonl", default="", help="also append the result line to this file")
     ap.add_argument("--mdd-iters", type=int, default=10)
     ap.add_argument("--serving-config", type=int, default=5)
     ap.add_argument("--serving-rate", type=float, default=50.0)

@@ -11,7 +11,12 @@ namespace mdc {
 static thread_local int g_last_cuda_error = 0;
 void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
 
+// NVTX range names of the kernel classes (host ranges around each launch; free without a tool)
+static const char* const kClassRange[MDC_KC_COUNT] = {"mdc rfft", "mdc product forward", "mdc product adjoint",
+                                                      "mdc irfft", "mdc solver"};
+
 LaunchScope::LaunchScope(mdc_plan* p_, cudaStream_t s_, int cls_) : p(p_), s(s_), cls(cls_) {
+    nvtxRangePushA(kClassRange[cls]);
     p->launch_count++;
     p->timing.launches[cls]++;
     if (p->timing.on && p->timing.used < p->timing.pool.size()) {
@@ -24,6 +29,7 @@ LaunchScope::LaunchScope(mdc_plan* p_, cudaStream_t s_, int cls_) : p(p_), s(s_)
 }
 LaunchScope::~LaunchScope() {
     if (ev) cudaEventRecord(ev->b, s);
+    nvtxRangePop();
 }
 
 int ensure_scratch(mdc_plan* p, int ncols);

@@ -1,6 +1,7 @@
 // Internal definitions shared by the MDC library's translation units.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>

@@ -210,12 +210,14 @@ struct Solver {
         lsqr_init(x1, x2, zero_x, act0, resid0);
         for (int it = 1; it <= niter; ++it) {
             const int* a = act0 + it;
+            nvtxRangePushA("mdc lsqr iteration");
             iter_fwd_pre(a);
             launch_product(p, false, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, a);
             iter_fwd_post(a);
             iter_adj_pre(a);
             launch_product(p, true, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, a);
             iter_adj_post(it, niter, tol, act0, resid0, itp, x1, x2);
+            nvtxRangePop();
         }
     }
 
