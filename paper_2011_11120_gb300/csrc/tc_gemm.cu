@@ -33,9 +33,9 @@ namespace {
 
 // warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: epilogue (two warps per TMEM lane
 // quarter, each taking half of the accumulator columns); for the E4M3 kernel copy warps
-// 10..13 widen each stage's A tile to FP16
+// 10..17 widen each stage's A tile to FP16
 constexpr int TC_THREADS = 320;
-constexpr int TC_CVT_THREADS = 128;
+constexpr int TC_CVT_THREADS = 256;
 constexpr uint32_t TC_STG_BYTES = 128 * 64;     // E4M3 A tile: 128 rows x 64 one-byte reals
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
@@ -233,7 +233,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // multicast commits).  n_tiles_m then counts row-tile pairs.
 //
 // CVT (E4M3 kernel copy): TMA brings each stage's A tile as bytes (128 rows x 64 B, unswizzled)
-// beside its B tile; warps 10..13 widen it to FP16 into the next free tile w of a small ring,
+// beside its B tile; warps 10..17 widen it to FP16 into the next free tile w of a small ring,
 // laid out as a 16-bit TMA load would have put it (128-byte swizzle), and arrive on conv[w]; the
 // MMA issuer waits for the stage (B) and conv[w] (A), and its commit frees both.  The MMA is
 // the ordinary kind::f16 with FP16 operands.
