@@ -50,6 +50,11 @@ def test_strerror_and_null_handle_without_device(lib):
     assert L.mdc_destroy(None) == -1
     h = ctypes.c_void_p()
     assert L.mdc_create(ctypes.byref(h), None, 10, 5, 5, 64, 0.004, 1.0, 0, None) == -1
+    # argument checks come before any device call
+    assert L.mdc_create_empty(ctypes.byref(h), 40, 5, 5, 64, 0.004, 1.0, 0, None) == -1   # nfmax > nt/2 + 1
+    assert L.mdc_create_empty(ctypes.byref(h), 10, 5, 5, 100, 0.004, 1.0, 0, None) == -1  # nt not a power of 2
+    assert L.mdc_create_empty(ctypes.byref(h), 10, 5, 5, 64, 0.004, 1.0, 9, None) == -1   # unknown storage
+    assert L.mdc_load_slab(None, None, 0, 1, None) == -1
 
 
 def test_kernel_bytes_reproduce_table1(lib):
