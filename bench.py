@@ -56,6 +56,18 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def tc_peak(sustained=False):
+    """Dense bf16 tensor peak (FP16 runs at the same rate) from MEASURED_PEAKS.json: the burst figure
+    for a kernel timed alone, the sustained one for a kernel timed inside a long step."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        key = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in p else "bf16_tflops"
+        return float(p[key]), f"measured ({key})"
+    return (1700.0 if sustained else 1900.0), "fallback"
+
+
 def kernel_source_sha(kernel_file):
     """sha256 of the complex64 GEMV kernels' source text (between their begin/end markers)."""
     src = open(os.path.join(ROOT, "paper_2011_11120_gb300", "csrc", kernel_file)).read()
@@ -296,7 +308,7 @@ def run_redatum(args, dev):
     torch.cuda.synchronize()
     for name, h in (("fp16_kernel", lo.h), ("reference_kernel", ref.h)):
         breakdown[name] = {}
-        for cls in ("rfft", "product_fwd", "product_adj", "irfft", "solver"):
+        for cls in ("rfft", "tc_prep", "product_fwd", "product_adj", "irfft", "solver"):
             t, n = mdc.mdc_timing_read(h, cls)
             breakdown[name][cls] = {"ms": t, "launches": n}
         mdc.mdc_timing(h, False)
@@ -309,6 +321,20 @@ def run_redatum(args, dev):
     ref.close()
     plain_op.close()
     med = statistics.median(times)
+    # the tensor-core GEMM of the FP16 kernel on its own (B-operand preparation excluded), against the
+    # sustained bf16 peak (it runs inside a long solve); every such product has 2 nv columns
+    fb = breakdown["fp16_kernel"]
+    gemm_ms = fb["product_fwd"]["ms"] + fb["product_adj"]["ms"]
+    gemm_n = fb["product_fwd"]["launches"] + fb["product_adj"]["launches"]
+    tc_roof = None
+    if gemm_n and gemm_ms > 0:
+        flops = 8.0 * cfg.nf * cfg.nr * cfg.ns * 2 * cfg.nv
+        achieved = flops / (gemm_ms / gemm_n / 1e3) / 1e12
+        pk, kind = tc_peak(sustained=True)
+        tc_roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (FP16, 512 columns, forward and adjoint)",
+                   "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                   "ms_per_launch": gemm_ms / gemm_n, "peak_kind": kind,
+                   "operand_prep_ms_per_launch": fb["tc_prep"]["ms"] / max(fb["tc_prep"]["launches"], 1)}
     return {"workload": f"Marchenko LSQR, nr=ns={cfg.nr} (41x41, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
                         f"nv={cfg.nv} (16x16 focusing points, z=800 m), ||R||=0.5, {niter} LSQR iterations "
                         f"on a {args.redatum_storage} kernel + {nref} float32 refinement step of {nin} iterations "
@@ -318,6 +344,7 @@ def run_redatum(args, dev):
             "iterations": out["iters"], "final_residual": out["final_residual"],
             "rel_l2_vs_fp32_solve": err,
             "device_ms_per_kernel_class": breakdown,
+            "tc_roofline": tc_roof,
             "clocks": clocks,
             "fp32_one_job": {"solves_per_s": 1.0 / t_plain, "ms_per_solve": 1e3 * t_plain,
                              "iterations": plain["iters"], "storage": "c64"}}
@@ -398,6 +425,7 @@ def run_precision(args, dev):
                        f"{cfg.n_events} hyperbolic events; rel L2 on 8 sampled rows/columns at nv=16 vs the FP64 oracle"}
 
     def timed(fn, cls, h):
+        """(whole product ms, tensor-core operand preparation ms) per call"""
         fn()
         torch.cuda.synchronize()
         mdc.mdc_timing(h, True)
@@ -405,8 +433,9 @@ def run_precision(args, dev):
             fn()
         torch.cuda.synchronize()
         ms, n = mdc.mdc_timing_read(h, cls)
+        pms, _ = mdc.mdc_timing_read(h, "tc_prep")
         mdc.mdc_timing(h, False)
-        return ms / max(n, 1)
+        return (ms + pms) / max(n, 1), pms / max(n, 1)
 
     for fmt in ("c64", "c32s", "c16f", "cbf16", "ce4m3"):
         op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=fmt)
@@ -415,12 +444,15 @@ def run_precision(args, dev):
         for nv in (1, 16, 128):
             x = torch.randn((cfg.nt, cfg.ns, nv), generator=gen, device=dev)
             y = torch.randn((cfg.nt, cfg.nr, nv), generator=gen, device=dev)
-            tf = timed(lambda: op.forward(x), "product_fwd", op.h)
-            ta = timed(lambda: op.adjoint(y), "product_adj", op.h)
+            tf, pf = timed(lambda: op.forward(x), "product_fwd", op.h)
+            ta, pa = timed(lambda: op.adjoint(y), "product_adj", op.h)
             flops = 8.0 * cfg.nf * cfg.nr * cfg.ns * nv
             res[f"nv{nv}"] = {"product_fwd_ms": tf, "product_adj_ms": ta,
                               "kernel_gbs": kb / (0.5 * (tf + ta)) / 1e6,
                               "tflops": flops / (0.5 * (tf + ta)) / 1e9}
+            if pf + pa > 0:          # tensor-core products: the GEMM alone, without its operand preparation
+                res[f"nv{nv}"].update({"tc_prep_fwd_ms": pf, "tc_prep_adj_ms": pa,
+                                       "tflops_gemm": flops / (0.5 * (tf + ta - pf - pa)) / 1e9})
             del x, y
         yg = op.forward(torch.from_numpy(x16).to(dev)).cpu().numpy()[:, rows]
         xg = op.adjoint(torch.from_numpy(y16).to(dev)).cpu().numpy()[:, cols]
@@ -513,7 +545,7 @@ def run_paper_full(args, dev):
             op.marchenko(cut, fd, niter)
             torch.cuda.synchronize()
             split = {}
-            for cls in ("rfft", "product_fwd", "product_adj", "irfft", "solver"):
+            for cls in ("rfft", "tc_prep", "product_fwd", "product_adj", "irfft", "solver"):
                 t, n = mdc.mdc_timing_read(op.h, cls)
                 split[cls] = {"ms": t, "launches": n}
             mdc.mdc_timing(op.h, False)
@@ -729,7 +761,7 @@ def run_ours(args):
     launches = mdc.mdc_launch_count(op.h) - n0
     ms = e0.elapsed_time(e1)
     kern = {}
-    for name in ("rfft", "product_fwd", "product_adj", "irfft"):
+    for name in ("rfft", "tc_prep", "product_fwd", "product_adj", "irfft"):
         t, n = mdc.mdc_timing_read(op.h, name)
         kern[name] = {"ms_total": t, "launches": n, "ms_avg": t / n if n else None}
     mdc.mdc_timing(op.h, False)

@@ -64,7 +64,9 @@ typedef enum {
     MDC_KC_PRODUCT_ADJ = 2, /* K-hat^H of Eq. 3: per-frequency G(w)^H Y(w) */
     MDC_KC_IRFFT = 3,       /* I_wmax^H and F^H of Eq. 3 (plus fused epilogues) */
     MDC_KC_SOLVER = 4,      /* LSQR scalar recurrences and vector updates */
-    MDC_KC_COUNT = 5
+    MDC_KC_TC_PREP = 5,     /* tensor-core products: spectra to the 16-bit B operand and column scales
+                               (the products' own time is in MDC_KC_PRODUCT_FWD / _ADJ) */
+    MDC_KC_COUNT = 6
 } mdc_kernel_class;
 
 /*

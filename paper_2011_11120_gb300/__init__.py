@@ -21,9 +21,9 @@ MDC_OK = 0
 MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3, MDC_C32S = 0, 1, 2, 3, 4
 STORAGE = {"c64": MDC_C64, "c16f": MDC_C16F, "cbf16": MDC_CBF16, "ce4m3": MDC_CE4M3, "c32s": MDC_C32S}
 MDC_CONJ_KERNEL = 0x1
-KC_RFFT, KC_PRODUCT_FWD, KC_PRODUCT_ADJ, KC_IRFFT, KC_SOLVER = range(5)
+KC_RFFT, KC_PRODUCT_FWD, KC_PRODUCT_ADJ, KC_IRFFT, KC_SOLVER, KC_TC_PREP = range(6)
 KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj": KC_PRODUCT_ADJ,
-                  "irfft": KC_IRFFT, "solver": KC_SOLVER}
+                  "irfft": KC_IRFFT, "solver": KC_SOLVER, "tc_prep": KC_TC_PREP}
 
 # exported symbol -> (restype, argtypes)
 _vp, _i, _d, _u, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_int64

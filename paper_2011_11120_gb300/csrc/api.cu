@@ -13,7 +13,7 @@ void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
 
 // NVTX range names of the kernel classes (host ranges around each launch; free without a tool)
 static const char* const kClassRange[MDC_KC_COUNT] = {"mdc rfft", "mdc product forward", "mdc product adjoint",
-                                                      "mdc irfft", "mdc solver"};
+                                                      "mdc irfft", "mdc solver", "mdc tensor-core operand"};
 
 LaunchScope::LaunchScope(mdc_plan* p_, cudaStream_t s_, int cls_) : p(p_), s(s_), cls(cls_) {
     nvtxRangePushA(kClassRange[cls]);

@@ -53,8 +53,8 @@ struct TimingState {
     std::vector<EventPair> pool;
     std::vector<int> used_class;   // class of each used pair
     size_t used = 0;
-    int64_t launches[MDC_KC_COUNT] = {0, 0, 0, 0, 0};
-    int64_t recorded[MDC_KC_COUNT] = {0, 0, 0, 0, 0};
+    int64_t launches[MDC_KC_COUNT] = {};
+    int64_t recorded[MDC_KC_COUNT] = {};
 };
 
 }  // namespace mdc
@@ -141,8 +141,10 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
 
 // Tensor-core products (tc_gemm.cu).
 bool tc_supported(const mdc_plan* p, int ncol);
+// scoped: time the B-operand preparation (MDC_KC_TC_PREP) and the GEMM (product class) separately
 bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
-                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override = 0);
+                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override = 0,
+                       bool scoped = false);
 // One product with an explicit variant (autotuner); returns false if the variant cannot run.
 bool launch_product_variant(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out,
                             int ldo, int voff_o, int ncol, cudaStream_t s, int path, int bn);

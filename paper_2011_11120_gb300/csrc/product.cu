@@ -842,7 +842,6 @@ bool launch_product_variant(mdc_plan* p, bool adjoint, const float2* in, int ldi
 void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i,
                     float2* out, int ldo, int voff_o, int ncol, cudaStream_t s,
                     const int* active) {
-    LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
     int path = PATH_AUTO, bn = 0;
     if (!p->force_tc) {
         // autotuned variant of the smallest tuned bucket holding ncol columns
@@ -855,10 +854,11 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
     }
     if (path == PATH_TC || (path == PATH_AUTO && tc_supported(p, ncol))) {
         if (storage_tc(p->storage) && p->tcB && ncol <= p->tc_cap &&
-            launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, bn))
+            launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, bn, true))
             return;
         path = PATH_AUTO;
     }
+    LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
     if (!product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path))
         product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, PATH_AUTO);
 }

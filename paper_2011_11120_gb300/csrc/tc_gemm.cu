@@ -24,6 +24,7 @@
 // an error code, the producer drains its own copies in flight, TMEM is freed and
 // the CTA exits.
 #include <cuda.h>
+#include <optional>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
@@ -890,7 +891,7 @@ bool tc_supported(const mdc_plan* p, int ncol) {
 
 // Per-frequency product on tensor cores; returns false if it could not be launched.
 bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
-                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override) {
+                       int voff_o, int ncol, cudaStream_t s, const int* active, int bn_override, bool scoped) {
     const bool bf16 = p->storage == MDC_CBF16;
     const bool split = p->storage == MDC_C32S;
     const bool e4m3 = p->storage == MDC_CE4M3;      // bytes widened to FP16 in shared memory
@@ -904,6 +905,8 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     // B operand (and its lo half for the split format, one plane further)
     const size_t plane = (size_t)p->nf * rows_pad * (adjoint ? (size_t)kpitch : (size_t)kp);
     dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
+    std::optional<LaunchScope> scope;
+    if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
 #define MDC_PREP(KER, T, SP, ...) KER<T, SP><<<pg, 256, 0, s>>>(__VA_ARGS__, active, plane)
     if (!adjoint) {
         if (bf16)
@@ -927,6 +930,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
                      (__half*)p->tcB, p->tcSigma);
     }
 #undef MDC_PREP
+    scope.reset();
     // tensor maps: A over the kernel copy [nf][nr][2*ldg] (16-bit reals), B over the prepared operand
     CUtensorMap maps[4];
     const unsigned char* G = static_cast<const unsigned char*>(p->G);
@@ -974,6 +978,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((adjoint ? 1u : 0u) << 15) |
                            ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     dim3 grid((unsigned)(rows_pad / bn), (unsigned)mrows, (unsigned)p->nf);
+    if (scoped) scope.emplace(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
 #define MDC_TC_LAUNCH(ADJV, BV, SPV)                                                             \
     if (e4m3)                                                                                    \
         launched = pair ? launch_tc<ADJV, BV, false, true, true>(maps, a, idesc, grid, s, active)   \
