@@ -638,12 +638,31 @@ __device__ __forceinline__ void prep_scales(const float2* __restrict__ Xk, int l
                                             float* __restrict__ inv_sigma_k) {
     const int j0 = threadIdx.x & 7;
     float m = 0.f;
-    if (n0 + j0 < ncol)
-        for (int s = threadIdx.x >> 3; s < nrows; s += 32) {
+    if (n0 + j0 < ncol) {
+        // eight rows in flight per thread
+        constexpr int U = 8;
+        float mu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) mu[u] = 0.f;
+        int s = threadIdx.x >> 3;
+        for (; s + 32 * (U - 1) < nrows; s += 32 * U) {
+            float2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = Xk[(size_t)(s + 32 * u) * ldi + n0 + j0];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float w = rw ? rw[s + 32 * u] : 1.f;
+                mu[u] = fmaxf(mu[u], fmaxf(fabsf(v[u].x), fabsf(v[u].y)) * w);
+            }
+        }
+        for (; s < nrows; s += 32) {
             const float2 v = Xk[(size_t)s * ldi + n0 + j0];
             const float w = rw ? rw[s] : 1.f;
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)) * w);
+            mu[0] = fmaxf(mu[0], fmaxf(fabsf(v.x), fabsf(v.y)) * w);
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) m = fmaxf(m, mu[u]);
+    }
     red[threadIdx.x] = m;
     __syncthreads();
     if (threadIdx.x < PREP_COLS) {
@@ -656,23 +675,35 @@ __device__ __forceinline__ void prep_scales(const float2* __restrict__ Xk, int l
     __syncthreads();
 }
 
-// Stage rows [s0, s0 + 256) x 8 columns of a complex block in shared memory (coalesced reads),
-// scaled by sig[column] (and by rw[row] if given); rows or columns outside the block are zero.
-__device__ __forceinline__ void prep_stage(const float2* __restrict__ Xk, int ldi, int nrows, int s0, int n0,
-                                           int ncol, const float* __restrict__ rw, const float* sig,
-                                           float2 (*tile)[PREP_COLS + 1]) {
+// Rows [s0, s0 + 256) x 8 columns of a complex block, staged through shared memory: prep_load
+// reads this thread's eight values (coalesced; rows or columns outside the block read as zero)
+// and their row weights into registers, prep_put scales them by sig[column] * rw[row] into the
+// tile.  Loading block b + 1 while block b is written out keeps reads in flight across the
+// barriers.
+constexpr int PREP_PER = PREP_ROWS * PREP_COLS / 256;
+__device__ __forceinline__ void prep_load(const float2* __restrict__ Xk, int ldi, int nrows, int s0, int n0,
+                                          int ncol, const float* __restrict__ rw, float2 (&v)[PREP_PER],
+                                          float (&w)[PREP_PER]) {
 #pragma unroll
-    for (int u = 0; u < PREP_ROWS * PREP_COLS / 256; ++u) {
+    for (int u = 0; u < PREP_PER; ++u) {
         const int idx = threadIdx.x + 256 * u;
         const int rr = idx >> 3, j = idx & 7, s = s0 + rr;
-        float2 v = make_float2(0.f, 0.f);
+        v[u] = make_float2(0.f, 0.f);
+        w[u] = 1.f;
         if (s < nrows && n0 + j < ncol) {
-            v = Xk[(size_t)s * ldi + n0 + j];
-            const float f = sig[j] * (rw ? rw[s] : 1.f);
-            v.x *= f;
-            v.y *= f;
+            v[u] = Xk[(size_t)s * ldi + n0 + j];
+            if (rw) w[u] = rw[s];
         }
-        tile[rr][j] = v;
+    }
+}
+__device__ __forceinline__ void prep_put(const float2 (&v)[PREP_PER], const float (&w)[PREP_PER], const float* sig,
+                                         float2 (*tile)[PREP_COLS + 1]) {
+#pragma unroll
+    for (int u = 0; u < PREP_PER; ++u) {
+        const int idx = threadIdx.x + 256 * u;
+        const int rr = idx >> 3, j = idx & 7;
+        const float f = sig[j] * w[u];
+        tile[rr][j] = make_float2(v[u].x * f, v[u].y * f);
     }
 }
 
@@ -690,13 +721,17 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
     __shared__ float red[256];
     __shared__ float sig[PREP_COLS];
     __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    float2 pv[PREP_PER];
+    float pw[PREP_PER];
+    prep_load(Xk, ldi, ns, 0, n0, ncol, nullptr, pv, pw);      // first block in flight during the scales
     prep_scales(Xk, ldi, ns, n0, ncol, nullptr, red, sig, inv_sigma + (size_t)k * ncol);
     const size_t kp = 2 * (size_t)ldg;
     P2* Bk = reinterpret_cast<P2*>(BT + (size_t)k * rows_pad * kp);      // one pair per s
     const size_t kp2 = kp / 2, plane2 = plane / 2;
     for (int s0 = 0; s0 < ldg; s0 += PREP_ROWS) {
-        prep_stage(Xk, ldi, ns, s0, n0, ncol, nullptr, sig, tile);
+        prep_put(pv, pw, sig, tile);
         __syncthreads();
+        if (s0 + PREP_ROWS < ldg) prep_load(Xk, ldi, ns, s0 + PREP_ROWS, n0, ncol, nullptr, pv, pw);
         const int s = s0 + threadIdx.x;
         if (s < ldg) {
 #pragma unroll
@@ -735,12 +770,16 @@ __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y,
     __shared__ float red[256];
     __shared__ float sig[PREP_COLS];
     __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    float2 pv[PREP_PER];
+    float pw[PREP_PER];
+    prep_load(Yk, ldi, nr, 0, n0, ncol, gs, pv, pw);            // first block in flight during the scales
     prep_scales(Yk, ldi, nr, n0, ncol, gs, red, sig, inv_sigma + (size_t)k * ncol);
     P2* Bk = reinterpret_cast<P2*>(BT + (size_t)k * rows_pad * kpitch);  // kpitch is a multiple of 8
     const size_t kq = (size_t)kpitch / 2, plane2 = plane / 2;
     for (int r0 = 0; r0 < kpitch; r0 += PREP_ROWS) {
-        prep_stage(Yk, ldi, nr, r0, n0, ncol, gs, sig, tile);
+        prep_put(pv, pw, sig, tile);
         __syncthreads();
+        if (r0 + PREP_ROWS < kpitch) prep_load(Yk, ldi, nr, r0 + PREP_ROWS, n0, ncol, gs, pv, pw);
         // threads 0..127 each take rows r0 + 2t, r0 + 2t + 1 for columns 0..3, threads 128..255 columns 4..7
         const int t = threadIdx.x & 127, jb = (threadIdx.x >> 7) * (PREP_COLS / 2);
         const int r = r0 + 2 * t;
