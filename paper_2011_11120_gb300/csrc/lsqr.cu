@@ -201,7 +201,15 @@ struct Solver {
                                                         tol);
         }
         LaunchScope ls(p, s, MDC_KC_SOLVER);
-        lsqr_xw<<<elementwise_grid(B), 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc, a);
+        const bool vec = (B % 4) == 0 && aligned16(x1) && aligned16(x2) && aligned16(W1()) && aligned16(W2()) &&
+                         aligned16(V1()) && aligned16(V2());
+        if (vec)
+            lsqr_xw4<<<elementwise_grid(B / 4), 256, 0, s>>>(
+                B / 4, reinterpret_cast<float4*>(x1), reinterpret_cast<float4*>(x2), reinterpret_cast<float4*>(W1()),
+                reinterpret_cast<float4*>(W2()), reinterpret_cast<const float4*>(V1()),
+                reinterpret_cast<const float4*>(V2()), sc, a);
+        else
+            lsqr_xw<<<elementwise_grid(B), 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc, a);
     }
 
     // LSQR on u-hat (already holding the right-hand side and its column sums); x accumulates.

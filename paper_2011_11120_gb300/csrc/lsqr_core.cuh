@@ -18,10 +18,24 @@ enum Slot {
 
 constexpr int RED_THREADS = 1024;
 
+// Sum of v[0..n) by one CTA in a fixed order (deterministic): each thread keeps eight partial sums
+// (eight loads in flight), combined pairwise, then a tree over the threads.
 __device__ double block_sum(const double* v, int n) {
     __shared__ double red[RED_THREADS];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += RED_THREADS) acc += v[i];
+    constexpr int U = 8;
+    double a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = 0.0;
+    int i = threadIdx.x;
+    for (; i + (U - 1) * RED_THREADS < n; i += U * RED_THREADS) {
+        double t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[u] = v[i + u * RED_THREADS];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] += t[u];
+    }
+    for (; i < n; i += RED_THREADS) a[0] += v[i];
+    const double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     red[threadIdx.x] = acc;
     __syncthreads();
     for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
@@ -110,7 +124,30 @@ __global__ void __launch_bounds__(RED_THREADS) lsqr_alpha_rotate(double* sc, con
     }
 }
 
-// x += (phi/rho) w ;  w = v-hat / alpha - (theta/rho) w, over both blocks.
+// The x and w updates with one rounding order for the scalar and the vector kernels.
+__device__ __forceinline__ float xw_x(float x, float w, float kx) { return fmaf(kx, w, x); }
+__device__ __forceinline__ float xw_w(float v, float w, float ia, float kw) { return fmaf(kw, w, ia * v); }
+
+// x += (phi/rho) w ;  w = v-hat / alpha - (theta/rho) w, over both blocks; four elements per thread
+// and step (n4 = n / 4 16-byte vectors, every array 16-byte aligned: checked by the caller).
+__global__ void lsqr_xw4(int64_t n4, float4* __restrict__ x1, float4* __restrict__ x2,
+                         float4* __restrict__ w1, float4* __restrict__ w2,
+                         const float4* __restrict__ v1, const float4* __restrict__ v2,
+                         const double* sc, const int* act) {
+    if (*act == 0) return;
+    const float kx = (float)sc[S_KX], kw = (float)sc[S_KW], ia = (float)sc[S_INV_ALPHA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 wa = w1[i], xa = x1[i], va = v1[i], wb = w2[i], xb = x2[i], vb = v2[i];
+        x1[i] = make_float4(xw_x(xa.x, wa.x, kx), xw_x(xa.y, wa.y, kx), xw_x(xa.z, wa.z, kx), xw_x(xa.w, wa.w, kx));
+        w1[i] = make_float4(xw_w(va.x, wa.x, ia, kw), xw_w(va.y, wa.y, ia, kw), xw_w(va.z, wa.z, ia, kw),
+                            xw_w(va.w, wa.w, ia, kw));
+        x2[i] = make_float4(xw_x(xb.x, wb.x, kx), xw_x(xb.y, wb.y, kx), xw_x(xb.z, wb.z, kx), xw_x(xb.w, wb.w, kx));
+        w2[i] = make_float4(xw_w(vb.x, wb.x, ia, kw), xw_w(vb.y, wb.y, ia, kw), xw_w(vb.z, wb.z, ia, kw),
+                            xw_w(vb.w, wb.w, ia, kw));
+    }
+}
+
 __global__ void lsqr_xw(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
                         float* __restrict__ w1, float* __restrict__ w2,
                         const float* __restrict__ v1, const float* __restrict__ v2,
@@ -120,11 +157,11 @@ __global__ void lsqr_xw(int64_t n, float* __restrict__ x1, float* __restrict__ x
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float w = w1[i];
-        x1[i] += kx * w;
-        w1[i] = ia * v1[i] + kw * w;
+        x1[i] = xw_x(x1[i], w, kx);
+        w1[i] = xw_w(v1[i], w, ia, kw);
         w = w2[i];
-        x2[i] += kx * w;
-        w2[i] = ia * v2[i] + kw * w;
+        x2[i] = xw_x(x2[i], w, kx);
+        w2[i] = xw_w(v2[i], w, ia, kw);
     }
 }
 
@@ -152,6 +189,8 @@ __global__ void vec_add(int64_t n, const float* a, const float* b, float* out) {
 __global__ void fill_d(double* p, int n, double v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
+
+inline bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; }
 
 int elementwise_grid(int64_t n) {
     int64_t g = (n + 255) / 256;
