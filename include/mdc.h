@@ -363,8 +363,9 @@ int mdc_timing(mdc_handle h, int enable);
 /*
  * mdc_autotune -- choose, per direction and per column count (buckets 1, 2, 4, ... up to
  * ncol_max), the fastest per-frequency product variant for this handle by timing every variant
- * that can run on the handle's own buffers: the GEMV (up to 4 columns), the SIMT GEMM, and, for
- * 16-bit storage, the tensor-core GEMM with each column-tile width (32, 64, 128, 256).  Later
+ * that can run on the handle's own buffers: the GEMV (up to 4 columns, or in passes over groups of
+ * 4 up to 64 columns), the SIMT GEMM, and, for 16-bit and E4M3 storage, the tensor-core GEMM with
+ * each column-tile width (32, 64, 128, 256).  Later
  * products use the variant of the smallest bucket holding their column count (the serving
  * engine still forces tensor cores so a job's arithmetic does not depend on its batch).  With
  * the environment variable MDC_AUTOTUNE_CACHE naming a file, a stored table for the same device,
@@ -373,7 +374,8 @@ int mdc_timing(mdc_handle h, int enable);
  */
 int mdc_autotune(mdc_handle h, int ncol_max, void* stream);
 /* mdc_autotune_choice -- the variant selected for ncol columns: *path 0 = default rule, 1 = GEMV,
- * 2 = SIMT GEMM, 3 = tensor cores with column tile *bn. */
+ * 2 = SIMT GEMM, 3 = tensor cores with column tile *bn, 4 = GEMV passes over groups of up to 4
+ * columns. */
 int mdc_autotune_choice(mdc_handle h, int adjoint, int ncol, int* path, int* bn);
 
 /* mdc_set_option -- MDC_OPT_GRAPHS (value 1/0): when on, a marchenko_lsqr or

@@ -258,7 +258,7 @@ def mdc_launch_count(h) -> int:
 
 
 MDC_OPT_GRAPHS = 1
-PATHS = {0: "default", 1: "gemv", 2: "simt", 3: "tensor-core"}
+PATHS = {0: "default", 1: "gemv", 2: "simt", 3: "tensor-core", 4: "gemv-groups"}
 
 
 def mdc_autotune(h, ncol_max: int, stream=None) -> None:

@@ -41,7 +41,8 @@ constexpr int G_PITCH_ALIGN = 64;
 struct EventPair { cudaEvent_t a, b; };
 
 // Product variant chosen by the autotuner for column counts up to `ncol`.
-enum ProductPath { PATH_AUTO = 0, PATH_GEMV = 1, PATH_SIMT = 2, PATH_TC = 3 };
+// PATH_GEMV_GROUPS: GEMV passes over groups of up to 4 columns (one kernel read per group)
+enum ProductPath { PATH_AUTO = 0, PATH_GEMV = 1, PATH_SIMT = 2, PATH_TC = 3, PATH_GEMV_GROUPS = 4 };
 struct ProductChoice {
     int ncol;
     int path;

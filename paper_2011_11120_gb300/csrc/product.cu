@@ -785,25 +785,40 @@ bool gemv_fits(const mdc_plan* p, bool adjoint, int ncol, int cpv) {
     return ncol <= gemv_max_columns() && staged && red <= 200 * 1024;
 }
 
-// path: PATH_GEMV or PATH_SIMT (PATH_AUTO: GEMV when it fits, else SIMT)
+// Default rule for column counts above the GEMV width: up to this many columns the GEMV runs in
+// passes over groups of 4 (each pass streams the kernel near the HBM rate, while the FP32 SIMT
+// GEMM's 64-column tiles are mostly empty at these widths); above it, the SIMT GEMM.  Where the
+// crossover lies depends on the shape (at 20 columns of a 3721 x 841 kernel the SIMT GEMM still
+// wins); mdc_autotune measures it.
+constexpr int GEMV_GROUP_MAX = 16;
+
+// path: PATH_GEMV, PATH_GEMV_GROUPS or PATH_SIMT (PATH_AUTO: GEMV when it fits, GEMV groups up to
+// GEMV_GROUP_MAX columns, else SIMT)
 template <int FMT>
 bool product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                  int voff_o, int ncol, cudaStream_t s, const int* active, int path) {
+    const int gw = gemv_max_columns();
     const bool fits = gemv_fits(p, adjoint, ncol, Fmt<FMT>::CPV);
+    const bool group_fits = ncol > gw && gemv_fits(p, adjoint, gw, Fmt<FMT>::CPV);
     if (path == PATH_GEMV && !fits) return false;
-    if (fits && path != PATH_SIMT) {
-#define MDC_GEMV_CASE(n)                                                                       \
-    case n:                                                                                    \
-        if (adjoint) gemv_adj_launch<FMT, n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active); \
-        else gemv_fwd_launch<FMT, n>(p, in, ldi, voff_i, out, ldo, voff_o, s, active);         \
+    if (path == PATH_GEMV_GROUPS && !group_fits) return false;
+    const bool groups = group_fits && (path == PATH_GEMV_GROUPS || (path == PATH_AUTO && ncol <= GEMV_GROUP_MAX));
+    if ((fits && path != PATH_SIMT && path != PATH_GEMV_GROUPS) || groups) {
+        for (int c0 = 0; c0 < ncol; c0 += gw) {
+            const int nc = ncol - c0 < gw ? ncol - c0 : gw;
+#define MDC_GEMV_CASE(n)                                                                                       \
+    case n:                                                                                                    \
+        if (adjoint) gemv_adj_launch<FMT, n>(p, in, ldi, voff_i + c0, out, ldo, voff_o + c0, s, active);      \
+        else gemv_fwd_launch<FMT, n>(p, in, ldi, voff_i + c0, out, ldo, voff_o + c0, s, active);              \
         break;
-        switch (ncol) {
-            MDC_GEMV_CASE(1)
-            MDC_GEMV_CASE(2)
-            MDC_GEMV_CASE(3)
-            MDC_GEMV_CASE(4)
-        }
+            switch (nc) {
+                MDC_GEMV_CASE(1)
+                MDC_GEMV_CASE(2)
+                MDC_GEMV_CASE(3)
+                MDC_GEMV_CASE(4)
+            }
 #undef MDC_GEMV_CASE
+        }
         return true;
     }
     const int M = adjoint ? p->ns : p->nr;
@@ -1036,6 +1051,7 @@ int autotune(mdc_plan* p, int ncol_max, cudaStream_t s) {
             struct Cand { int path, bn; };
             std::vector<Cand> cands;
             if (ncol <= gemv_max_columns()) cands.push_back({PATH_GEMV, 0});
+            else if (ncol <= 64) cands.push_back({PATH_GEMV_GROUPS, 0});
             cands.push_back({PATH_SIMT, 0});
             if (storage_tc(p->storage) && p->tcB)
                 for (int bn = 32; bn <= 256; bn *= 2)

@@ -26,9 +26,11 @@ def test_autotune_choices_and_parity(tmp_path, storage):
         for adj in (False, True):
             for ncol in (1, 3, 5, 8, 17, 40):
                 path, bn = m.mdc_autotune_choice(op.h, adj, ncol)
-                assert path in ("gemv", "simt", "tensor-core")
+                assert path in ("gemv", "gemv-groups", "simt", "tensor-core")
                 if path == "gemv":
                     assert ncol <= 4
+                if path == "gemv-groups":
+                    assert 4 < ncol <= 64
                 if path == "tensor-core":
                     assert storage != "c64" and bn in (32, 64, 128, 256)
         Gq = dequantised(G, storage) if storage == "c16f" else G

@@ -48,6 +48,7 @@ CASES = [
     (1024, 61, 67, 200, 1),
     (4096, 9, 5, 2049, 2),
     (2048, 17, 23, 300, 1),
+    (128, 45, 133, 40, 11),     # GEMV passes over column groups of 4, 4 and 3
     (2048, 33, 40, 1025, 3),    # every bin of nt = 2048, Nyquist included
     (2048, 9, 14, 1, 6),        # DC only
 ]
