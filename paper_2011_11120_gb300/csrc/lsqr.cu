@@ -40,6 +40,7 @@ struct Solver {
     float* blk[7] = {};        // U1 U2 V1 V2 W1 W2 D1
     double* csU = nullptr;
     double* csV = nullptr;
+    double* part = nullptr;    // [PART_CTAS] partial sums of csU or csV
     double* sc = nullptr;      // [S_COUNT] LSQR scalars
     double* xs = nullptr;      // [X_COUNT] data norm, final residual ratio
     double* resid = nullptr;   // [nresid]
@@ -56,7 +57,7 @@ struct Solver {
     }
     ~Solver() {
         for (float* b : blk) release(b);
-        release(csU); release(csV); release(sc); release(xs); release(resid); release(act); release(iters);
+        release(csU); release(csV); release(part); release(sc); release(xs); release(resid); release(act); release(iters);
     }
     template <typename T> cudaError_t get(T** q, size_t bytes) {
         return async_alloc ? cudaMallocAsync((void**)q, bytes, s) : cudaMalloc((void**)q, bytes);
@@ -73,6 +74,7 @@ struct Solver {
         for (int i = 0; i < (keep_data ? 7 : 6) && e == cudaSuccess; ++i) e = get(&blk[i], B * sizeof(float));
         if (e == cudaSuccess) e = get(&csU, 2 * (size_t)C * sizeof(double));
         if (e == cudaSuccess) e = get(&csV, 2 * (size_t)C * sizeof(double));
+        if (e == cudaSuccess) e = get(&part, PART_CTAS * sizeof(double));
         if (e == cudaSuccess) e = get(&sc, S_COUNT * sizeof(double));
         if (e == cudaSuccess) e = get(&xs, X_COUNT * sizeof(double));
         if (e == cudaSuccess) e = get(&resid, nresid * sizeof(double));
@@ -123,7 +125,8 @@ struct Solver {
         cudaMemsetAsync(csU + C, 0, C * sizeof(double), s);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            norm_store<<<1, RED_THREADS, 0, s>>>(csU, 2 * C, xs + X_DNORM);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, 2 * C, part, nullptr);
+            norm_store<<<1, RED_THREADS, 0, s>>>(part, PART_CTAS, xs + X_DNORM);
         }
         if (D1()) {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
@@ -161,12 +164,14 @@ struct Solver {
         cudaMemsetAsync(sc, 0, S_COUNT * sizeof(double), s);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, 2 * C, resid0, act0 + 1);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, 2 * C, part, nullptr);
+            lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, resid0, act0 + 1);
         }
         apply_MH(act0 + 1, zero);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(sc, csV, 2 * C, act0 + 1);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, 2 * C, part, act0 + 1);
+            lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, act0 + 1);
         }
         LaunchScope ls(p, s, MDC_KC_SOLVER);
         if (zero_x) lsqr_xw_init<<<eg, 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc);
@@ -183,7 +188,8 @@ struct Solver {
         irfft(p, 0, 0, U1(), C1(-1.f), cut, V1(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU, 0, a);
         irfft(p, nv, 1, U2(), C1(-1.f), cut, V2(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU + C, 0, a);
         LaunchScope ls(p, s, MDC_KC_SOLVER);
-        lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, 2 * C, a);
+        colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, 2 * C, part, a);
+        lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a);
     }
     //   v-hat <- M^H u - beta v
     void iter_adj_pre(const int* a) {
@@ -197,8 +203,9 @@ struct Solver {
         irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, a);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, csV, 2 * C, a, act0 + it + 1, resid0, itp, it, niter,
-                                                        tol);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, 2 * C, part, a);
+            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act0 + it + 1, resid0, itp, it,
+                                                        niter, tol);
         }
         LaunchScope ls(p, s, MDC_KC_SOLVER);
         const bool vec = (B % 4) == 0 && aligned16(x1) && aligned16(x2) && aligned16(W1()) && aligned16(W2()) &&
@@ -306,7 +313,8 @@ void solve_body(Solver& S, const float* fd, int niter, int nref, int niter_ref, 
     if (want_final) {
         S.residual_pass(fm, fmp);
         LaunchScope ls(S.p, S.s, MDC_KC_SOLVER);
-        norm_ratio<<<1, RED_THREADS, 0, S.s>>>(S.csU, 2 * S.C, S.xs + X_DNORM, S.xs + X_FINAL);
+        colsum_partials<<<PART_CTAS, 256, 0, S.s>>>(S.csU, 2 * S.C, S.part, nullptr);
+        norm_ratio<<<1, RED_THREADS, 0, S.s>>>(S.part, PART_CTAS, S.xs + X_DNORM, S.xs + X_FINAL);
     }
     if (gm || gp) S.greens(fd, fm, fmp, gm, gp);
 }
@@ -744,7 +752,8 @@ void finish_job(mdc_server* v, ServeJob* j) {
     S->residual_pass(j->x[0], j->x[1]);
     {
         LaunchScope ls(v->p, v->s, MDC_KC_SOLVER);
-        norm_ratio<<<1, RED_THREADS, 0, v->s>>>(S->csU, 2 * S->C, S->xs + X_DNORM, S->xs + X_FINAL);
+        colsum_partials<<<PART_CTAS, 256, 0, v->s>>>(S->csU, 2 * S->C, S->part, nullptr);
+        norm_ratio<<<1, RED_THREADS, 0, v->s>>>(S->part, PART_CTAS, S->xs + X_DNORM, S->xs + X_FINAL);
     }
     S->greens(j->fd_d, j->x[0], j->x[1], j->x[2], j->x[3]);
     const size_t bytes = (size_t)S->B * sizeof(float);

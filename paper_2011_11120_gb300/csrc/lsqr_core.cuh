@@ -47,6 +47,32 @@ __device__ double block_sum(const double* v, int n) {
     return r;
 }
 
+// Sums of squares are reduced in two fixed-order steps: colsum_partials writes PART_CTAS partial
+// sums of contiguous chunks of the per-column sums (all SMs reading), then the one-CTA scalar
+// kernel below sums the partials.  Skips its work when *act == 0 (act may be null).
+constexpr int PART_CTAS = 304;
+__global__ void __launch_bounds__(256) colsum_partials(const double* __restrict__ cs, int n,
+                                                       double* __restrict__ part, const int* act) {
+    if (act && *act == 0) return;
+    __shared__ double red[256];
+    const int chunk = (n + PART_CTAS - 1) / PART_CTAS;
+    const int b0 = blockIdx.x * chunk, b1 = b0 + chunk < n ? b0 + chunk : n;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = b0 + threadIdx.x;
+    for (; i + 3 * 256 < b1; i += 4 * 256) {
+        const double t0 = cs[i], t1 = cs[i + 256], t2 = cs[i + 512], t3 = cs[i + 768];
+        a[0] += t0; a[1] += t1; a[2] += t2; a[3] += t3;
+    }
+    for (; i < b1; i += 256) a[0] += cs[i];
+    red[threadIdx.x] = (a[0] + a[1]) + (a[2] + a[3]);
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
 // beta_1 = ||d||, u_1 = d / beta_1 (Paige-Saunders initialisation).
 __global__ void __launch_bounds__(RED_THREADS) lsqr_init_beta(double* sc, const double* cs, int n,
                                                               double* resid, int* act1) {

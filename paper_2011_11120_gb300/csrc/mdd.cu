@@ -64,11 +64,11 @@ struct MddSolver {
     int nv = 0, Cu = 0, Cv = 0;   // columns of the data (nr * nv) and model (ns * nv) spaces
     int64_t Bu = 0, Bv = 0;       // elements of one data / model vector
     float *U = nullptr, *V = nullptr, *W = nullptr;
-    double *csU = nullptr, *csV = nullptr, *sc = nullptr, *resid = nullptr;
+    double *csU = nullptr, *csV = nullptr, *part = nullptr, *sc = nullptr, *resid = nullptr;
     int *act = nullptr, *iters = nullptr;
 
     ~MddSolver() {
-        for (void* q : {(void*)U, (void*)V, (void*)W, (void*)csU, (void*)csV, (void*)sc, (void*)resid, (void*)act,
+        for (void* q : {(void*)U, (void*)V, (void*)W, (void*)csU, (void*)csV, (void*)part, (void*)sc, (void*)resid, (void*)act,
                         (void*)iters})
             if (q) cudaFree(q);
     }
@@ -78,6 +78,7 @@ struct MddSolver {
         if (e == cudaSuccess) e = cudaMalloc(&W, Bv * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&csU, (size_t)Cu * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&csV, (size_t)Cv * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&part, PART_CTAS * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&sc, S_COUNT * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&resid, (size_t)(niter + 1) * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&act, (size_t)(niter + 2) * sizeof(int));
@@ -121,7 +122,8 @@ struct MddSolver {
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
             copy_colsum<<<(Cu + 255) / 256, 256, 0, s>>>(p->nt, Cu, d, U, csU);
-            lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, Cu, resid, act + 1);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, Cu, part, nullptr);
+            lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, resid, act + 1);
         }
         // alpha_1 v_1 = G+^H u_1
         rfft(U, p->nr, CD(1.f, sc + S_INV_BETA), act + 1);
@@ -129,7 +131,8 @@ struct MddSolver {
         irfft(V, p->ns, C1(0.f), csV, act + 1);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(sc, csV, Cv, act + 1);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, Cv, part, act + 1);
+            lsqr_init_alpha<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, act + 1);
             lsqr_xw_one_init<<<eg, 256, 0, s>>>(Bv, x, W, V, sc);
         }
         for (int it = 1; it <= niter; ++it) {
@@ -140,14 +143,17 @@ struct MddSolver {
             irfft(U, p->nr, CD(1.f, sc + S_U_PREV), csU, a);
             {
                 LaunchScope ls(p, s, MDC_KC_SOLVER);
-                lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, csU, Cu, a);
+                colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, Cu, part, a);
+                lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a);
             }
             // v-hat <- G+^H u - beta v
             rfft(U, p->nr, CD(1.f, sc + S_INV_BETA), a);
             product(true, a);
             irfft(V, p->ns, CD(1.f, sc + S_V_PREV), csV, a);
             LaunchScope ls(p, s, MDC_KC_SOLVER);
-            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, csV, Cv, a, act + it + 1, resid, iters, it, niter, tol);
+            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, Cv, part, a);
+            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act + it + 1, resid, iters, it, niter,
+                                                        tol);
             lsqr_xw_one<<<eg, 256, 0, s>>>(Bv, x, W, V, sc, a);
         }
     }
