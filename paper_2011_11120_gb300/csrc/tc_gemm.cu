@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     ok = false;
                     break;
                 }
-                // the MMAs that read this widened tile last time round are complete
+                // the MMAs that read this widened tile on its previous use are complete
                 if (g >= WBUF && !mbar_wait(wfree0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1) - 1) & 1, a.err, 8)) {
                     ok = false;
                     break;

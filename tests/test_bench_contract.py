@@ -1,5 +1,5 @@
 """bench.py keeps its output contract: the reference arm (the FP64 oracle on the host cores) prints one
-JSON line with the keys the benchmark driver reads, and the helpers count algorithmic bytes as stated."""
+JSON line with the keys of the output contract, and the helpers count algorithmic bytes as stated."""
 import json
 import os
 import subprocess
