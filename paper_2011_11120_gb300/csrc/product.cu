@@ -796,15 +796,17 @@ bool gemv_fits(const mdc_plan* p, bool adjoint, int ncol, int cpv) {
     return ncol <= gemv_max_columns() && staged && red <= 200 * 1024;
 }
 
-// Default rule for column counts above the GEMV width: up to this many columns the GEMV runs in
-// passes over groups of 4 (each pass streams the kernel near the HBM rate, while the FP32 SIMT
-// GEMM's 64-column tiles are mostly empty at these widths); above it, the SIMT GEMM.  Where the
-// crossover lies depends on the shape (at 20 columns of a 3721 x 841 kernel the SIMT GEMM still
-// wins); mdc_autotune measures it.
-constexpr int GEMV_GROUP_MAX = 16;
+// Default rule for column counts above the GEMV width: up to GEMV_GROUP_MAX_FWD (forward) or
+// GEMV_GROUP_MAX_ADJ (adjoint) columns the GEMV runs in passes over groups of 4, each streaming the
+// kernel near the HBM rate; above, the FP32 SIMT GEMM (128 x 32 tiles up to 32 columns).  The
+// crossover depends on the shape (measured on 8281^2, 3721 x 841 and 1681^2 complex64 kernels:
+// groups win at 8 columns forward, at 8 and 16 adjoint, except the 3721 x 841 forward at 8);
+// mdc_autotune measures it per handle.
+constexpr int GEMV_GROUP_MAX_FWD = 8;
+constexpr int GEMV_GROUP_MAX_ADJ = 16;
 
 // path: PATH_GEMV, PATH_GEMV_GROUPS or PATH_SIMT (PATH_AUTO: GEMV when it fits, GEMV groups up to
-// GEMV_GROUP_MAX columns, else SIMT)
+// GEMV_GROUP_MAX_FWD or _ADJ columns, else SIMT)
 template <int FMT>
 bool product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_i, float2* out, int ldo,
                  int voff_o, int ncol, cudaStream_t s, const int* active, int path) {
@@ -813,7 +815,8 @@ bool product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_
     const bool group_fits = ncol > gw && gemv_fits(p, adjoint, gw, Fmt<FMT>::CPV);
     if (path == PATH_GEMV && !fits) return false;
     if (path == PATH_GEMV_GROUPS && !group_fits) return false;
-    const bool groups = group_fits && (path == PATH_GEMV_GROUPS || (path == PATH_AUTO && ncol <= GEMV_GROUP_MAX));
+    const int gmax = adjoint ? GEMV_GROUP_MAX_ADJ : GEMV_GROUP_MAX_FWD;
+    const bool groups = group_fits && (path == PATH_GEMV_GROUPS || (path == PATH_AUTO && ncol <= gmax));
     if ((fits && path != PATH_SIMT && path != PATH_GEMV_GROUPS) || groups) {
         for (int c0 = 0; c0 < ncol; c0 += gw) {
             const int nc = ncol - c0 < gw ? ncol - c0 : gw;
