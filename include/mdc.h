@@ -171,6 +171,12 @@ int mdc_reserve(mdc_handle h, int nv_max);
  * contents; every call overwrites all of it that it reads, so nothing needs
  * clearing.  Calls whose execution overlaps on the GPU (different streams without
  * ordering between them) race on the array and give wrong results: order them.
+ * Overlapping calls on the same handle also share the handle's tensor-core operand
+ * buffers, and race on those too.
+ * Tensor cores: with 16-bit, split or E4M3 storage, products of 8 or more columns run
+ * on tensor cores only if the handle's operand buffers were reserved beforehand
+ * (mdc_reserve(h, nv), which allocates, so call it at set-up); otherwise the product
+ * runs on the slower SIMT path (correct, and counted by mdc_tc_fallback_count).
  * Arguments, layout, ownership and errors are otherwise those of mdc_forward.
  */
 #define MDC_STATIC_SCRATCH_COMPLEX (1 << 21)
@@ -384,7 +390,21 @@ int mdc_autotune_choice(mdc_handle h, int adjoint, int ncol, int* path, int* bn)
  * (data vector, all LSQR iterations, refinement, Green's functions) is captured on first use with
  * a workspace the handle keeps (up to 4 cached solves; turning the option off frees them). */
 #define MDC_OPT_GRAPHS 1
+/* MDC_OPT_WAIT_LIMIT_US (value >= 0): bound, in microseconds of wall time, on each wait inside the
+ * tensor-core product kernel (TMA stages, MMA completion, accumulator hand-off); 0 restores the
+ * default of 2 s.  A wait that runs out makes the kernel record MDC_ERR_TIMEOUT in the handle's
+ * device flag (read by mdc_device_status), finish its copies and MMAs in flight, free its tensor
+ * memory and exit; the product's output is then incomplete.  Negative values: MDC_ERR_ARG.
+ * (Failure detection: a limit the pipeline cannot meet exercises that path.) */
+#define MDC_OPT_WAIT_LIMIT_US 2
 int mdc_set_option(mdc_handle h, int option, int value);
+/* mdc_tc_fallback_count -- number of per-frequency products, since the handle was created, that
+ * the tensor-core rule assigned to tensor cores (16-bit, split or E4M3 storage at 8 or more
+ * columns, or an autotuned tensor-core choice) but that ran on the SIMT/GEMV path instead, because
+ * the tensor-core operand buffers were not reserved for that many columns (mdc_reserve) or the
+ * launch could not be set up.  Results are correct either way; the count exposes the slower
+ * path.  -1 for a NULL handle.  Host-only. */
+int64_t mdc_tc_fallback_count(mdc_handle h);
 /* mdc_device_status -- synchronise `stream` and report MDC_ERR_TIMEOUT if a kernel of this
  * handle gave up a bounded device-side wait since the last check (the flag is then cleared). */
 int mdc_device_status(mdc_handle h, void* stream);

@@ -21,6 +21,7 @@ MDC_OK = 0
 MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3, MDC_C32S = 0, 1, 2, 3, 4
 STORAGE = {"c64": MDC_C64, "c16f": MDC_C16F, "cbf16": MDC_CBF16, "ce4m3": MDC_CE4M3, "c32s": MDC_C32S}
 MDC_CONJ_KERNEL = 0x1
+MDC_OPT_GRAPHS, MDC_OPT_WAIT_LIMIT_US = 1, 2
 KC_RFFT, KC_PRODUCT_FWD, KC_PRODUCT_ADJ, KC_IRFFT, KC_SOLVER, KC_TC_PREP = range(6)
 KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj": KC_PRODUCT_ADJ,
                   "irfft": KC_IRFFT, "solver": KC_SOLVER, "tc_prep": KC_TC_PREP}
@@ -51,6 +52,7 @@ SIGNATURES = {
     "mdc_launch_count": (_i64, [_vp]),
     "mdc_device_status": (_i, [_vp, _vp]),
     "mdc_set_option": (_i, [_vp, _i, _i]),
+    "mdc_tc_fallback_count": (_i64, [_vp]),
     "mdc_autotune": (_i, [_vp, _i, _vp]),
     "mdc_autotune_choice": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "srv_create": (_i, [ctypes.POINTER(_vp), _vp, _vp, _i64, _i, _i, _i, _vp]),
@@ -274,6 +276,11 @@ def mdc_autotune_choice(h, adjoint: bool, ncol: int) -> tuple:
 
 def mdc_set_option(h, option: int, value: int) -> None:
     _check(lib().mdc_set_option(h, option, value), "mdc_set_option")
+
+
+def mdc_tc_fallback_count(h) -> int:
+    """Products the tensor-core rule chose that ran on the SIMT/GEMV path (operands not reserved)."""
+    return int(lib().mdc_tc_fallback_count(h))
 
 
 def mdc_device_status(h, stream=None) -> None:

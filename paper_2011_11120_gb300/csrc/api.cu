@@ -388,10 +388,16 @@ extern "C" int mdc_set_option(mdc_handle h, int option, int value) {
                 h->graph_cache.clear();
             }
             return MDC_OK;
+        case MDC_OPT_WAIT_LIMIT_US:
+            if (value < 0) return MDC_ERR_ARG;
+            h->wait_ns = value == 0 ? 2000000000ull : (unsigned long long)value * 1000ull;
+            return MDC_OK;
         default:
             return MDC_ERR_ARG;
     }
 }
+
+extern "C" int64_t mdc_tc_fallback_count(mdc_handle h) { return h ? h->tc_fallbacks : -1; }
 
 extern "C" int mdc_device_status(mdc_handle h, void* stream) {
     if (!h) return MDC_ERR_ARG;

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "../../include/mdc.h"
@@ -20,6 +22,26 @@ __host__ __device__ inline float2 cmul(float2 a, float2 b) {
 __host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __host__ __device__ inline float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Dynamic shared-memory limit of one kernel, raised once per device.  The attribute belongs to the
+// device that is current when it is set, so a process driving several devices sets it on each; only
+// a successful call is remembered, and concurrent first calls are serialised.  A failure leaves the
+// error for the launch that follows (which then fails and is reported by the caller).
+struct SmemLimit {
+    std::atomic<uint64_t> done{0};
+    std::mutex m;
+    template <typename F> void ensure(F* func, int bytes) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0;
+        if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+        std::lock_guard<std::mutex> g(m);
+        if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+        if (cudaFuncSetAttribute(reinterpret_cast<const void*>(func), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes) == cudaSuccess)
+            done.fetch_or(bit, std::memory_order_release);
+    }
+};
 
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -78,6 +100,8 @@ struct mdc_plan {
     float* tcSigma = nullptr;   // [nf][tc_cap]
     int tc_cap = 0;
     int* err_flag = nullptr;    // device int: non-zero after a bounded device wait gave up
+    unsigned long long wait_ns = 2000000000ull;   // bound on each tensor-core pipeline wait
+    int64_t tc_fallbacks = 0;   // products the tensor-core rule chose that ran on another path
     bool force_tc = false;      // FP16/BF16: tensor-core products for every column count
     bool graphs = false;        // capture repeated solves into CUDA graphs (mdc_set_option)
     std::vector<mdc::ProductChoice> tune[2];   // autotuned variants [forward, adjoint], ascending ncol

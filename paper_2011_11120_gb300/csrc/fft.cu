@@ -924,11 +924,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
 template <int N1, int N2>
 void rfft_half_launch(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     using H = HalfStep<N1, N2>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(rfft_half_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H::smem);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(rfft_half_kernel<N1, N2>, (int)H::smem);
     LaunchScope ls(p, s, MDC_KC_RFFT);
     rfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
 }
@@ -939,11 +936,8 @@ void irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(irfft_half_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H::smem);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(irfft_half_kernel<N1, N2>, (int)H::smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
     irfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
 }
@@ -953,11 +947,8 @@ void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     using F = FourStep<N1, N2>;
     RfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && ((uintptr_t)a.x % 16 == 0) && (!a.x2 || (uintptr_t)a.x2 % 16 == 0);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(rfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem_full);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(rfft4_kernel<N1, N2>, (int)F::smem_full);
     LaunchScope ls(p, s, MDC_KC_RFFT);
     rfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
 }
@@ -968,11 +959,8 @@ void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(irfft4_kernel<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(irfft4_kernel<N1, N2>, (int)F::smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
     irfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
 }
@@ -1002,11 +990,8 @@ void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     }
     const int logCT = tile_log_columns(a.nt);
     const size_t smem = rfft_smem(a.nt, logCT);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(rfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static SmemLimit attr_set;
+    attr_set.ensure(rfft_kernel, 200 * 1024);
     const int grid = (a.C + (1 << logCT) - 1) >> logCT;
     LaunchScope ls(p, s, MDC_KC_RFFT);
     rfft_kernel<<<grid, FFT_THREADS, smem, s>>>(a, logCT);
@@ -1024,11 +1009,8 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     }
     const int logCT = tile_log_columns(a.nt);
     const size_t smem = irfft_smem(a.nt, logCT);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(irfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    static SmemLimit attr_set;
+    attr_set.ensure(irfft_kernel, 200 * 1024);
     const int grid = (a.C + (1 << logCT) - 1) >> logCT;
     LaunchScope ls(p, s, MDC_KC_IRFFT);
     irfft_kernel<<<grid, FFT_THREADS, smem, s>>>(a, logCT);

@@ -723,18 +723,12 @@ void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
             ldo, voff_o, active, lo_plane_vec(p));
         return;
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(gemv_fwd<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(gemv_fwd<FMT, NVC>, 220 * 1024);
     dim3 grid((p->nr + FWD_ROWS_PER_CTA - 1) / FWD_ROWS_PER_CTA, p->nf);
     if constexpr (FMT == MDC_C64) {
-        static bool attr64 = false;
-        if (!attr64) {
-            cudaFuncSetAttribute(gemv_fwd_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            attr64 = true;
-        }
+        static SmemLimit attr64;
+        attr64.ensure(gemv_fwd_c64<NVC>, 220 * 1024);
         gemv_fwd_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
             reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
             voff_o, active);
@@ -754,12 +748,8 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
     if (smem > (size_t)GEMV_STAGE_MAX && gemv_chunk_allowed()) {
         size_t csmem = (size_t)AdjChunk<NVC>::CHR * NVC * sizeof(float2);
         if (csmem < red) csmem = red;
-        static bool cattr = false;
-        if (!cattr) {
-            cudaFuncSetAttribute(gemv_adj_chunked<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 220 * 1024);
-            cattr = true;
-        }
+        static SmemLimit cattr;
+        cattr.ensure(gemv_adj_chunked<FMT, NVC>, 220 * 1024);
         dim3 grid((unsigned)((p->ldg + TILE - 1) / TILE), p->nf);
         gemv_adj_chunked<FMT, NVC><<<grid, GEMV_THREADS, csmem, s>>>(
             reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
@@ -767,18 +757,12 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         return;
     }
     if (smem < red) smem = red;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(gemv_adj<FMT, NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
+    static SmemLimit attr;
+    attr.ensure(gemv_adj<FMT, NVC>, 220 * 1024);
     dim3 grid((unsigned)((p->ldg + TILE - 1) / TILE), p->nf);
     if constexpr (FMT == MDC_C64) {
-        static bool attr64 = false;
-        if (!attr64) {
-            cudaFuncSetAttribute(gemv_adj_c64<NVC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-            attr64 = true;
-        }
+        static SmemLimit attr64;
+        attr64.ensure(gemv_adj_c64<NVC>, 220 * 1024);
         gemv_adj_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
             reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
             voff_o, active);
@@ -891,12 +875,18 @@ void launch_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int vo
                 break;
             }
     }
+    // the tensor-core rule wants this product on tensor cores (a tuned choice, or the default rule
+    // for tensor-core storage); when the operand buffers are missing (no mdc_reserve for this many
+    // columns) or the launch cannot be made, it runs on the SIMT/GEMV path and is counted
+    const bool tc_wanted =
+        path == PATH_TC || (path == PATH_AUTO && storage_tc(p->storage) && (ncol >= 8 || p->force_tc));
     if (path == PATH_TC || (path == PATH_AUTO && tc_supported(p, ncol))) {
         if (storage_tc(p->storage) && p->tcB && ncol <= p->tc_cap &&
             launch_tc_product(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, bn, true))
             return;
         path = PATH_AUTO;
     }
+    if (tc_wanted) ++p->tc_fallbacks;
     LaunchScope ls(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
     if (!product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, path))
         product_simt_or_gemv(p, adjoint, in, ldi, voff_i, out, ldo, voff_o, ncol, s, active, PATH_AUTO);

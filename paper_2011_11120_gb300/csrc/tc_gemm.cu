@@ -44,7 +44,9 @@ constexpr int TC_BK = 64;                       // reduction elements per stage 
 // added into float32 registers by the epilogue (round to nearest), so the tensor core's own
 // accumulation spans at most TC_KCHUNK * TC_BK products per output.
 constexpr int TC_KCHUNK = 4;
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // 2 s per wait
+// Bound on the two drain waits before a CTA exits (the producer's copies in flight, the MMA issuer's
+// last MMAs).  Those always complete, so this limit is not shortened with the pipeline's limit.
+constexpr unsigned long long TC_DRAIN_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long gtime() {
@@ -72,14 +74,14 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete, for at most TC_WAIT_NS.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// Wait for the phase with the given parity to complete, for at most limit_ns nanoseconds.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, unsigned long long limit_ns) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
         for (int i = 0; i < 256; ++i)
             if (mbar_test(bar, parity)) return true;
-        if (gtime() - t0 > TC_WAIT_NS) {
+        if (gtime() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             return false;
         }
@@ -92,24 +94,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
         "l"((unsigned long long)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
-}
-// Multicast variant: the box lands at the same shared-memory offset in every CTA of ctaMask and
-// signals the mbarrier at the same offset in each of them.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
-                                               int c1, int c2, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(dst),
-        "l"((unsigned long long)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -138,12 +122,6 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
-// Arrive (once the issued MMAs complete) on the mbarrier at this offset in every CTA of ctaMask.
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
-                 : "memory");
-}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -170,6 +148,7 @@ struct TcArgs {
     float2* out;
     int ldo, voff_o;
     int* err;
+    unsigned long long wait_ns; // bound on every mbarrier wait (wall time)
 };
 
 // Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies.
@@ -227,24 +206,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // continuously across tiles and the accumulator is double-buffered in TMEM (2 x BN columns),
 // so the epilogue of one tile overlaps the main loop of the next.
 //
-// PAIR: the grid is launched as clusters of two CTAs that take row tiles 2j and 2j + 1 of the
-// same column tile together; each loads its own A tile and half of the shared B tile, which TMA
-// multicasts into both CTAs' shared memory, so the L2-to-SM traffic for B halves.  A stage is
-// refilled only after both CTAs' MMAs have consumed it (the empty barrier counts the two
-// multicast commits).  n_tiles_m then counts row-tile pairs.
-//
 // CVT (E4M3 kernel copy): TMA brings each stage's A tile as bytes (128 rows x 64 B, unswizzled)
 // beside its B tile; warps 10..17 widen it to FP16 into the next free tile w of a small ring,
 // laid out as a 16-bit TMA load would have put it (128-byte swizzle), and arrive on conv[w]; the
 // MMA issuer waits for the stage (B) and conv[w] (A), and its commit frees both.  The MMA is
 // the ordinary kind::f16 with FP16 operands.
-template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
+template <bool ADJ, int BN, bool SPLIT, bool CVT = false>
 __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a,
                    uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
     static_assert(!(CVT && SPLIT), "E4M3 widening has no split form");
-    // the early exit is uniform over a cluster (the flag is one device word read by every CTA)
     if (active && *active == 0) return;
     using SC = TcStages<BN, SPLIT, CVT, ADJ>;
     constexpr int STAGES = SC::v;
@@ -264,30 +236,32 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     unsigned char* gbase = smem_raw + (base - raw);
     const uint32_t wbase = base + STAGES * STAGE_BYTES;          // (CVT) widened A tiles
     uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES + WBUF * WA_BYTES);
-    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot (two words), (CVT)
-    // conv[WBUF], wfree[WBUF], then the epilogue's double-buffered column scales of the current
-    // tile (16-byte aligned)
+    // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot (two words), the MMA
+    // issuer's drain barrier, (CVT) conv[WBUF], wfree[WBUF], then the epilogue's double-buffered
+    // column scales of the current tile (16-byte aligned)
     constexpr int SIG_OFF = 2 * STAGES + 6 + 2 * WBUF;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
     float* sig_s = reinterpret_cast<float*>(bars + SIG_OFF);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
+    const uint32_t drain0 = su32(bars + 2 * STAGES + 5);
     const uint32_t conv0 = su32(bars + 2 * STAGES + 6), wfree0 = conv0 + 8 * WBUF;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rank = PAIR ? (int)cluster_rank() : 0;
-    const int t_first = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-    const int t_stride = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int t_first = (int)blockIdx.x;
+    const int t_stride = (int)gridDim.x;
+    const unsigned long long wl = a.wait_ns;
 
     if (warp == 0) tmem_alloc(su32(tmem_slot), 2 * BN);
     if (threadIdx.x == 32) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(full0 + 8 * i, 1);
-            mbar_init(empty0 + 8 * i, PAIR ? 2 : 1);
+            mbar_init(empty0 + 8 * i, 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(accf0 + 8 * i, 1);
             mbar_init(acce0 + 8 * i, 256);
         }
+        mbar_init(drain0, 1);
         for (int i = 0; i < WBUF; ++i) {
             mbar_init(conv0 + 8 * i, TC_CVT_THREADS / 32);
             mbar_init(wfree0 + 8 * i, 1);
@@ -296,7 +270,6 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     }
     tc_fence_before();
     __syncthreads();
-    if (PAIR) cluster_sync();            // the peer's barriers exist before any multicast lands
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int per_freq = n_tiles_n * n_tiles_m;
@@ -305,7 +278,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
         k = t / per_freq;
         const int rem = t - k * per_freq;
         const int mt = rem / n_tiles_n;
-        m0 = (PAIR ? 2 * mt + rank : mt) * TC_BM;
+        m0 = mt * TC_BM;
         n0 = (rem - mt * n_tiles_n) * BN;
     };
 
@@ -319,7 +292,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 for (int kb = 0; kb < ksteps; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
                     const uint32_t round = (uint32_t)(g / STAGES);
-                    if (g >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1)) {
+                    if (g >= STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, a.err, 1, wl)) {
                         ok = false;
                         break;
                     }
@@ -336,11 +309,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                         for (int h = 0; h < KSUB; ++h) {
                             const uint32_t bt = sa + h * B_BYTES;
                             const int kx = (kb * KSUB + h) * TC_BK;
-                            if (PAIR)
-                                tma_load_3d_mc(bt + rank * (B_BYTES / 2), &tmB, full0 + 8 * s, kx,
-                                               n0 + rank * (BN / 2), k, (uint16_t)0x3);
-                            else
-                                tma_load_3d(bt, &tmB, full0 + 8 * s, kx, n0, k);
+                            tma_load_3d(bt, &tmB, full0 + 8 * s, kx, n0, k);
                         }
                         continue;
                     }
@@ -356,17 +325,13 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                             tma_load_3d(ha, ma, full0 + 8 * s, m0, kb * TC_BK, k);
                             tma_load_3d(ha + A_BYTES / 2, ma, full0 + 8 * s, m0 + 64, kb * TC_BK, k);
                         }
-                        if (PAIR)   // this CTA's half of the B tile, into both CTAs of the pair
-                            tma_load_3d_mc(hb + rank * (B_BYTES / 2), mb, full0 + 8 * s, kb * TC_BK,
-                                           n0 + rank * (BN / 2), k, (uint16_t)0x3);
-                        else
-                            tma_load_3d(hb, mb, full0 + 8 * s, kb * TC_BK, n0, k);
+                        tma_load_3d(hb, mb, full0 + 8 * s, kb * TC_BK, n0, k);
                     }
                 }
             }
             // drain: every copy this thread issued must have landed before the CTA can exit
             for (long q = g > STAGES ? g - STAGES : 0; q < g; ++q)
-                mbar_wait(full0 + 8 * (int)(q % STAGES), (uint32_t)(q / STAGES) & 1, a.err, 2);
+                mbar_wait(full0 + 8 * (int)(q % STAGES), (uint32_t)(q / STAGES) & 1, a.err, 2, TC_DRAIN_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -377,7 +342,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
               for (int kb0 = 0; kb0 < ksteps && ok; kb0 += kc, ++i) {
                 const int buf = (int)(i & 1);
-                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5)) {
+                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5, wl)) {
                     ok = false;
                     break;
                 }
@@ -386,13 +351,13 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 const int kb1 = kb0 + kc < ksteps ? kb0 + kc : ksteps;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
-                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3)) {
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 3, wl)) {
                         ok = false;
                         break;
                     }
                     const int w = CVT ? (int)(g % WBUF) : 0;
                     // CVT: the widened A tile of this step
-                    if (CVT && !mbar_wait(conv0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1)) & 1, a.err, 7)) {
+                    if (CVT && !mbar_wait(conv0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1)) & 1, a.err, 7, wl)) {
                         ok = false;
                         break;
                     }
@@ -416,12 +381,15 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                             umma_f16(d, sdesc(sa2 + ao, lbo, 1024), bd, idesc, 1u);
                         }
                     }
-                    if (PAIR) umma_commit_mc(empty0 + 8 * s, (uint16_t)0x3);   // both CTAs refill s
-                    else umma_commit(empty0 + 8 * s);
+                    umma_commit(empty0 + 8 * s);
                     if (CVT) umma_commit(wfree0 + 8 * w);                     // the widened tile is free
                 }
                 umma_commit(accf0 + 8 * buf);
               }
+            // drain: every MMA this thread issued has completed (it reads shared memory and writes
+            // TMEM) before the CTA frees TMEM and exits, also when a wait above gave up
+            umma_commit(drain0);
+            mbar_wait(drain0, 0, a.err, 9, TC_DRAIN_NS);
         }
     } else if (CVT && warp >= TC_THREADS / 32) {
         // widen each stage's byte tile: item (row R, 8-byte chunk j) -> 16 bytes at row R, chunk
@@ -433,12 +401,12 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             for (int kb = 0; kb < ksteps; ++kb, ++g) {
                 const int s = (int)(g % STAGES);
                 const int w = (int)(g % (CVT ? WBUF : 1));
-                if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 6)) {
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 6, wl)) {
                     ok = false;
                     break;
                 }
                 // the MMAs that read this widened tile on its previous use are complete
-                if (g >= WBUF && !mbar_wait(wfree0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1) - 1) & 1, a.err, 8)) {
+                if (g >= WBUF && !mbar_wait(wfree0 + 8 * w, (uint32_t)(g / (CVT ? WBUF : 1) - 1) & 1, a.err, 8, wl)) {
                     ok = false;
                     break;
                 }
@@ -553,7 +521,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 for (int c = 0; c < BH; ++c) acc[c] = 0.f;
                 for (int ch = 0; ch < nch; ++ch, ++i) {
                     const int buf = (int)(i & 1);
-                    if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) {
+                    if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4, wl))) {
                         ok = false;
                         break;
                     }
@@ -574,7 +542,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 for (int c0 = 0; c0 < BH; c0 += 16) emit(cbeg + c0, acc + c0);
             } else {
                 const int buf = (int)(i & 1);
-                if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4))) break;
+                if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4, wl))) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
 #pragma unroll 1
@@ -594,7 +562,6 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     }
     tc_fence_before();
     __syncthreads();
-    if (PAIR) cluster_sync();            // no CTA leaves while its peer may still multicast into it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 2 * BN);
@@ -841,71 +808,28 @@ int pick_bn(int n2) {
     return 256;
 }
 
+// SMs of the current device (queried per call: a process may drive several devices)
 int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
 }
 
-// grid: (column tiles, row tiles, frequencies).  PAIR launches clusters of two CTAs over row-tile
-// pairs (an odd last row tile is paired with an empty one whose rows fall outside the output).
-bool g_pair_off = false;   // set when a cluster launch is refused: later products use single CTAs
-
-template <bool ADJ, int BN, bool SPLIT, bool PAIR, bool CVT = false>
+// grid: (column tiles, row tiles, frequencies), walked by min(tiles, SMs) persistent CTAs.
+template <bool ADJ, int BN, bool SPLIT, bool CVT = false>
 bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 grid, cudaStream_t s,
                const int* active) {
-    static bool attr = false;
+    static SmemLimit attr;
     const size_t smem = tc_smem_bytes<BN, SPLIT, CVT, ADJ>();
     constexpr int THREADS = CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS;
-    auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, PAIR, CVT>;
-    if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    const int rows = PAIR ? (int)(grid.y + 1) / 2 : (int)grid.y;
-    const int n_tiles = (int)grid.x * rows * (int)grid.z;
-    if (!PAIR) {
-        const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
-        kern<<<ctas, THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
-                                         n_tiles);
-        return true;
-    }
-    const int pairs = n_tiles < sm_count() / 2 ? n_tiles : sm_count() / 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * pairs));
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x, rows,
-                           n_tiles) != cudaSuccess) {
-        cudaGetLastError();
-        g_pair_off = true;
-        return false;
-    }
+    auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, CVT>;
+    attr.ensure(kern, (int)smem);
+    const int n_tiles = (int)grid.x * (int)grid.y * (int)grid.z;
+    const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
+    kern<<<ctas, THREADS, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a, idesc, active, (int)grid.x,
+                                     (int)grid.y, n_tiles);
     return true;
-}
-
-// Paired CTAs (B multicast) for wide column tiles with at least two row tiles; MDC_TC_PAIR=0 in
-// the environment turns it off.
-bool use_pair(int bn, int row_tiles) {
-    static int env = -1;
-    if (env < 0) {
-        const char* e = getenv("MDC_TC_PAIR");
-        env = (e && e[0] == '0') ? 0 : 1;
-    }
-    return env == 1 && !g_pair_off && bn >= 128 && row_tiles >= 2;
 }
 
 }  // namespace
@@ -978,8 +902,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const size_t blo = plane * 2;                                          // lo plane of B (bytes)
     // row tiles of the product (kernel rows forward; 2 * ldg interleaved reals adjoint)
     const int mrows = adjoint ? (int)(kp / TC_BM) : (p->nr + TC_BM - 1) / TC_BM;
-    const bool pair = use_pair(bn, mrows);
-    const int bbox = pair ? bn / 2 : bn;      // paired CTAs each load half of the B tile
+    const int bbox = bn;
     bool ok = true;
     const uint64_t ab = e4m3 ? 1 : 2;         // bytes per real of the kernel copy
     // E4M3 byte tiles: forward 128 rows x 128 bytes for B tiles of <= 64 columns (two reduction
@@ -1013,6 +936,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     a.ldo = ldo;
     a.voff_o = voff_o;
     a.err = p->err_flag;
+    a.wait_ns = p->wait_ns;
     const uint32_t fmt = bf16 ? 1u : 0u;
     const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((adjoint ? 1u : 0u) << 15) |
                            ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
@@ -1020,11 +944,9 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     if (scoped) scope.emplace(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
 #define MDC_TC_LAUNCH(ADJV, BV, SPV)                                                             \
     if (e4m3)                                                                                    \
-        launched = pair ? launch_tc<ADJV, BV, false, true, true>(maps, a, idesc, grid, s, active)   \
-                        : launch_tc<ADJV, BV, false, false, true>(maps, a, idesc, grid, s, active); \
+        launched = launch_tc<ADJV, BV, false, true>(maps, a, idesc, grid, s, active);               \
     else                                                                                         \
-        launched = pair ? launch_tc<ADJV, BV, SPV, true>(maps, a, idesc, grid, s, active)           \
-                        : launch_tc<ADJV, BV, SPV, false>(maps, a, idesc, grid, s, active);
+        launched = launch_tc<ADJV, BV, SPV>(maps, a, idesc, grid, s, active);
 #define MDC_TC_CASE(BNV)                                                                   \
     case BNV:                                                                              \
         if (split) {                                                                       \

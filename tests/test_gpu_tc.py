@@ -84,40 +84,3 @@ def test_tc_e4m3_widened_matches_oracle(nt, nr, ns, nf, nv):
     lhs = np.vdot(yg.astype(np.float64), y)
     rhs = np.vdot(x.astype(np.float64), xg)
     assert abs(lhs - rhs) <= 8 * U16 * np.linalg.norm(yg) * np.linalg.norm(y)
-
-
-_PAIR_SCRIPT = r"""
-import sys, numpy as np, torch
-sys.path.insert(0, {root!r})
-import paper_2011_11120_gb300 as m
-rng = np.random.default_rng(5)
-nt, nr, ns, nf, nv = 128, 300, 280, 6, 150
-G = (rng.standard_normal((nf, nr, ns)) + 1j * rng.standard_normal((nf, nr, ns))) / np.sqrt(ns)
-x = rng.standard_normal((nt, ns, nv)).astype(np.float32)
-y = rng.standard_normal((nt, nr, nv)).astype(np.float32)
-op = m.MDC(torch.from_numpy(G.astype(np.complex64)).cuda(), nt, 0.004, 400.0, storage={storage!r})
-yg = op.forward(torch.from_numpy(x).cuda()).cpu().numpy()
-xg = op.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
-m.mdc_device_status(op.h)
-op.close()
-np.save({out!r}, np.concatenate([yg.ravel(), xg.ravel()]))
-"""
-
-
-@pytest.mark.parametrize("storage", ["c16f", "c32s", "ce4m3"])
-def test_paired_and_single_cta_products_agree(tmp_path, storage):
-    """The two-CTA clusters sharing B by multicast (default for wide column tiles) and the
-    single-CTA kernel (MDC_TC_PAIR=0) give bit-identical products: pairing only changes which SM
-    computes a tile, not the order of any sum."""
-    import os
-    import subprocess
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    outs = []
-    for pair in ("1", "0"):
-        out = str(tmp_path / f"p{pair}.npy")
-        env = dict(os.environ, MDC_TC_PAIR=pair)
-        code = _PAIR_SCRIPT.format(root=root, storage=storage, out=out)
-        subprocess.run([sys.executable, "-c", code], env=env, check=True, timeout=600)
-        outs.append(np.load(out))
-    assert np.array_equal(outs[0], outs[1])

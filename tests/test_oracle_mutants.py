@@ -5,6 +5,7 @@ import pytest
 
 from oracle import marchenko, mdc, solvers
 
+import test_oracle_greens as pins_g
 import test_oracle_marchenko_lsqr as pins_m
 import test_oracle_mdc as pins
 
@@ -37,6 +38,25 @@ def _one_sided_window(cutoffs, nt):
 def _rmatvec_wrong_block(self, g):
     a, b = g
     return (a - self.RH(self.theta * b), b - self.RH(self.theta * a))
+
+
+def _data_without_window(self, fd_plus):
+    fd_plus = np.asarray(fd_plus, dtype=np.float64)
+    return (self.R(fd_plus), np.zeros_like(fd_plus))
+
+
+def _greens_r_rstar_swapped(self, f_minus, f_mplus, fd_plus):
+    f_plus = np.asarray(fd_plus, dtype=np.float64) + f_mplus
+    g_minus = -(f_minus - self.Rstar(f_plus))
+    g_plus_star = f_plus - self.R(f_minus)
+    return g_minus, g_plus_star, marchenko.time_reverse(g_plus_star)
+
+
+def _greens_g_minus_sign(self, f_minus, f_mplus, fd_plus):
+    f_plus = np.asarray(fd_plus, dtype=np.float64) + f_mplus
+    g_minus = f_minus - self.R(f_plus)
+    g_plus_star = f_plus - self.Rstar(f_minus)
+    return g_minus, g_plus_star, marchenko.time_reverse(g_plus_star)
 
 
 def _lsqr_wrong_rhobar_sign(matvec, rmatvec, b, niter, tol=0.0, x_like=None):
@@ -83,6 +103,14 @@ MUTANTS = [
      pins_m.test_dense_adjoint_is_transpose),
     ("LSQR rhobar sign error", solvers, "lsqr", _lsqr_wrong_rhobar_sign,
      pins_m.test_lsqr_n_iterations_equals_dense_lstsq),
+    ("data vector without the window", marchenko.Marchenko, "data", _data_without_window,
+     pins_g.test_data_vector_is_windowed_convolution),
+    ("Green's functions with R and R* exchanged", marchenko.Marchenko, "greens", _greens_r_rstar_swapped,
+     pins_g.test_greens_with_zero_f_minus),
+    ("Green's functions with R and R* exchanged (f+ = 0)", marchenko.Marchenko, "greens",
+     _greens_r_rstar_swapped, pins_g.test_greens_with_zero_f_plus),
+    ("g- with the opposite sign", marchenko.Marchenko, "greens", _greens_g_minus_sign,
+     pins_g.test_greens_general_case_is_linear_combination),
 ]
 
 
