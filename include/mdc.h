@@ -147,6 +147,50 @@ int mdc_adjoint(mdc_handle h, const float* y, float* x, int nv, unsigned flags, 
 int mdc_reserve(mdc_handle h, int nv_max);
 
 /*
+ * Frequency shards.  The method partitions the kernel along frequency with no communication
+ * inside the per-frequency products (Section "Implementing the batch matrix multiplication
+ * operator", Fig. 2): since the inverse transform is linear, the output of C is the sum over
+ * disjoint bands of frequencies of each band's partial inverse transform.  A shard handle holds
+ * bins k0 .. k0+nk-1 of the kernel; several of them (one per device or process) whose bands
+ * tile 0 .. nfmax-1 make up the whole operator.
+ *
+ * mdc_create_shard -- as mdc_create for the kernel frequencies k0 .. k0+nk-1 only.
+ *   G       device pointer, complex64 [nk][nr][ns] (bins k0 .. k0+nk-1), or NULL for a zero
+ *           kernel to be filled with mdc_load_slab (its k0 then counts from the shard's first
+ *           bin, 0 <= k0 + nk <= this shard's nk).
+ *   k0, nk  0 <= k0, nk >= 1, k0 + nk <= nt/2 + 1 (MDC_ERR_ARG otherwise).
+ * Without a reduction hook, mdc_forward / mdc_adjoint on a shard return the shard's partial
+ * output (the inverse transform of its bins only, with the DC and Nyquist bins weighted once
+ * and every other bin twice, as in the whole operator); the caller sums them.  Blocking.
+ */
+int mdc_create_shard(mdc_handle* out, const void* G, int k0, int nk, int nr, int ns, int nt, double dt, double dr,
+                     int storage, void* stream);
+
+/*
+ * mdc_allreduce_fn -- the caller's sum over shards.  Called on the host thread of the library
+ * call, in stream order: buf is a library-owned device array of `count` float32 values holding
+ * this shard's partial signal; on return the work the function enqueued on `stream` (a
+ * cudaStream_t as void*) must leave in buf the element-wise sum over all shards, or the
+ * function must have synchronised `stream`, summed and copied back itself.  Every shard calls
+ * it the same number of times with the same counts.  Returns MDC_OK or a negative status,
+ * which the library call then returns.
+ */
+typedef int (*mdc_allreduce_fn)(float* buf, int64_t count, void* stream, void* ctx);
+
+/*
+ * mdc_set_allreduce -- give a shard handle its sum over shards (fn NULL removes it).  With a
+ * hook, every inverse transform of the handle (mdc_forward, mdc_adjoint, marchenko_lsqr,
+ * marchenko_lsqr_refined, marchenko_neumann, mdd_lsqr) writes its partial signal [nt][C] to a
+ * handle-owned buffer (allocated on first use, grown as needed), calls fn on it, and applies
+ * the remaining terms (window, identity and LSQR terms, norms) to the sum, so every shard
+ * holds the complete result and identical LSQR scalars: the shards' solvers run in lock step,
+ * one sum per pass, the LSQR vectors replicated.  Solves on a shard handle need a hook
+ * (MDC_ERR_STATE otherwise); CUDA-graph replay is not used on hooked handles, and the serving
+ * engine does not take shards.  MDC_ERR_ARG for a handle that is not a shard.
+ */
+int mdc_set_allreduce(mdc_handle h, mdc_allreduce_fn fn, void* ctx);
+
+/*
  * mdc_forward_static_scratch -- y = C x (or R* x with MDC_CONJ_KERNEL) exactly as
  * mdc_forward, but without allocating anything: the two frequency-domain work
  * arrays live in one fixed device array compiled into the library instead of in

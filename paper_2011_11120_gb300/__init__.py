@@ -28,11 +28,15 @@ KERNEL_CLASSES = {"rfft": KC_RFFT, "product_fwd": KC_PRODUCT_FWD, "product_adj":
 
 # exported symbol -> (restype, argtypes)
 _vp, _i, _d, _u, _i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_int64
+# mdc_allreduce_fn: int (*)(float* buf, int64_t count, void* stream, void* ctx)
+MDC_ALLREDUCE_FN = ctypes.CFUNCTYPE(_i, _vp, _i64, _vp, _vp)
 SIGNATURES = {
     "mdc_create": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i, _i, _d, _d, _i, _vp]),
     "mdc_create_weighted": (_i, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(_d), _i, _i, _i, _i, _d, _d, _i, _vp]),
     "mdc_create_empty": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _d, _d, _i, _vp]),
     "mdc_load_slab": (_i, [_vp, _vp, _i, _i, _vp]),
+    "mdc_create_shard": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i, _i, _i, _d, _d, _i, _vp]),
+    "mdc_set_allreduce": (_i, [_vp, MDC_ALLREDUCE_FN, _vp]),
     "mdc_forward": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_adjoint": (_i, [_vp, _vp, _vp, _i, _u, _vp]),
     "mdc_reserve": (_i, [_vp, _i]),
@@ -370,6 +374,82 @@ class MDC:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ frequency shards
+def shard_bounds(nf: int, world: int, rank: int) -> tuple:
+    """Bins (k0, nk) of shard ``rank`` when nf kernel frequencies are split into ``world``
+    contiguous bands of near-equal size (the first nf % world bands one bin longer)."""
+    if world < 1 or not 0 <= rank < world or nf < world:
+        raise ValueError("need 0 <= rank < world <= nf")
+    base, extra = divmod(nf, world)
+    k0 = rank * base + min(rank, extra)
+    return k0, base + (1 if rank < extra else 0)
+
+
+def mdc_create_shard(G_shard: Optional[torch.Tensor], k0: int, nk: int, nr: int, ns: int, nt: int, dt: float,
+                     dr: float, storage="c64", stream=None) -> ctypes.c_void_p:
+    """A handle for kernel bins k0 .. k0+nk-1 (G_shard complex64 [nk, nr, ns], or None for a zero
+    kernel filled with ``mdc_load_slab``)."""
+    if G_shard is not None and (G_shard.dtype != torch.complex64 or tuple(G_shard.shape) != (nk, nr, ns)):
+        raise ValueError("G_shard must be complex64 [nk, nr, ns]")
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    h = ctypes.c_void_p()
+    _check(lib().mdc_create_shard(ctypes.byref(h), _ptr(G_shard, name="G_shard"), k0, nk, nr, ns, nt, dt, dr, st,
+                                  _stream(stream)), "mdc_create_shard")
+    return h
+
+
+def mdc_set_allreduce(h, fn, ctx=None) -> None:
+    """Register an MDC_ALLREDUCE_FN (keep a reference to it while the handle lives), or None."""
+    _check(lib().mdc_set_allreduce(h, fn if fn is not None else MDC_ALLREDUCE_FN(), ctx), "mdc_set_allreduce")
+
+
+class _DeviceFloats:
+    """A float32 device array owned by the library, seen by torch without a copy."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+class ShardedMDC(MDC):
+    """This process's frequency shard of an MDC operator; the partial inverse transforms are
+    summed over a ``torch.distributed`` group (NCCL on device buffers, or any CPU backend such as
+    gloo through host copies), once per pass.  Every process of the group holds the complete
+    results, and solves (``marchenko``, ``neumann``, ``mdd``, ``marchenko_refined``) run in lock
+    step on every process with identical arguments.
+
+    ``G_shard`` is the kernel's bins ``k0 .. k0+nk-1`` (complex64 [nk, nr, ns]), or None with
+    ``shape=(nk, nr, ns)`` for a zero kernel filled with ``load_slab``."""
+
+    def __init__(self, G_shard: Optional[torch.Tensor], k0: int, nt: int, dt: float, dr: float, storage="c64",
+                 group=None, shape=None, stream=None):
+        import torch.distributed as dist
+        nk, nr, ns = tuple(G_shard.shape) if G_shard is not None else tuple(shape)
+        self.nf, self.nr, self.ns, self.k0 = nk, nr, ns, k0
+        self.nt, self.dt, self.dr = nt, dt, dr
+        self.group = group
+        self._dist = dist
+        self._nccl = dist.get_backend(group) == "nccl"
+        self.h = mdc_create_shard(G_shard, k0, nk, nr, ns, nt, dt, dr, storage, stream)
+        self._fn = MDC_ALLREDUCE_FN(self._allreduce)
+        mdc_set_allreduce(self.h, self._fn)
+
+    def _allreduce(self, buf, count, stream, ctx):
+        try:
+            t = torch.as_tensor(_DeviceFloats(int(buf), int(count)), device="cuda")
+            st = torch.cuda.ExternalStream(int(stream)) if stream else torch.cuda.default_stream()
+            with torch.cuda.stream(st):
+                if self._nccl:
+                    self._dist.all_reduce(t, group=self.group)
+                else:
+                    host = t.cpu()                   # ordered after the partial transform
+                    self._dist.all_reduce(host, group=self.group)
+                    t.copy_(host)
+            return MDC_OK
+        except Exception:                             # noqa: BLE001 -- no exception crosses the C ABI
+            return -7
 
 
 # ------------------------------------------------------------------ serving

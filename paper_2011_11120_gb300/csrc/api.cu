@@ -94,6 +94,7 @@ static void free_plan(mdc_plan* p) {
     cudaFree(p->tcB);
     cudaFree(p->tcSigma);
     cudaFree(p->err_flag);
+    cudaFree(p->red_buf);
     for (auto& e : p->timing.pool) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -111,11 +112,11 @@ __global__ void scale_columns(float2* __restrict__ G, int ns, size_t ldg, const 
 }
 
 static int create_plan(mdc_handle* out, const void* G, const double* weights, int nfmax, int nr, int ns, int nt,
-                       double dt, double dr, int storage, void* stream) {
+                       double dt, double dr, int storage, void* stream, int k0 = 0, bool shard = false) {
     if (!out) return MDC_ERR_ARG;
     *out = nullptr;
     // G == nullptr: an empty (zero) kernel copy, filled later by mdc_load_slab
-    if (nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || nfmax > nt / 2 + 1) return MDC_ERR_ARG;
+    if (nr < 1 || ns < 1 || !valid_nt(nt) || nfmax < 1 || k0 < 0 || k0 + nfmax > nt / 2 + 1) return MDC_ERR_ARG;
     if (!(dt > 0.0) || !(dr > 0.0) || !std::isfinite(dt) || !std::isfinite(dr)) return MDC_ERR_ARG;
     if (storage < MDC_C64 || storage > MDC_C32S) return MDC_ERR_ARG;
     if ((int64_t)nr * nfmax > (int64_t)1 << 31) return MDC_ERR_ARG;
@@ -123,6 +124,7 @@ static int create_plan(mdc_handle* out, const void* G, const double* weights, in
     mdc_plan* p = new (std::nothrow) mdc_plan();
     if (!p) return MDC_ERR_OOM;
     p->nf = nfmax; p->nr = nr; p->ns = ns; p->nt = nt; p->logn = ilog2(nt);
+    p->k0 = k0; p->shard = shard;
     p->dt = dt; p->dr = dr; p->storage = storage;
     p->ldg = round_up(ns, G_PITCH_ALIGN);
     const size_t rowbytes = (size_t)p->ldg * storage_bytes(storage);
@@ -196,6 +198,18 @@ extern "C" int mdc_create(mdc_handle* out, const void* G, int nfmax, int nr, int
 extern "C" int mdc_create_empty(mdc_handle* out, int nfmax, int nr, int ns, int nt, double dt, double dr,
                                 int storage, void* stream) {
     return create_plan(out, nullptr, nullptr, nfmax, nr, ns, nt, dt, dr, storage, stream);
+}
+
+extern "C" int mdc_create_shard(mdc_handle* out, const void* G, int k0, int nk, int nr, int ns, int nt, double dt,
+                                double dr, int storage, void* stream) {
+    return create_plan(out, G, nullptr, nk, nr, ns, nt, dt, dr, storage, stream, k0, true);
+}
+
+extern "C" int mdc_set_allreduce(mdc_handle h, mdc_allreduce_fn fn, void* ctx) {
+    if (!h || !h->shard) return MDC_ERR_ARG;
+    h->red_fn = fn;
+    h->red_ctx = fn ? ctx : nullptr;
+    return MDC_OK;
 }
 
 extern "C" int mdc_load_slab(mdc_handle h, const void* G_slab, int k0, int nk, void* stream) {
@@ -284,13 +298,13 @@ static int mdc_pass(mdc_plan* p, bool adjoint, const float* in, float* outp, int
     const int conj = (flags & MDC_CONJ_KERNEL) ? 1 : 0;
     RfftArgs ra{};
     ra.x = in; ra.x2 = nullptr; ra.C = S_in * nv; ra.S = S_in; ra.nv = nv;
-    ra.nt = p->nt; ra.logn = p->logn; ra.nf = p->nf; ra.cut = nullptr; ra.scale = C1(1.f);
+    ra.nt = p->nt; ra.logn = p->logn; ra.nf = p->nf; ra.k0 = p->k0; ra.cut = nullptr; ra.scale = C1(1.f);
     ra.conj = conj; ra.X = p->specA; ra.ldv = nv; ra.voff = 0; ra.tw = p->tw; ra.active = nullptr;
     launch_rfft(p, ra, s);
     launch_product(p, adjoint, p->specA, nv, 0, p->specB, nv, 0, nv, s, nullptr);
     IrfftArgs ia{};
     ia.Y = p->specB; ia.ldv = nv; ia.voff = 0; ia.C = S_out * nv; ia.S = S_out; ia.nv = nv;
-    ia.nt = p->nt; ia.logn = p->logn; ia.nf = p->nf; ia.conj_in = conj;
+    ia.nt = p->nt; ia.logn = p->logn; ia.nf = p->nf; ia.k0 = p->k0; ia.conj_in = conj;
     ia.scale = (float)(p->dt * p->dr / (double)p->nt);
     ia.out = outp; ia.a_mdc = C1(1.f); ia.a_base = C1(0.f); ia.a_prev = C1(0.f);
     ia.base = nullptr; ia.cut = nullptr; ia.reverse_out = 0; ia.colsum = nullptr; ia.tw = p->tw;
@@ -298,7 +312,7 @@ static int mdc_pass(mdc_plan* p, bool adjoint, const float* in, float* outp, int
     launch_irfft(p, ia, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(e); return MDC_ERR_CUDA; }
-    return MDC_OK;
+    return take_host_error(p);
 }
 
 extern "C" int mdc_forward(mdc_handle h, const float* x, float* y, int nv, unsigned flags, void* stream) {

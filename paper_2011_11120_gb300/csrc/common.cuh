@@ -84,6 +84,17 @@ struct TimingState {
 
 struct mdc_plan {
     int nf, nr, ns, nt, logn;
+    // Frequency shard: this handle holds bins k0 .. k0 + nf - 1 of the nt-point transform (k0 = 0
+    // and no hook for an ordinary handle).  With a reduction hook every inverse transform writes
+    // its partial signal to red_buf, the hook sums it over all shards, and the epilogue runs on
+    // the sum.
+    int k0 = 0;
+    bool shard = false;
+    mdc_allreduce_fn red_fn = nullptr;
+    void* red_ctx = nullptr;
+    float* red_buf = nullptr;
+    int64_t red_cap = 0;        // floats in red_buf
+    int host_error = 0;         // first failure inside a pass (allocation, hook), taken by the entry point
     double dt, dr;
     int storage;
     int64_t ldg;                // row pitch of the kernel copy, in complex elements
@@ -128,6 +139,7 @@ struct RfftArgs {
     const float* x2;       // optional second input added to x (same layout), or null
     int C, S, nv;          // C = S * nv real columns
     int nt, logn, nf;
+    int k0;                // first bin kept: X[j] holds bin k0 + j, j < nf (a frequency slab)
     const int* cut;        // Theta cut-offs [C] applied to the input, or null
     Coef scale;            // multiplies the input
     int conj;              // conjugate the output spectrum (time reversal of the input)
@@ -141,6 +153,7 @@ struct IrfftArgs {
     const float2* Y;       // [nf][S][ldv]
     int ldv, voff;
     int C, S, nv, nt, logn, nf;
+    int k0;                // Y[j] holds bin k0 + j (j < nf); every other bin is zero
     int conj_in;           // conjugate the input spectrum before the inverse transform
     float scale;           // multiplies the inverse transform (1/nt and dt*dr folded in)
     float* out;            // [nt][C]
@@ -155,7 +168,15 @@ struct IrfftArgs {
     int vec4;              // set by the launcher: aligned 4-column output path
 };
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
+// The inverse transform; on a frequency shard with a reduction hook: the partial transform, the
+// hook's sum over shards, then the epilogue (failures go to p->host_error).
 void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
+// Status of the plan's last failure inside a pass (MDC_OK if none), cleared.
+inline int take_host_error(mdc_plan* p) {
+    const int e = p->host_error;
+    p->host_error = 0;
+    return e;
+}
 
 // Per-frequency products on the library layout.
 //   forward: Y[k][r][voff_o + j] = sum_s G[k][r][s] X[k][s][voff_i + j], j < ncol

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft_kernel(RfftArgs a, int logCT
     for (int idx = threadIdx.x; idx < (a.nf << logCT); idx += FFT_THREADS) {
         const int k = idx >> logCT, cl = idx & (CT - 1), c = c0 + cl;
         if (c >= a.C) continue;
-        const int j = cl >> 1;
-        const float2 Z = reinterpret_cast<const float2*>(zf + k * RS)[j];
-        const float2 Zm = reinterpret_cast<const float2*>(zf + ((nt - k) & (nt - 1)) * RS)[j];
+        const int j = cl >> 1, kb = k + a.k0;                    // bin of the slab's k-th entry
+        const float2 Z = reinterpret_cast<const float2*>(zf + kb * RS)[j];
+        const float2 Zm = reinterpret_cast<const float2*>(zf + ((nt - kb) & (nt - 1)) * RS)[j];
         float2 r;
         if ((cl & 1) == 0) r = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
         else               r = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
@@ -114,10 +114,10 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft_kernel(IrfftArgs a, int log
         const int j = idx & (P - 1), k = idx >> logP;
         const int kk = k <= (nt >> 1) ? k : nt - k;
         float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-        if (kk < a.nf) {
+        if (kk >= a.k0 && kk < a.k0 + a.nf) {
             const int ca = c0 + 2 * j;
-            if (ca < a.C) A = load_bin(a, kk, ca);
-            if (ca + 1 < a.C) B = load_bin(a, kk, ca + 1);
+            if (ca < a.C) A = load_bin(a, kk - a.k0, ca);
+            if (ca + 1 < a.C) B = load_bin(a, kk - a.k0, ca + 1);
             if (a.conj_in) { A.y = -A.y; B.y = -B.y; }
             if (kk == 0 || 2 * kk == nt) { A.y = 0.f; B.y = 0.f; }
             if (k > (nt >> 1)) { A.y = -A.y; B.y = -B.y; }
@@ -451,18 +451,20 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         const size_t kstride = (size_t)a.S * a.ldv;
         const int j = cl >> 1;
         const bool odd = (cl & 1) != 0;
-        for (int k1 = g; k1 < N1 && k1 < a.nf; k1 += G) {
+        const int kend = a.k0 + a.nf;                              // bins [k0, kend) are written
+        for (int k1 = g; k1 < N1 && k1 < kend; k1 += G) {
             const int mk1 = (N1 - k1) & (N1 - 1);
             const float2* zr = z + F::zi(k1 * N2, j);              // rows k1 * N2 + k2
             const float2* zm = z + F::zi(mk1 * N2, j);             // rows mk1 * N2 + (...)
             int mrow2 = NT / N1 - (k1 > 0 ? 1 : 0);                // second index of the mirror row
-            for (int k = k1, k2 = 0; k < a.nf; k += N1, ++k2, --mrow2) {
+            for (int k = k1, k2 = 0; k < kend; k += N1, ++k2, --mrow2) {
+                if (k < a.k0) continue;
                 const float2 Z = zr[k2 * F::RS];
                 const float2 Zm = k == 0 ? Z : zm[(mrow2 & (N2 - 1)) * F::RS];
                 float2 r = odd ? make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x))
                                : make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
                 if (a.conj) r.y = -r.y;
-                dst[(size_t)k * kstride] = r;
+                dst[(size_t)(k - a.k0) * kstride] = r;
             }
         }
     }
@@ -479,12 +481,15 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
     const int c0 = blockIdx.x * CT;
     for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = cconj(a.tw[i]);
-    // rows no bin reaches are zero
+    // rows no bin of the slab [k0, k0 + nf) reaches are zero
+    const int kend = a.k0 + a.nf;
     for (int idx = threadIdx.x; idx < NT * P; idx += FFT_THREADS) {
         const int k = idx / P;
-        if (k >= a.nf && NT - k >= a.nf) z[F::zi(k, idx % P)] = make_float2(0.f, 0.f);
+        const bool hit = (k >= a.k0 && k < kend) || (NT - k >= a.k0 && NT - k < kend);
+        if (!hit) z[F::zi(k, idx % P)] = make_float2(0.f, 0.f);
     }
-    // Each loaded bin kk < nf of the two columns fills Z[kk] and its Hermitian mirror Z[NT - kk].
+    // Each loaded entry kk < nf (bin kb = k0 + kk) of the two columns fills Z[kb] and its
+    // Hermitian mirror Z[NT - kb].
     // When nv is a multiple of CT every column of this CTA has the same spatial index s0.
     const bool same_s = (a.nv % CT) == 0;
     const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
@@ -535,12 +540,12 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
             for (int u = 0; u < B; ++u) {
                 const int idx = b0 + threadIdx.x + u * FFT_THREADS;
                 if (idx >= items) continue;
-                const int j = idx % P, kk = idx / P;
+                const int j = idx % P, kb = idx / P + a.k0;
                 float2 Av = A[u], Bw = Bv[u];
                 if (a.conj_in) { Av.y = -Av.y; Bw.y = -Bw.y; }
-                if (kk == 0 || 2 * kk == NT) { Av.y = 0.f; Bw.y = 0.f; }
-                z[F::zi(kk, j)] = make_float2(Av.x - Bw.y, Av.y + Bw.x);
-                if (kk > 0 && 2 * kk < NT) z[F::zi(NT - kk, j)] = make_float2(Av.x + Bw.y, Bw.x - Av.y);
+                if (kb == 0 || 2 * kb == NT) { Av.y = 0.f; Bw.y = 0.f; }
+                z[F::zi(kb, j)] = make_float2(Av.x - Bw.y, Av.y + Bw.x);
+                if (kb > 0 && 2 * kb < NT) z[F::zi(NT - kb, j)] = make_float2(Av.x + Bw.y, Bw.x - Av.y);
             }
         }
     }
@@ -727,8 +732,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     const int s = c / a.nv, v = c - s * a.nv;
     float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
     const size_t kstride = (size_t)a.S * a.ldv;
-    for (int k1 = g; k1 < N1 && k1 < a.nf; k1 += G) {
-        for (int k = k1, k2 = 0; k < a.nf; k += N1, ++k2) {
+    const int kend = a.k0 + a.nf;                                  // bins [k0, kend) are written
+    for (int k1 = g; k1 < N1 && k1 < kend; k1 += G) {
+        for (int k = k1, k2 = 0; k < kend; k += N1, ++k2) {
+            if (k < a.k0) continue;
             float2 X;
             if (k >= NC) {                                     // Nyquist bin k = NC
                 const float2 Z0 = z[F::zi(0, cl)];
@@ -742,7 +749,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
                 X = cadd(E, cmul(O, a.tw[k]));
             }
             if (a.conj) X.y = -X.y;
-            dst[(size_t)k * kstride] = X;
+            dst[(size_t)(k - a.k0) * kstride] = X;
         }
     }
 }
@@ -774,8 +781,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
             if (idx < ITEMS && c < a.C) {
                 const int sp = c / a.nv, vp = c - sp * a.nv;
                 const float2* col = a.Y + (size_t)sp * a.ldv + a.voff + vp;
-                if (kk < a.nf) Al[u] = col[(size_t)kk * kstride];
-                if (NC - kk < a.nf) Bl[u] = col[(size_t)(NC - kk) * kstride];
+                if (kk >= a.k0 && kk < a.k0 + a.nf) Al[u] = col[(size_t)(kk - a.k0) * kstride];
+                if (NC - kk >= a.k0 && NC - kk < a.k0 + a.nf) Bl[u] = col[(size_t)(NC - kk - a.k0) * kstride];
             }
           }
 #pragma unroll
@@ -997,7 +1004,88 @@ void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     rfft_kernel<<<grid, FFT_THREADS, smem, s>>>(a, logCT);
 }
 
+namespace {
+
+void launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
+
+// Epilogue of a frequency shard's inverse transform, run on T = the partial transforms summed over
+// every shard (so the same signal on every shard): out = a_mdc Theta T + a_base base + a_prev out,
+// optionally written time-reversed, with per-column sums of squares -- the terms the local
+// kernels fuse into their own epilogue, which cannot be applied to a partial sum.
+__global__ void __launch_bounds__(256) shard_epilogue(IrfftArgs a, const float* __restrict__ T) {
+    if (a.active && *a.active == 0) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
+    const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
+    double ss = 0.0;
+    if (c < a.C) {
+        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        for (int t = ty; t < a.nt; t += 8) {
+            const int tau = t < (a.nt >> 1) ? t : a.nt - t;
+            const float val = tau >= cut ? 0.f : T[(size_t)t * a.C + c];
+            float r = am * val;
+            if (a.base) r += ab * a.base[(size_t)t * a.C + c];
+            const int to = a.reverse_out ? ((a.nt - t) & (a.nt - 1)) : t;
+            const size_t o = (size_t)to * a.C + c;
+            if (has_prev) r += ap * a.out[o];
+            a.out[o] = r;
+            ss += (double)r * (double)r;
+        }
+    }
+    if (a.colsum) {
+        __shared__ double red[256];
+        red[threadIdx.x] = ss;
+        __syncthreads();
+        if (ty == 0 && c < a.C) {
+            double tot = 0.0;
+            for (int i = 0; i < 8; ++i) tot += red[32 * i + tx];
+            a.colsum[c] = tot;
+        }
+    }
+}
+
+}  // namespace
+
 void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+    if (!p->red_fn) {
+        launch_irfft_local(p, a, s);
+        return;
+    }
+    const int64_t count = (int64_t)a.nt * a.C;
+    if (count > p->red_cap) {
+        float* b = nullptr;
+        const cudaError_t e = cudaMalloc(&b, (size_t)count * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_cuda_error(e);
+            if (!p->host_error) p->host_error = MDC_ERR_OOM;
+            return;
+        }
+        cudaStreamSynchronize(s);            // nothing in flight still uses the old buffer
+        cudaFree(p->red_buf);
+        p->red_buf = b;
+        p->red_cap = count;
+    }
+    IrfftArgs part = a;                      // this shard's bins only, no epilogue terms
+    part.out = p->red_buf;
+    part.a_mdc = C1(1.f);
+    part.a_base = C1(0.f);
+    part.a_prev = C1(0.f);
+    part.base = nullptr;
+    part.cut = nullptr;
+    part.reverse_out = 0;
+    part.colsum = nullptr;
+    launch_irfft_local(p, part, s);
+    const int st = p->red_fn(p->red_buf, count, (void*)s, p->red_ctx);
+    if (st != MDC_OK && !p->host_error) p->host_error = st < 0 ? st : MDC_ERR_STATE;
+    LaunchScope ls(p, s, MDC_KC_IRFFT);
+    shard_epilogue<<<(unsigned)((a.C + 31) / 32), 256, 0, s>>>(a, p->red_buf);
+}
+
+namespace {
+
+void launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     switch (a.nt) {
         case 64: irfft4_launch<8, 8>(p, a, s); return;
         case 128: irfft4_launch<16, 8>(p, a, s); return;
@@ -1015,5 +1103,7 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     LaunchScope ls(p, s, MDC_KC_IRFFT);
     irfft_kernel<<<grid, FFT_THREADS, smem, s>>>(a, logCT);
 }
+
+}  // namespace
 
 }  // namespace mdc

@@ -100,7 +100,7 @@ struct Solver {
     void rfft(mdc_plan* q, const float* x, const float* x2, const int* cutp, Coef scale, int conj, int voff,
               const int* active) {
         RfftArgs a{};
-        a.x = x; a.x2 = x2; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt; a.logn = q->logn; a.nf = q->nf;
+        a.x = x; a.x2 = x2; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt; a.logn = q->logn; a.nf = q->nf; a.k0 = q->k0;
         a.cut = cutp; a.scale = scale; a.conj = conj; a.X = q->specA; a.ldv = LD(); a.voff = voff0 + voff;
         a.tw = q->tw; a.active = active;
         launch_rfft(q, a, s);
@@ -109,7 +109,8 @@ struct Solver {
                Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active) {
         IrfftArgs a{};
         a.Y = q->specB; a.ldv = LD(); a.voff = voff0 + voff; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt;
-        a.logn = q->logn; a.nf = q->nf; a.conj_in = conj_in; a.scale = (float)(q->dt * q->dr / (double)q->nt);
+        a.logn = q->logn; a.nf = q->nf; a.k0 = q->k0; a.conj_in = conj_in;
+        a.scale = (float)(q->dt * q->dr / (double)q->nt);
         a.out = out; a.a_mdc = a_mdc; a.a_base = a_base; a.a_prev = a_prev; a.base = base; a.cut = cutp;
         a.reverse_out = reverse; a.colsum = colsum; a.tw = q->tw; a.active = active;
         launch_irfft(q, a, s);
@@ -342,6 +343,9 @@ void init_solver(Solver& S, mdc_plan* p, mdc_plan* pr, const int* cut, int nv, i
 int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, int nv, int niter, int nref,
                   int niter_ref, double tol, float* fm, float* fmp, float* gm, float* gp, double* resid_h,
                   double* final_h, int* iters_h, cudaStream_t s) {
+    // a frequency shard solves in lock step with the others only through its sum over shards
+    if ((p->shard && !p->red_fn) || (pr->shard && !pr->red_fn)) return MDC_ERR_STATE;
+    if (pr->k0 != p->k0 || pr->shard != p->shard) return MDC_ERR_ARG;
     int st = ensure_scratch(p, 2 * nv);
     if (st == MDC_OK && pr != p) st = ensure_scratch(pr, 2 * nv);
     if (st != MDC_OK) return st;
@@ -350,7 +354,7 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
     Solver* S = &local;
     GraphEntry* ge = nullptr;
     cudaStream_t caller = s;
-    if (p->graphs) {
+    if (p->graphs && !p->red_fn && !pr->red_fn) {
         // capture and replay on the handle's own stream (the legacy default stream cannot be
         // captured), ordered after and before the caller's stream with events
         if (!p->graph_stream) {
@@ -440,6 +444,9 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
     int err = 0;
     cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
     if (err) return MDC_ERR_TIMEOUT;
+    const int he = take_host_error(p), her = pr != p ? take_host_error(pr) : MDC_OK;
+    if (he != MDC_OK) return he;
+    if (her != MDC_OK) return her;
     return sch[S_STATUS] != 0.0 ? MDC_ERR_NUMERIC : MDC_OK;
 }
 
@@ -473,6 +480,7 @@ extern "C" int marchenko_neumann(mdc_handle R, const int* window, const float* f
                                  float* f_minus, float* f_mplus, float* g_minus, float* g_plus, void* stream) {
     if (!R || !window || !fd_plus || !f_minus || !f_mplus || nv < 1 || niter < 0) return MDC_ERR_ARG;
     if (R->nr != R->ns) return MDC_ERR_ARG;
+    if (R->shard && !R->red_fn) return MDC_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int st = mdc::ensure_scratch(R, 2 * nv);
     if (st != MDC_OK) return st;
@@ -491,7 +499,8 @@ extern "C" int marchenko_neumann(mdc_handle R, const int* window, const float* f
     }
     int err = 0;
     cudaMemcpy(&err, R->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    return err ? MDC_ERR_TIMEOUT : MDC_OK;
+    if (err) return MDC_ERR_TIMEOUT;
+    return mdc::take_host_error(R);
 }
 
 // ======================================================================== serving
@@ -778,6 +787,7 @@ extern "C" int srv_create(mdc_server** out, mdc_handle R, mdc_handle R_ref, int6
     if (!out) return MDC_ERR_ARG;
     *out = nullptr;
     if (!R || hbm_budget_bytes <= 0 || max_cols < 2 || R->nr != R->ns || nrefine < 0) return MDC_ERR_ARG;
+    if (R->shard || (R_ref && R_ref->shard)) return MDC_ERR_ARG;   // the server takes whole operators
     if (R_ref && ((R_ref->storage != MDC_C64 && R_ref->storage != MDC_C32S) || R_ref->nr != R->nr ||
                   R_ref->ns != R->ns || R_ref->nt != R->nt || R_ref->nf != R->nf))
         return MDC_ERR_ARG;

@@ -100,6 +100,7 @@ struct MddSolver {
     void rfft(const float* in, int S, Coef scale, const int* active) {
         RfftArgs a{};
         a.x = in; a.x2 = nullptr; a.C = S * nv; a.S = S; a.nv = nv; a.nt = p->nt; a.logn = p->logn; a.nf = p->nf;
+        a.k0 = p->k0;
         a.cut = nullptr; a.scale = scale; a.conj = 0; a.X = p->specA; a.ldv = nv; a.voff = 0; a.tw = p->tw;
         a.active = active;
         launch_rfft(p, a, s);
@@ -108,7 +109,7 @@ struct MddSolver {
     void irfft(float* out, int S, Coef a_prev, double* colsum, const int* active) {
         IrfftArgs a{};
         a.Y = p->specB; a.ldv = nv; a.voff = 0; a.C = S * nv; a.S = S; a.nv = nv; a.nt = p->nt; a.logn = p->logn;
-        a.nf = p->nf; a.conj_in = 0; a.scale = (float)(p->dt * p->dr / (double)p->nt); a.out = out;
+        a.nf = p->nf; a.k0 = p->k0; a.conj_in = 0; a.scale = (float)(p->dt * p->dr / (double)p->nt); a.out = out;
         a.a_mdc = C1(1.f); a.a_base = C1(0.f); a.a_prev = a_prev; a.base = nullptr; a.cut = nullptr;
         a.reverse_out = 0; a.colsum = colsum; a.tw = p->tw; a.active = active;
         launch_irfft(p, a, s);
@@ -168,6 +169,7 @@ extern "C" int mdd_lsqr(mdc_handle Gplus, const float* g_minus, int nv, int nite
                         double* resid, int* iters_done, void* stream) {
     if (!Gplus || !g_minus || !r || nv < 1 || niter < 1 || !std::isfinite(tol)) return MDC_ERR_ARG;
     mdc_plan* p = Gplus;
+    if (p->shard && !p->red_fn) return MDC_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int st = ensure_scratch(p, nv);
     if (st != MDC_OK) return st;
@@ -199,5 +201,7 @@ extern "C" int mdd_lsqr(mdc_handle Gplus, const float* g_minus, int nv, int nite
     int err = 0;
     cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
     if (err) return MDC_ERR_TIMEOUT;
+    const int he = take_host_error(p);
+    if (he != MDC_OK) return he;
     return sch[S_STATUS] != 0.0 ? MDC_ERR_NUMERIC : MDC_OK;
 }

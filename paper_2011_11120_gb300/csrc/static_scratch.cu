@@ -52,6 +52,7 @@ using namespace mdc;
 extern "C" int mdc_forward_static_scratch(mdc_handle h, const float* x, float* y, int nv, unsigned flags,
                                           void* stream) {
     if (!h || !x || !y || nv < 1 || (flags & ~MDC_CONJ_KERNEL)) return MDC_ERR_ARG;
+    if (h->red_fn) return MDC_ERR_STATE;       // the sum over shards would need a reduction buffer
     const size_t nspace = (size_t)(h->nr > h->ns ? h->nr : h->ns);
     if ((size_t)h->nf * nspace * (size_t)nv > kSpectrumCapacity) return MDC_ERR_BUDGET;
     float2* base = nullptr;
@@ -64,13 +65,13 @@ extern "C" int mdc_forward_static_scratch(mdc_handle h, const float* x, float* y
 
     RfftArgs ra{};
     ra.x = x; ra.x2 = nullptr; ra.C = h->ns * nv; ra.S = h->ns; ra.nv = nv;
-    ra.nt = h->nt; ra.logn = h->logn; ra.nf = h->nf; ra.cut = nullptr; ra.scale = C1(1.f);
+    ra.nt = h->nt; ra.logn = h->logn; ra.nf = h->nf; ra.k0 = h->k0; ra.cut = nullptr; ra.scale = C1(1.f);
     ra.conj = conj; ra.X = specX; ra.ldv = nv; ra.voff = 0; ra.tw = h->tw; ra.active = nullptr;
     launch_rfft(h, ra, s);
     launch_product(h, false, specX, nv, 0, specY, nv, 0, nv, s, nullptr);
     IrfftArgs ia{};
     ia.Y = specY; ia.ldv = nv; ia.voff = 0; ia.C = h->nr * nv; ia.S = h->nr; ia.nv = nv;
-    ia.nt = h->nt; ia.logn = h->logn; ia.nf = h->nf; ia.conj_in = conj;
+    ia.nt = h->nt; ia.logn = h->logn; ia.nf = h->nf; ia.k0 = h->k0; ia.conj_in = conj;
     ia.scale = (float)(h->dt * h->dr / (double)h->nt);
     ia.out = y; ia.a_mdc = C1(1.f); ia.a_base = C1(0.f); ia.a_prev = C1(0.f);
     ia.base = nullptr; ia.cut = nullptr; ia.reverse_out = 0; ia.colsum = nullptr; ia.tw = h->tw;

@@ -63,24 +63,28 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+// One bounded try: true once the phase with the given parity has completed; the thread may be
+// suspended for at most about hint_ns nanoseconds (a hint) while it is not.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete, for at most limit_ns nanoseconds.
+// Wait for the phase with the given parity to complete, for at most about limit_ns nanoseconds:
+// every try is bounded by a suspend hint no longer than the limit (1 ms at most), so the clock
+// is checked at least that often.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, unsigned long long limit_ns) {
-    if (mbar_test(bar, parity)) return true;
+    const uint32_t hint = (uint32_t)(limit_ns < 1000000ull ? limit_ns : 1000000ull);
+    if (mbar_try(bar, parity, hint)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_test(bar, parity)) return true;
+        if (mbar_try(bar, parity, hint)) return true;
         if (gtime() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             return false;

@@ -17,6 +17,7 @@ HEADER = os.path.join(ROOT, "include", "mdc.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"^\s*typedef[^;]*;", "", text, flags=re.M | re.S)      # function-pointer types
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w]*\s*\*?\s*(\w+)\s*\(", text, flags=re.M)))
 
 

@@ -62,7 +62,9 @@ def _worker(rank, world, port, q):
         nt, nf, nr, ns, nv = 64, 17, 5, 8, 3
         G = rng.standard_normal((nf, nr, ns)) + 1j * rng.standard_normal((nf, nr, ns))
         x = rng.standard_normal((nt, ns, nv))
-        ks = np.array_split(np.arange(nf), world)[rank]
+        import paper_2011_11120_gb300 as m
+        k0, nk = m.shard_bounds(nf, world, rank)        # the library's band split (host logic)
+        ks = np.arange(k0, k0 + nk)
         y = torch.from_numpy(shard_forward(G, x, 0.004, 400.0, ks))
         dist.all_reduce(y, op=dist.ReduceOp.SUM)
         full = omdc.forward(G, x, 0.004, 400.0)
@@ -87,3 +89,17 @@ def test_gloo_two_ranks():
     for rank, got, err in res:
         assert got == [2.0, 5.0]
         assert err <= 1e-13
+
+
+def test_shard_bounds_tile_the_band():
+    """The band split gives contiguous, disjoint bands covering 0 .. nf-1, sizes differing by
+    at most one, and rejects more ranks than bins."""
+    import paper_2011_11120_gb300 as m
+    for nf in (1, 2, 7, 150, 300, 513):
+        for world in range(1, min(nf, 9) + 1):
+            b = [m.shard_bounds(nf, world, r) for r in range(world)]
+            assert b[0][0] == 0 and sum(nk for _, nk in b) == nf
+            assert all(b[i][0] + b[i][1] == b[i + 1][0] for i in range(world - 1))
+            assert max(nk for _, nk in b) - min(nk for _, nk in b) <= 1
+    with pytest.raises(ValueError):
+        m.shard_bounds(3, 4, 0)
