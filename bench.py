@@ -340,7 +340,8 @@ def run_redatum(args, dev):
                         f"on a {args.redatum_storage} kernel + {nref} float32 refinement step of {nin} iterations "
                         f"({args.redatum_ref_storage} reference kernel)",
             "solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "solves_timed": len(times),
-            "p50_ms": 1e3 * med, "p99_ms": 1e3 * max(times),
+            "p50_ms": 1e3 * med, "p99_ms": 1e3 * float(np.percentile(np.asarray(times), 99)),
+            "max_ms": 1e3 * max(times),
             "iterations": out["iters"], "final_residual": out["final_residual"],
             "rel_l2_vs_fp32_solve": err,
             "device_ms_per_kernel_class": breakdown,
@@ -463,6 +464,191 @@ def run_precision(args, dev):
         out[fmt] = res
     del G
     torch.cuda.empty_cache()
+    return out
+
+
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz max SM clock
+
+
+def run_small(args, dev):
+    """The small workload (441 x 441, nt=256, nfmax=64, nv=1; complex64 kernel 99.6 MB, smaller than
+    L2): forward+adjoint pairs timed one by one (CUDA events around each pair, median of
+    ``--small-reps``), with the kernel left resident in L2 between pairs and with L2 flushed
+    (a 512 MB buffer written) before each pair, each as ordinary stream launches and as a replayed
+    CUDA graph of the pair.  At this size launch overhead is a large part of a pass."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    cfg = synth.config(1)
+    d = synth.draw(cfg)
+    op = mdc.MDC(torch.from_numpy(synth.kernel(cfg, d).astype(np.complex64)).to(dev), cfg.nt, cfg.dt, cfg.dr)
+    mdc.mdc_reserve(op.h, 1)
+    x = torch.from_numpy(synth.ricker_traces(cfg, d)).to(dev)
+    y = torch.empty((cfg.nt, cfg.nr, 1), device=dev)
+    xo = torch.empty((cfg.nt, cfg.ns, 1), device=dev)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        op.forward(x, out=y)
+        op.adjoint(y, out=xo)
+
+    for _ in range(10):
+        step()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    bytes_pair, _ = algorithmic_bytes(cfg, 1)
+    peak, _ = peaks()
+    out = {"workload": f"MDC fwd+adj, nr=ns={cfg.nr} (21x21, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
+                       f"{cfg.n_events} events, c64 kernel {cfg.nf * cfg.nr * cfg.ns * 8 / 1e6:.1f} MB, nv=1",
+           "reps": args.small_reps, "bytes_per_pair": bytes_pair}
+    stream = torch.cuda.current_stream()
+    for name, use_graph, do_flush in (("l2_resident", False, False), ("l2_flushed", False, True),
+                                      ("l2_resident_graph", True, False), ("l2_flushed_graph", True, True)):
+        evs = []
+        for i in range(args.small_reps):
+            if do_flush:
+                flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if use_graph:
+                graph.replay()
+            else:
+                step()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        med = statistics.median(us)
+        out[name] = {"median_us": med, "p10_us": us[len(us) // 10], "p90_us": us[(9 * len(us)) // 10],
+                     "gbs": bytes_pair / med / 1e3, "frac_of_measured_hbm": bytes_pair / med / 1e3 / peak}
+    n0 = mdc.mdc_launch_count(op.h)
+    step()
+    out["launches_per_pair"] = int(mdc.mdc_launch_count(op.h) - n0)
+    del graph
+    op.close()
+    return out
+
+
+def run_batched64(args, dev):
+    """The paper-scale kernel (3721 x 3721, nt=1024, nfmax=200) with nv = 64 random focusing points:
+    every product is a dense GEMM per frequency (1.42 TFLOP).  Split FP16 storage (three FP16
+    tensor-core products per GEMM, float32-level accuracy) against complex64 on the FP32 SIMT GEMM;
+    sampled rows/columns against the FP64 oracle."""
+    import torch
+    import paper_2011_11120_gb300 as mdc
+    from oracle import mdc as omdc
+    from synth import gpu as sgpu
+    nv = 64
+    cfg = synth.config(2, nv=nv)
+    d = synth.draw(cfg)
+    G = sgpu.kernel_on_device(cfg, d)
+    x_np = synth.ricker_traces(cfg, d)
+    rng = np.random.default_rng(32)
+    y_np = rng.standard_normal((cfg.nt, cfg.nr, nv)).astype(np.float32)
+    rows = np.sort(rng.choice(cfg.nr, size=8, replace=False))
+    cols = np.sort(rng.choice(cfg.ns, size=8, replace=False))
+    ref_f = omdc.forward_rows(synth.kernel(cfg, d, rows=rows), x_np, cfg.dt, cfg.dr)
+    ref_a = omdc.adjoint_cols(synth.kernel(cfg, d, cols=cols), y_np, cfg.dt, cfg.dr)
+    x, y = torch.from_numpy(x_np).to(dev), torch.from_numpy(y_np).to(dev)
+    flops = 8.0 * cfg.nf * cfg.nr * cfg.ns * nv
+    out = {"workload": f"MDC fwd+adj, nr=ns={cfg.nr} (61x61, 20 m), nt={cfg.nt}, nfmax={cfg.nf}, "
+                       f"{cfg.n_events} events, nv={nv} random focusing points; {flops / 1e12:.2f} TFLOP per product"}
+    for storage in ("c32s", "c64"):
+        op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=storage)
+        mdc.mdc_reserve(op.h, nv)
+        yo = torch.empty((cfg.nt, cfg.nr, nv), device=dev)
+        xo = torch.empty((cfg.nt, cfg.ns, nv), device=dev)
+        op.forward(x, out=yo)
+        op.adjoint(y, out=xo)
+        torch.cuda.synchronize()
+        reps = args.batched_reps if storage == "c32s" else max(2, args.batched_reps // 4)
+        mdc.mdc_timing(op.h, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            op.forward(x, out=yo)
+            op.adjoint(y, out=xo)
+        e1.record()
+        torch.cuda.synchronize()
+        kc = {c: mdc.mdc_timing_read(op.h, c) for c in ("rfft", "tc_prep", "product_fwd", "product_adj", "irfft")}
+        mdc.mdc_timing(op.h, False)
+        mdc.mdc_device_status(op.h)
+        gemm_ms = (kc["product_fwd"][0] + kc["product_adj"][0]) / max(kc["product_fwd"][1] + kc["product_adj"][1], 1)
+        pair_ms = e0.elapsed_time(e1) / reps
+        res = {"ms_per_pair": pair_ms, "tflops_per_pair": 2 * flops / pair_ms / 1e9,
+               "product_ms": gemm_ms, "tflops_product": flops / gemm_ms / 1e9,
+               "device_ms_per_kernel_class_per_pair": {c: v[0] / reps for c, v in kc.items()},
+               "tc_fallbacks": mdc.mdc_tc_fallback_count(op.h),
+               "rel_l2_forward": float(np.linalg.norm(yo.cpu().numpy()[:, rows] - ref_f) / np.linalg.norm(ref_f)),
+               "rel_l2_adjoint": float(np.linalg.norm(xo.cpu().numpy()[:, cols] - ref_a) / np.linalg.norm(ref_a))}
+        if storage == "c32s":
+            pk, kind = tc_peak(sustained=False)
+            issued = 3 * flops / gemm_ms / 1e9
+            res["roofline"] = {"bound": "tensor", "kernel": "tc_gemm_kernel (split FP16: three FP16 MMAs per product)",
+                               "achieved": issued, "peak": pk, "unit": "TFLOP/s", "frac": issued / pk,
+                               "peak_kind": kind, "note": "achieved counts the three tensor-core products issued"}
+        else:
+            res["roofline"] = {"bound": "alu", "kernel": "cgemm_simt (FP32 FMA)", "achieved": flops / gemm_ms / 1e9,
+                               "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                               "frac": flops / gemm_ms / 1e9 / FP32_ALU_TFLOPS,
+                               "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz"}
+        out[storage] = res
+        op.close()
+        torch.cuda.empty_cache()
+    del G
+    torch.cuda.empty_cache()
+    return out
+
+
+def sections_summary(result):
+    """A compact digest of every section's headline numbers, kept as the line's last key."""
+    def g(dct, *path):
+        for k in path:
+            if not isinstance(dct, dict) or k not in dct:
+                return None
+            dct = dct[k]
+        return round(dct, 4) if isinstance(dct, float) else dct
+    out = {"headline_gbs": g(result, "value"), "headline_frac": g(result, "roofline", "frac"),
+           "e2e_gbs": g(result, "e2e", "value")}
+    if "redatum" in result:
+        out["redatum"] = {"solves_per_s": g(result, "redatum", "solves_per_s"), "p50_ms": g(result, "redatum", "p50_ms"),
+                          "p99_ms": g(result, "redatum", "p99_ms"), "solves": g(result, "redatum", "solves_timed"),
+                          "rel_l2_vs_fp32": g(result, "redatum", "rel_l2_vs_fp32_solve"),
+                          "gemm_frac": g(result, "redatum", "tc_roofline", "frac"),
+                          "fp32_one_job_solves_per_s": g(result, "redatum", "fp32_one_job", "solves_per_s")}
+    if "small" in result:
+        out["small_us"] = {k: g(result, "small", k, "median_us") for k in
+                           ("l2_resident", "l2_flushed", "l2_resident_graph", "l2_flushed_graph")}
+    if "batched64" in result:
+        out["batched64"] = {k: {"tflops_product": g(result, "batched64", k, "tflops_product"),
+                                "frac": g(result, "batched64", k, "roofline", "frac"),
+                                "rel_l2_fwd": g(result, "batched64", k, "rel_l2_forward")} for k in ("c32s", "c64")}
+    if "mdd" in result:
+        out["mdd_batches_per_s"] = {k: g(result, "mdd", k, "solves_per_s") for k in ("c64", "c32s", "c16f")}
+    if "precision" in result:
+        out["precision_nv128_tflops"] = {k: g(result, "precision", k, "nv128", "tflops")
+                                         for k in ("c64", "c32s", "c16f", "cbf16", "ce4m3")}
+        out["precision_rel_l2_fwd"] = {k: g(result, "precision", k, "rel_l2_forward")
+                                       for k in ("c64", "c32s", "c16f", "cbf16", "ce4m3")}
+    if "serving" in result:
+        out["serving"] = {"capacity_solves_per_s": g(result, "serving", "offered", "solves_per_s"),
+                          "offered_p50_s": g(result, "serving", "offered", "p50_s"),
+                          "offered_p99_s": g(result, "serving", "offered", "p99_s"),
+                          "at_0.7_p50_s": g(result, "serving", "at_0.7_capacity", "p50_s"),
+                          "at_0.7_p99_s": g(result, "serving", "at_0.7_capacity", "p99_s"),
+                          "fp32_one_job_solves_per_s": g(result, "serving", "fp32_one_job_at_a_time", "solves_per_s"),
+                          "rel_l2_fp16_vs_fp32": g(result, "serving", "rel_l2_fp16_vs_fp32")}
+    if "paper_full" in result:
+        out["paper_full"] = {"c64_pair_ms": g(result, "paper_full", "c64", "ms_per_mdc_pair"),
+                             "c64_frac": g(result, "paper_full", "c64", "frac_of_measured_hbm"),
+                             "c64_marchenko_1pt_s": g(result, "paper_full", "c64", "marchenko_nv1", "s_per_solve"),
+                             "c16f_marchenko_20pt_s": g(result, "paper_full", "c16f", "marchenko_nv20", "s_per_solve")}
     return out
 
 
@@ -716,8 +902,16 @@ def run_ours(args):
         cfg = cfg.with_(nf=args.nf, normalise=False)   # profiling case: normalisation not needed
     nv = args.nv
     d = synth.draw(cfg)
-    G = sgpu.kernel_on_device(cfg, d)
-    op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.storage)
+    shard = args.shard and world > 1
+    if shard:
+        # this rank's band of frequencies; every pass ends with one NCCL all-reduce of the traces
+        k0, nk = mdc.shard_bounds(cfg.nf, world, rank)
+        G = sgpu.kernel_slab_on_device(cfg, k0, nk, d)
+        op = mdc.ShardedMDC(G, k0, cfg.nt, cfg.dt, cfg.dr, storage=args.storage)
+    else:
+        k0, nk = 0, cfg.nf
+        G = sgpu.kernel_on_device(cfg, d)
+        op = mdc.MDC(G, cfg.nt, cfg.dt, cfg.dr, storage=args.storage)
     del G
     torch.cuda.empty_cache()
     mdc.mdc_reserve(op.h, nv)
@@ -791,11 +985,14 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    value = world * bytes_step * args.steps / (ms / 1e3) / 1e9
-    e2e_value = world * bytes_step * args.steps / (ms_e2e / 1e3) / 1e9
+    # replicas: every rank runs the whole operator; shards: the ranks together run one operator
+    copies = 1 if shard else world
+    value = copies * bytes_step * args.steps / (ms / 1e3) / 1e9
+    e2e_value = copies * bytes_step * args.steps / (ms_e2e / 1e3) / 1e9
     peak, peak_kind = peaks()
     prod_ms = kern["product_fwd"]["ms_total"] + kern["product_adj"]["ms_total"]
     prod_n = kern["product_fwd"]["launches"] + kern["product_adj"]["launches"]
+    kernel_bytes = kernel_bytes * nk // cfg.nf         # this rank's band (the whole kernel unless sharded)
     achieved = kernel_bytes * prod_n / (prod_ms / 1e3) / 1e9 if prod_ms > 0 else None
     # the committed DRAM capture covers the complex64 GEMV pair of the default workload only
     profiled = args.config == 2 and not args.nf and nv == 1 and args.storage == "c64"
@@ -803,8 +1000,10 @@ def run_ours(args):
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(config_block(cfg, nv, args.storage), parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(config_block(cfg, nv, args.storage),
+                       parallelism=(f"frequency shards x{world} (one NCCL all-reduce per pass)" if shard
+                                    else f"replicas x{world}" if world > 1 else "single GPU")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "kernel": f"per-frequency product (forward + adjoint, {args.storage}, {nv} column(s))",
@@ -816,6 +1015,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if world == 1 and not args.no_small:
+        result["small"] = run_small(args, dev)
+    if world == 1 and not args.no_batched64:
+        result["batched64"] = run_batched64(args, dev)
     if world == 1 and not args.no_redatum:
         result["redatum"] = run_redatum(args, dev)
     if world == 1 and not args.no_mdd:
@@ -829,6 +1032,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cfg, nv, min_seconds=args.cpu_seconds)
         result["cpu_baseline"]["paper_style"] = paper_style_cpu(cfg, nv)
+    result["sections_summary"] = sections_summary(result)
     print(json.dumps(result), flush=True)
     if args.metrics_jsonl:
         with open(args.metrics_jsonl, "a") as fh:
@@ -854,13 +1058,20 @@ def main():
     ap.add_argument("--no-mdd", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-paper-full", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-batched64", action="store_true")
+    ap.add_argument("--small-reps", type=int, default=200)
+    ap.add_argument("--batched-reps", type=int, default=8)
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1 GPUs: split the kernel's frequencies over the ranks (one all-reduce per "
+                         "pass, strong scaling) instead of running N replicas")
     ap.add_argument("--metrics-jsonl", default="", help="also append the result line to this file")
     ap.add_argument("--mdd-iters", type=int, default=10)
     ap.add_argument("--serving-config", type=int, default=5)
     ap.add_argument("--serving-rate", type=float, default=50.0)
     ap.add_argument("--serving-horizon", type=float, default=20.0)
     ap.add_argument("--serving-pool", type=int, default=2)
-    ap.add_argument("--redatum-solves", type=int, default=3)
+    ap.add_argument("--redatum-solves", type=int, default=10)
     ap.add_argument("--redatum-storage", default="c16f", choices=["c16f", "cbf16"])
     ap.add_argument("--redatum-refine-iters", type=int, default=5)
     ap.add_argument("--redatum-ref-storage", default="c32s", choices=["c64", "c32s"])
