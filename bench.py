@@ -613,7 +613,7 @@ def sections_summary(result):
             if not isinstance(dct, dict) or k not in dct:
                 return None
             dct = dct[k]
-        return round(dct, 4) if isinstance(dct, float) else dct
+        return float(f"{dct:.4g}") if isinstance(dct, float) else dct
     out = {"headline_gbs": g(result, "value"), "headline_frac": g(result, "roofline", "frac"),
            "e2e_gbs": g(result, "e2e", "value")}
     if "redatum" in result:
