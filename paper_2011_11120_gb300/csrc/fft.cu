@@ -343,7 +343,9 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
 template <int N1, int N2>
 __device__ __forceinline__ int out_row(int q) { return (q % N1) * N2 + q / N1; }
 
-template <int N1, int N2>
+// WIN: the window Theta multiplies the input; X2: a second input is added.  The input scale is
+// applied to the separated spectrum (the transform is linear), together with its factor 1/2.
+template <int N1, int N2, bool WIN, bool X2>
 __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     using F = FourStep<N1, N2>;
     constexpr int NT = F::NT, CT = F::CT;
@@ -357,15 +359,13 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         tw[i] = w;
         tw[i + NT / 2] = make_float2(-w.x, -w.y);
     }
-    const float sc = coef(a.scale);
     // Load the [NT][CT] tile with many independent loads in flight per thread.
     auto put = [&](int t, int cl, float v) {
-        const int c = c0 + cl;
-        if (a.cut) {
+        if constexpr (WIN) {
             const int tau = t < (NT >> 1) ? t : NT - t;
-            if (tau >= a.cut[c]) v = 0.f;
+            if (tau >= a.cut[c0 + cl]) v = 0.f;
         }
-        reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v * sc;
+        reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v;
     };
     if (a.vec4 && c0 + CT <= a.C) {
         // First pass straight from global memory: task (j, n2) loads the column pair
@@ -374,29 +374,31 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         // writes the tile; only the second pass goes through shared memory.
         __syncthreads();                                  // twiddle table
         constexpr int P = F::P;
+        const size_t rstride = (size_t)N2 * a.C;          // floats between the rows n1 and n1 + 1
         for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
             const int j = task % P, n2 = task / P, c = c0 + 2 * j;
-            const int cut0 = a.cut ? a.cut[c] : 0x7fffffff, cut1 = a.cut ? a.cut[c + 1] : 0x7fffffff;
-            const float* xb = a.x + c;
+            const float* xb = a.x + c + (size_t)n2 * a.C;
             float2 r[N1];
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1)
-                r[n1] = *reinterpret_cast<const float2*>(xb + (size_t)(n1 * N2 + n2) * a.C);
-            if (a.x2) {
-                const float* x2b = a.x2 + c;
+            for (int n1 = 0; n1 < N1; ++n1) r[n1] = *reinterpret_cast<const float2*>(xb + n1 * rstride);
+            if constexpr (X2) {
+                const float* x2b = a.x2 + c + (size_t)n2 * a.C;
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
-                    const float2 w = *reinterpret_cast<const float2*>(x2b + (size_t)(n1 * N2 + n2) * a.C);
+                    const float2 w = *reinterpret_cast<const float2*>(x2b + n1 * rstride);
                     r[n1].x += w.x;
                     r[n1].y += w.y;
                 }
             }
+            if constexpr (WIN) {
+                const int cut0 = a.cut[c], cut1 = a.cut[c + 1];
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const int t = n1 * N2 + n2;
-                const int tau = t < (NT >> 1) ? t : NT - t;
-                r[n1].x = tau >= cut0 ? 0.f : r[n1].x * sc;
-                r[n1].y = tau >= cut1 ? 0.f : r[n1].y * sc;
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    const int t = n1 * N2 + n2;
+                    const int tau = t < (NT >> 1) ? t : NT - t;
+                    if (tau >= cut0) r[n1].x = 0.f;
+                    if (tau >= cut1) r[n1].y = 0.f;
+                }
             }
             reg_fft<N1, false>(r);
 #pragma unroll
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 if (c < a.C) {
                     const size_t off = (size_t)t * a.C + c;
                     v[u] = a.x[off];
-                    if (a.x2) v[u] += a.x2[off];
+                    if constexpr (X2) v[u] += a.x2[off];
                 }
             }
 #pragma unroll
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         __syncthreads();
         four_step<N1, N2, false, true>(z, tw);
     }
+    const float hs = 0.5f * coef(a.scale);
     // Bin k = k1 + N1 * k2 sits in row k1 * N2 + k2, its mirror NT - k in row
     // ((-k1) mod N1) * N2 + (NT/N1 - k2 - [k1 > 0]) (k > 0).  A thread keeps one column and walks
     // the bins of every G-th block k1; the G threads of a column cover all N1 blocks, and the
@@ -461,8 +464,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 if (k < a.k0) continue;
                 const float2 Z = zr[k2 * F::RS];
                 const float2 Zm = k == 0 ? Z : zm[(mrow2 & (N2 - 1)) * F::RS];
-                float2 r = odd ? make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x))
-                               : make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+                float2 r = odd ? make_float2(hs * (Z.y + Zm.y), hs * (Zm.x - Z.x))
+                               : make_float2(hs * (Z.x + Zm.x), hs * (Z.y - Zm.y));
                 if (a.conj) r.y = -r.y;
                 dst[(size_t)(k - a.k0) * kstride] = r;
             }
@@ -470,7 +473,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     }
 }
 
-template <int N1, int N2>
+// PLAIN: the output is the transform alone (no window, base or previous-output terms, column sums
+// or time reversal, a_mdc = 1).  The inverse scale multiplies the spectrum as it is loaded.
+template <int N1, int N2, bool PLAIN>
 __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     using F = FourStep<N1, N2>;
     constexpr int NT = F::NT, CT = F::CT, P = F::P;
@@ -481,13 +486,14 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
     const int c0 = blockIdx.x * CT;
     for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = cconj(a.tw[i]);
-    // rows no bin of the slab [k0, k0 + nf) reaches are zero
+    // rows no bin of the slab [k0, k0 + nf) reaches are zero (16-byte stores, P is even)
     const int kend = a.k0 + a.nf;
-    for (int idx = threadIdx.x; idx < NT * P; idx += FFT_THREADS) {
-        const int k = idx / P;
+    for (int idx = threadIdx.x; idx < NT * (P / 2); idx += FFT_THREADS) {
+        const int k = idx / (P / 2);
         const bool hit = (k >= a.k0 && k < kend) || (NT - k >= a.k0 && NT - k < kend);
-        if (!hit) z[F::zi(k, idx % P)] = make_float2(0.f, 0.f);
+        if (!hit) *reinterpret_cast<float4*>(z + F::zi(k, 2 * (idx % (P / 2)))) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const float isc = a.scale;
     // Each loaded entry kk < nf (bin kb = k0 + kk) of the two columns fills Z[kb] and its
     // Hermitian mirror Z[NT - kb].
     // When nv is a multiple of CT every column of this CTA has the same spatial index s0.
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                 const int idx = b0 + threadIdx.x + u * FFT_THREADS;
                 if (idx >= items) continue;
                 const int j = idx % P, kb = idx / P + a.k0;
-                float2 Av = A[u], Bw = Bv[u];
+                float2 Av = make_float2(isc * A[u].x, isc * A[u].y), Bw = make_float2(isc * Bv[u].x, isc * Bv[u].y);
                 if (a.conj_in) { Av.y = -Av.y; Bw.y = -Bw.y; }
                 if (kb == 0 || 2 * kb == NT) { Av.y = 0.f; Bw.y = 0.f; }
                 z[F::zi(kb, j)] = make_float2(Av.x - Bw.y, Av.y + Bw.x);
@@ -552,6 +558,31 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     __syncthreads();
     four_step<N1, N2, true>(z, tw);
 
+    if constexpr (PLAIN) {
+        // storage row rho holds time sample t = (rho % N2) * N1 + rho / N2
+        if (a.vec4) {
+            constexpr int Q = CT / 4, TS = FFT_THREADS / Q;
+            const int q = threadIdx.x % Q, cq = c0 + 4 * q;
+            if (cq < a.C) {
+#pragma unroll 4
+                for (int rho = threadIdx.x / Q; rho < NT; rho += TS) {
+                    const int t = (rho % N2) * N1 + rho / N2;
+                    *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) =
+                        *reinterpret_cast<const float4*>(z + F::zi(rho, 2 * q));
+                }
+            }
+        } else {
+            const int cl = threadIdx.x % CT, c = c0 + cl;
+            if (c < a.C) {
+                for (int rho = threadIdx.x / CT; rho < NT; rho += FFT_THREADS / CT) {
+                    const int t = (rho % N2) * N1 + rho / N2;
+                    const float2 zz = z[F::zi(rho, cl >> 1)];
+                    a.out[(size_t)t * a.C + c] = (cl & 1) ? zz.y : zz.x;
+                }
+            }
+        }
+        return;
+    }
     const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
     if (a.vec4) {
@@ -587,7 +618,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                     const float pp[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        float val = tau >= cut[i] ? 0.f : v[i] * a.scale;
+                        float val = tau >= cut[i] ? 0.f : v[i];          // scale applied at load
                         v[i] = am * val + ab * bb[i] + ap * pp[i];
                         if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                     }
@@ -632,7 +663,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                 const int rho = t0 + (b0 + u) * TS;
                 const int t = (rho % N2) * N1 + rho / N2;
                 const float2 zz = z[F::zi(rho, cl >> 1)];
-                float val = ((cl & 1) ? zz.y : zz.x) * a.scale;
+                float val = (cl & 1) ? zz.y : zz.x;                      // scale applied at load
                 const int tau = t < (NT >> 1) ? t : NT - t;
                 if (tau >= cut) val = 0.f;
                 const float r = am * val + ab * bv[u] + ap * pv[u];
@@ -949,27 +980,50 @@ void irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     irfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
 }
 
+template <int N1, int N2, bool WIN, bool X2>
+void rfft4_go(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+    using F = FourStep<N1, N2>;
+    static SmemLimit attr;
+    attr.ensure(rfft4_kernel<N1, N2, WIN, X2>, (int)F::smem_full);
+    LaunchScope ls(p, s, MDC_KC_RFFT);
+    rfft4_kernel<N1, N2, WIN, X2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
+}
+
 template <int N1, int N2>
 void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
-    using F = FourStep<N1, N2>;
     RfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && ((uintptr_t)a.x % 16 == 0) && (!a.x2 || (uintptr_t)a.x2 % 16 == 0);
+    if (a.cut) {
+        if (a.x2) rfft4_go<N1, N2, true, true>(p, a, s);
+        else rfft4_go<N1, N2, true, false>(p, a, s);
+    } else {
+        if (a.x2) rfft4_go<N1, N2, false, true>(p, a, s);
+        else rfft4_go<N1, N2, false, false>(p, a, s);
+    }
+}
+
+template <int N1, int N2, bool PLAIN>
+void irfft4_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+    using F = FourStep<N1, N2>;
     static SmemLimit attr;
-    attr.ensure(rfft4_kernel<N1, N2>, (int)F::smem_full);
-    LaunchScope ls(p, s, MDC_KC_RFFT);
-    rfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
+    attr.ensure(irfft4_kernel<N1, N2, PLAIN>, (int)F::smem);
+    LaunchScope ls(p, s, MDC_KC_IRFFT);
+    irfft4_kernel<N1, N2, PLAIN><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+}
+
+// The transform alone: no window, base or previous-output terms, column sums or reversal.
+inline bool irfft_plain(const IrfftArgs& a) {
+    return !a.cut && !a.base && !a.colsum && !a.reverse_out && a.a_mdc.h == 1.f && !a.a_mdc.d &&
+           a.a_prev.h == 0.f && !a.a_prev.d;
 }
 
 template <int N1, int N2>
 void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
-    using F = FourStep<N1, N2>;
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
-    static SmemLimit attr;
-    attr.ensure(irfft4_kernel<N1, N2>, (int)F::smem);
-    LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft4_kernel<N1, N2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+    if (irfft_plain(a)) irfft4_go<N1, N2, true>(p, a, s);
+    else irfft4_go<N1, N2, false>(p, a, s);
 }
 
 int tile_log_columns(int nt) {
