@@ -277,10 +277,12 @@ __device__ __forceinline__ void reg_fft(float2 (&a)[R]) {
     for (int i = 0; i < R; ++i) a[i] = b[i];
 }
 
-template <int N1, int N2> struct FourStep {
+// PP: complex sequences per CTA, or 0 for the default of about 8192 complex values per tile (the
+// few-column variant PP = max(1024 / NT, 2) spreads small batches over more CTAs).
+template <int N1, int N2, int PP = 0> struct FourStep {
     static constexpr int NT = N1 * N2;
     static constexpr int P0 = 8192 / NT;
-    static constexpr int P = P0 > 32 ? 32 : (P0 < 8 ? 8 : P0);     // complex sequences per CTA
+    static constexpr int P = PP ? PP : (P0 > 32 ? 32 : (P0 < 8 ? 8 : P0));   // complex sequences per CTA
     static constexpr int CT = 2 * P;                                  // real columns per CTA
     // Rows of P complex values, unpadded, plus BP slots after every block of N2 rows: with P = 8
     // two consecutive rows (or blocks, in pass B) then fill all 16 bank pairs, and rows stay
@@ -301,9 +303,9 @@ __device__ __forceinline__ float2 tw_full(const float2* tw, int m, int nt) {
 
 // Second pass of the four-step transform: the length-N2 DFTs over n2 of every block k1, in
 // place; ends with a barrier.
-template <int N1, int N2, bool INV>
+template <int N1, int N2, bool INV, int PP = 0>
 __device__ __forceinline__ void four_step_pass_b(float2* z) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     constexpr int P = F::P;
     for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
         const int j = task % P, k1 = task / P;
@@ -319,9 +321,9 @@ __device__ __forceinline__ void four_step_pass_b(float2* z) {
 
 // tw: the twiddle table W_NT^m of the transform's sign (conjugated for INV), m < NT/2, or with
 // FULL the whole period m < NT (no sign select per twiddle).
-template <int N1, int N2, bool INV, bool FULL = false>
+template <int N1, int N2, bool INV, bool FULL = false, int PP = 0>
 __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     constexpr int P = F::P;
     for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
         const int j = task % P, n2 = task / P;
@@ -336,7 +338,7 @@ __device__ __forceinline__ void four_step(float2* z, const float2* tw) {
         }
     }
     __syncthreads();
-    four_step_pass_b<N1, N2, INV>(z);
+    four_step_pass_b<N1, N2, INV, PP>(z);
 }
 
 // Row holding bin (or time sample) q after four_step.
@@ -345,9 +347,9 @@ __device__ __forceinline__ int out_row(int q) { return (q % N1) * N2 + q / N1; }
 
 // WIN: the window Theta multiplies the input; X2: a second input is added.  The input scale is
 // applied to the separated spectrum (the transform is linear), together with its factor 1/2.
-template <int N1, int N2, bool WIN, bool X2>
+template <int N1, int N2, bool WIN, bool X2, int PP>
 __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     constexpr int NT = F::NT, CT = F::CT;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 sm2[];
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 z[F::zi(k1 * N2 + n2, j)] = k1 == 0 ? r[0] : cmul(r[k1], tw[n2 * k1]);
         }
         __syncthreads();
-        four_step_pass_b<N1, N2, false>(z);
+        four_step_pass_b<N1, N2, false, PP>(z);
     } else {
         constexpr int PER = NT * CT / FFT_THREADS, B = PER < 16 ? PER : 16;
 #pragma unroll 1
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
             }
         }
         __syncthreads();
-        four_step<N1, N2, false, true>(z, tw);
+        four_step<N1, N2, false, true, PP>(z, tw);
     }
     const float hs = 0.5f * coef(a.scale);
     // Bin k = k1 + N1 * k2 sits in row k1 * N2 + k2, its mirror NT - k in row
@@ -475,9 +477,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
 
 // PLAIN: the output is the transform alone (no window, base or previous-output terms, column sums
 // or time reversal, a_mdc = 1).  The inverse scale multiplies the spectrum as it is loaded.
-template <int N1, int N2, bool PLAIN>
+template <int N1, int N2, bool PLAIN, int PP>
 __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     constexpr int NT = F::NT, CT = F::CT, P = F::P;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 sm2[];
@@ -495,58 +497,49 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     }
     const float isc = a.scale;
     // Each loaded entry kk < nf (bin kb = k0 + kk) of the two columns fills Z[kb] and its
-    // Hermitian mirror Z[NT - kb].
-    // When nv is a multiple of CT every column of this CTA has the same spatial index s0.
-    const bool same_s = (a.nv % CT) == 0;
-    const int s0 = c0 / a.nv, v0 = c0 - s0 * a.nv;
+    // Hermitian mirror Z[NT - kb].  Every thread keeps one column pair j (FFT_THREADS is a
+    // multiple of P), so its two spectrum columns are located once.
     {
-        const int items = a.nf * P;
-        constexpr int B = 4;
+        const int j = threadIdx.x % P, ca = c0 + 2 * j;
+        const size_t kstride = (size_t)a.S * a.ldv;
+        const float2* pa = nullptr;
+        const float2* pb = nullptr;
+        if (ca < a.C) {
+            const int sa = ca / a.nv, va = ca - sa * a.nv;
+            pa = a.Y + (size_t)sa * a.ldv + a.voff + va;
+            if (ca + 1 < a.C) {
+                const int sb = (ca + 1) / a.nv, vb = ca + 1 - sb * a.nv;
+                pb = a.Y + (size_t)sb * a.ldv + a.voff + vb;
+            }
+        }
+        // both columns as one 16-byte load when they are adjacent and every row keeps the alignment
+        const bool pair16 = pb == pa + 1 && ((uintptr_t)pa & 15) == 0 && (kstride & 1) == 0;
+        constexpr int B = 4, STEP = FFT_THREADS / P;
 #pragma unroll 1
-        for (int b0 = 0; b0 < items; b0 += B * FFT_THREADS) {
+        for (int kk0 = threadIdx.x / P; kk0 < a.nf; kk0 += B * STEP) {
             float2 A[B], Bv[B];
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+                const int kk = kk0 + u * STEP;
                 A[u] = make_float2(0.f, 0.f);
                 Bv[u] = A[u];
-                if (idx < items) {
-                    const int j = idx % P, kk = idx / P, ca = c0 + 2 * j;
-                    if (same_s && ca + 1 < a.C) {
-                        const size_t ia = ((size_t)kk * a.S + s0) * a.ldv + a.voff + v0 + 2 * j;
-                        if ((ia & 1) == 0) {
-                            const float4 q = *reinterpret_cast<const float4*>(a.Y + ia);
-                            A[u] = make_float2(q.x, q.y);
-                            Bv[u] = make_float2(q.z, q.w);
-                        } else {
-                            A[u] = a.Y[ia];
-                            Bv[u] = a.Y[ia + 1];
-                        }
-                    } else if (ca < a.C) {
-                        const int sa = ca / a.nv, va = ca - sa * a.nv;
-                        const size_t ia = ((size_t)kk * a.S + sa) * a.ldv + a.voff + va;
-                        if (ca + 1 < a.C) {
-                            const int sb = (ca + 1) / a.nv, vb = ca + 1 - sb * a.nv;
-                            const size_t ib = ((size_t)kk * a.S + sb) * a.ldv + a.voff + vb;
-                            if (ib == ia + 1 && (ia & 1) == 0) {
-                                const float4 q = *reinterpret_cast<const float4*>(a.Y + ia);
-                                A[u] = make_float2(q.x, q.y);
-                                Bv[u] = make_float2(q.z, q.w);
-                            } else {
-                                A[u] = a.Y[ia];
-                                Bv[u] = a.Y[ib];
-                            }
-                        } else {
-                            A[u] = a.Y[ia];
-                        }
+                if (kk < a.nf && pa) {
+                    const size_t o = (size_t)kk * kstride;
+                    if (pair16) {
+                        const float4 q = *reinterpret_cast<const float4*>(pa + o);
+                        A[u] = make_float2(q.x, q.y);
+                        Bv[u] = make_float2(q.z, q.w);
+                    } else {
+                        A[u] = pa[o];
+                        if (pb) Bv[u] = pb[o];
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                const int idx = b0 + threadIdx.x + u * FFT_THREADS;
-                if (idx >= items) continue;
-                const int j = idx % P, kb = idx / P + a.k0;
+                const int kk = kk0 + u * STEP;
+                if (kk >= a.nf) continue;
+                const int kb = kk + a.k0;
                 float2 Av = make_float2(isc * A[u].x, isc * A[u].y), Bw = make_float2(isc * Bv[u].x, isc * Bv[u].y);
                 if (a.conj_in) { Av.y = -Av.y; Bw.y = -Bw.y; }
                 if (kb == 0 || 2 * kb == NT) { Av.y = 0.f; Bw.y = 0.f; }
@@ -556,7 +549,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
         }
     }
     __syncthreads();
-    four_step<N1, N2, true>(z, tw);
+    four_step<N1, N2, true, false, PP>(z, tw);
 
     if constexpr (PLAIN) {
         // storage row rho holds time sample t = (rho % N2) * N1 + rho / N2
@@ -706,7 +699,7 @@ struct HalfStep {
     static constexpr size_t smem = (size_t)F::ZSIZE * sizeof(float2);
 };
 
-template <int N1, int N2>
+template <int N1, int N2, bool WIN, bool X2>
 __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     using H = HalfStep<N1, N2>;
     using F = typename H::F;
@@ -715,35 +708,34 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     extern __shared__ __align__(16) float2 z[];
     const float2* __restrict__ twc = a.tw + NC;       // W_NC^m, m < NC
     const int c0 = blockIdx.x * P;
-    const float sc = coef(a.scale);
     // Pass A straight from global memory: task (j, n2) reads samples 2n and 2n + 1 of column
-    // c0 + j for n = n1 * N2 + n2, applies window and scale, and transforms over n1.
+    // c0 + j for n = n1 * N2 + n2, applies the window, and transforms over n1 (the input scale
+    // multiplies the split spectrum).
     for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
         const int j = task % P, n2 = task / P, c = c0 + j;
         float2 r[N1];
         if (c < a.C) {
-            const int cut = a.cut ? a.cut[c] : 0x7fffffff;
-            const float* xb = a.x + c;
-            const float* x2b = a.x2 ? a.x2 + c : nullptr;
+            const size_t rstride = (size_t)2 * N2 * a.C;       // floats between n1 and n1 + 1
+            const float* xb = a.x + c + (size_t)2 * n2 * a.C;
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const int t = 2 * (n1 * N2 + n2);
-                r[n1] = make_float2(xb[(size_t)t * a.C], xb[(size_t)(t + 1) * a.C]);
+            for (int n1 = 0; n1 < N1; ++n1) r[n1] = make_float2(xb[n1 * rstride], xb[n1 * rstride + a.C]);
+            if constexpr (X2) {
+                const float* x2b = a.x2 + c + (size_t)2 * n2 * a.C;
+#pragma unroll
+                for (int n1 = 0; n1 < N1; ++n1) {
+                    r[n1].x += x2b[n1 * rstride];
+                    r[n1].y += x2b[n1 * rstride + a.C];
+                }
             }
-            if (x2b) {
+            if constexpr (WIN) {
+                const int cut = a.cut[c];
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
                     const int t = 2 * (n1 * N2 + n2);
-                    r[n1].x += x2b[(size_t)t * a.C];
-                    r[n1].y += x2b[(size_t)(t + 1) * a.C];
+                    const int tau0 = t < NC ? t : NT - t, tau1 = t + 1 < NC ? t + 1 : NT - t - 1;
+                    if (tau0 >= cut) r[n1].x = 0.f;
+                    if (tau1 >= cut) r[n1].y = 0.f;
                 }
-            }
-#pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const int t = 2 * (n1 * N2 + n2);
-                const int tau0 = t < NC ? t : NT - t, tau1 = t + 1 < NC ? t + 1 : NT - t - 1;
-                r[n1].x = tau0 >= cut ? 0.f : r[n1].x * sc;
-                r[n1].y = tau1 >= cut ? 0.f : r[n1].y * sc;
             }
         } else {
 #pragma unroll
@@ -763,6 +755,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     const int s = c / a.nv, v = c - s * a.nv;
     float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
     const size_t kstride = (size_t)a.S * a.ldv;
+    const float sc = coef(a.scale), hs = 0.5f * sc;
     const int kend = a.k0 + a.nf;                                  // bins [k0, kend) are written
     for (int k1 = g; k1 < N1 && k1 < kend; k1 += G) {
         for (int k = k1, k2 = 0; k < kend; k += N1, ++k2) {
@@ -770,13 +763,13 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
             float2 X;
             if (k >= NC) {                                     // Nyquist bin k = NC
                 const float2 Z0 = z[F::zi(0, cl)];
-                X = make_float2(Z0.x - Z0.y, 0.f);
+                X = make_float2(sc * (Z0.x - Z0.y), 0.f);
             } else {
                 const float2 Z = z[F::zi(k1 * N2 + k2, cl)];
                 const int km = (NC - k) & (NC - 1);
                 const float2 Zm = z[F::zi((km % N1) * N2 + km / N1, cl)];
-                const float2 E = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
-                const float2 O = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
+                const float2 E = make_float2(hs * (Z.x + Zm.x), hs * (Z.y - Zm.y));
+                const float2 O = make_float2(hs * (Z.y + Zm.y), hs * (Zm.x - Z.x));
                 X = cadd(E, cmul(O, a.tw[k]));
             }
             if (a.conj) X.y = -X.y;
@@ -785,8 +778,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     }
 }
 
-template <int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a) {
+template <int N1, int N2, bool PLAIN>
+__global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(IrfftArgs a) {
     using H = HalfStep<N1, N2>;
     using F = typename H::F;
     constexpr int NC = H::NC, NT = H::NT, P = H::P;
@@ -796,32 +789,36 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
     const float2* __restrict__ twc = a.tw + 2 * NC;   // conj W_NC^m, m < NC
     const int c0 = blockIdx.x * P;
     // Item (kk, j), kk <= NC / 2, reads X[kk] and X[NC - kk] of column c0 + j and writes Z[kk]
-    // and Z[NC - kk]; bins >= nf are zero, DC and Nyquist lose their imaginary parts.
+    // and Z[NC - kk]; bins outside the band are zero, DC and Nyquist lose their imaginary parts.
+    // Every thread keeps one column j (FFT_THREADS is a multiple of P).
     {
-        constexpr int ITEMS = (NC / 2 + 1) * P, BL = 4;
+        constexpr int KK = NC / 2 + 1, BL = 4, STEP = FFT_THREADS / P;
         const size_t kstride = (size_t)a.S * a.ldv;
+        const int j = threadIdx.x % P, c = c0 + j, kend = a.k0 + a.nf;
+        const float2* col = nullptr;
+        if (c < a.C) {
+            const int sp = c / a.nv, vp = c - sp * a.nv;
+            col = a.Y + (size_t)sp * a.ldv + a.voff + vp;
+        }
 #pragma unroll 1
-        for (int b0 = 0; b0 < ITEMS; b0 += BL * FFT_THREADS) {
+        for (int kk0 = threadIdx.x / P; kk0 < KK; kk0 += BL * STEP) {
           float2 Al[BL], Bl[BL];
 #pragma unroll
           for (int u = 0; u < BL; ++u) {                 // loads first, BL items in flight
-            const int idx = b0 + threadIdx.x + u * FFT_THREADS;
+            const int kk = kk0 + u * STEP;
             Al[u] = make_float2(0.f, 0.f);
             Bl[u] = Al[u];
-            const int j = idx % P, kk = idx / P, c = c0 + j;
-            if (idx < ITEMS && c < a.C) {
-                const int sp = c / a.nv, vp = c - sp * a.nv;
-                const float2* col = a.Y + (size_t)sp * a.ldv + a.voff + vp;
-                if (kk >= a.k0 && kk < a.k0 + a.nf) Al[u] = col[(size_t)(kk - a.k0) * kstride];
-                if (NC - kk >= a.k0 && NC - kk < a.k0 + a.nf) Bl[u] = col[(size_t)(NC - kk - a.k0) * kstride];
+            if (kk < KK && col) {
+                if (kk >= a.k0 && kk < kend) Al[u] = col[(size_t)(kk - a.k0) * kstride];
+                if (NC - kk >= a.k0 && NC - kk < kend) Bl[u] = col[(size_t)(NC - kk - a.k0) * kstride];
             }
           }
 #pragma unroll
           for (int u = 0; u < BL; ++u) {
-            const int idx = b0 + threadIdx.x + u * FFT_THREADS;
-            if (idx >= ITEMS) continue;
-            const int j = idx % P, kk = idx / P;
-            float2 A = Al[u], B = Bl[u];
+            const int kk = kk0 + u * STEP;
+            if (kk >= KK) continue;
+            float2 A = make_float2(a.scale * Al[u].x, a.scale * Al[u].y);      // inverse scale at load
+            float2 B = make_float2(a.scale * Bl[u].x, a.scale * Bl[u].y);
             if (a.conj_in) { A.y = -A.y; B.y = -B.y; }
             if (kk == 0) { A.y = 0.f; B.y = 0.f; }
             // E = A + conj B, O = (A - conj B) W_nt^-kk; the mirror NC - kk has E' = conj E and
@@ -843,6 +840,35 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
 
     // Row rho holds complex sample n = (rho % N2) * N1 + rho / N2, i.e. real samples 2n (real
     // part) and 2n + 1 (imaginary part).
+    if constexpr (PLAIN) {
+        if (a.vec4) {
+            constexpr int Q = P / 4, TSQ = FFT_THREADS / Q;
+            const int q = threadIdx.x % Q, cq = c0 + 4 * q;
+            if (cq < a.C) {
+#pragma unroll 4
+                for (int rho = threadIdx.x / Q; rho < NC; rho += TSQ) {
+                    const int n = (rho % N2) * N1 + rho / N2;
+                    const float4 z01 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q));
+                    const float4 z23 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q + 2));
+                    *reinterpret_cast<float4*>(a.out + (size_t)(2 * n) * a.C + cq) =
+                        make_float4(z01.x, z01.z, z23.x, z23.z);
+                    *reinterpret_cast<float4*>(a.out + (size_t)(2 * n + 1) * a.C + cq) =
+                        make_float4(z01.y, z01.w, z23.y, z23.w);
+                }
+            }
+        } else {
+            const int cl = threadIdx.x % P, c = c0 + cl;
+            if (c < a.C) {
+                for (int rho = threadIdx.x / P; rho < NC; rho += FFT_THREADS / P) {
+                    const int n = (rho % N2) * N1 + rho / N2;
+                    const float2 zz = z[F::zi(rho, cl)];
+                    a.out[(size_t)(2 * n) * a.C + c] = zz.x;
+                    a.out[(size_t)(2 * n + 1) * a.C + c] = zz.y;
+                }
+            }
+        }
+        return;
+    }
     const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
     const bool want_ss = a.colsum != nullptr;
@@ -885,7 +911,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
                         float v[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const float val = tau >= cut[i] ? 0.f : (h ? im[i] : re[i]) * a.scale;
+                            const float val = tau >= cut[i] ? 0.f : (h ? im[i] : re[i]);
                             v[i] = am * val + ab * bb[i] + ap * pp[i];
                             if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                         }
@@ -937,7 +963,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
                 for (int h = 0; h < 2; ++h) {
                     const int t = 2 * n + h;
                     const int tau = t < NC ? t : NT - t;
-                    float val = (h ? zz.y : zz.x) * a.scale;
+                    float val = h ? zz.y : zz.x;
                     if (tau >= cut) val = 0.f;
                     const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                     const float r = am * val + ab * bv[u][h] + ap * pv[u][h];
@@ -959,62 +985,89 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) irfft_half_kernel(IrfftArgs a)
     }
 }
 
-template <int N1, int N2>
-void rfft_half_launch(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+// The transform alone: no window, base or previous-output terms, column sums or reversal.
+inline bool irfft_plain(const IrfftArgs& a) {
+    return !a.cut && !a.base && !a.colsum && !a.reverse_out && a.a_mdc.h == 1.f && !a.a_mdc.d &&
+           a.a_prev.h == 0.f && !a.a_prev.d;
+}
+
+template <int N1, int N2, bool WIN, bool X2>
+void rfft_half_go(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     using H = HalfStep<N1, N2>;
     static SmemLimit attr;
-    attr.ensure(rfft_half_kernel<N1, N2>, (int)H::smem);
+    attr.ensure(rfft_half_kernel<N1, N2, WIN, X2>, (int)H::smem);
     LaunchScope ls(p, s, MDC_KC_RFFT);
-    rfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+    rfft_half_kernel<N1, N2, WIN, X2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+}
+
+template <int N1, int N2, bool PLAIN>
+void irfft_half_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+    using H = HalfStep<N1, N2>;
+    static SmemLimit attr;
+    attr.ensure(irfft_half_kernel<N1, N2, PLAIN>, (int)H::smem);
+    LaunchScope ls(p, s, MDC_KC_IRFFT);
+    irfft_half_kernel<N1, N2, PLAIN><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+}
+
+template <int N1, int N2>
+void rfft_half_launch(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+    if (a.cut) {
+        if (a.x2) rfft_half_go<N1, N2, true, true>(p, a, s);
+        else rfft_half_go<N1, N2, true, false>(p, a, s);
+    } else {
+        if (a.x2) rfft_half_go<N1, N2, false, true>(p, a, s);
+        else rfft_half_go<N1, N2, false, false>(p, a, s);
+    }
 }
 
 template <int N1, int N2>
 void irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
-    using H = HalfStep<N1, N2>;
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
-    static SmemLimit attr;
-    attr.ensure(irfft_half_kernel<N1, N2>, (int)H::smem);
-    LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft_half_kernel<N1, N2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+    if (irfft_plain(a)) irfft_half_go<N1, N2, true>(p, a, s);
+    else irfft_half_go<N1, N2, false>(p, a, s);
 }
 
-template <int N1, int N2, bool WIN, bool X2>
+template <int N1, int N2, bool WIN, bool X2, int PP>
 void rfft4_go(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     static SmemLimit attr;
-    attr.ensure(rfft4_kernel<N1, N2, WIN, X2>, (int)F::smem_full);
+    attr.ensure(rfft4_kernel<N1, N2, WIN, X2, PP>, (int)F::smem_full);
     LaunchScope ls(p, s, MDC_KC_RFFT);
-    rfft4_kernel<N1, N2, WIN, X2><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
+    rfft4_kernel<N1, N2, WIN, X2, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
 }
+
+// Few columns: the default tile would leave most SMs idle (fewer than two CTAs per SM).
+template <int N1, int N2>
+constexpr int few_cols_p() { return 1024 / (N1 * N2) > 2 ? 1024 / (N1 * N2) : 2; }
+inline bool few_columns(int C, int ct) { return (C + ct - 1) / ct < 2 * 148; }
 
 template <int N1, int N2>
 void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     RfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && ((uintptr_t)a.x % 16 == 0) && (!a.x2 || (uintptr_t)a.x2 % 16 == 0);
+    constexpr int PS = few_cols_p<N1, N2>();
+    const bool few = few_columns(a.C, FourStep<N1, N2>::CT) && PS < FourStep<N1, N2>::P;
     if (a.cut) {
-        if (a.x2) rfft4_go<N1, N2, true, true>(p, a, s);
-        else rfft4_go<N1, N2, true, false>(p, a, s);
+        if (a.x2) rfft4_go<N1, N2, true, true, 0>(p, a, s);
+        else rfft4_go<N1, N2, true, false, 0>(p, a, s);
+    } else if (a.x2) {
+        rfft4_go<N1, N2, false, true, 0>(p, a, s);
+    } else if (few) {
+        rfft4_go<N1, N2, false, false, PS>(p, a, s);
     } else {
-        if (a.x2) rfft4_go<N1, N2, false, true>(p, a, s);
-        else rfft4_go<N1, N2, false, false>(p, a, s);
+        rfft4_go<N1, N2, false, false, 0>(p, a, s);
     }
 }
 
-template <int N1, int N2, bool PLAIN>
+template <int N1, int N2, bool PLAIN, int PP>
 void irfft4_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
-    using F = FourStep<N1, N2>;
+    using F = FourStep<N1, N2, PP>;
     static SmemLimit attr;
-    attr.ensure(irfft4_kernel<N1, N2, PLAIN>, (int)F::smem);
+    attr.ensure(irfft4_kernel<N1, N2, PLAIN, PP>, (int)F::smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft4_kernel<N1, N2, PLAIN><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
-}
-
-// The transform alone: no window, base or previous-output terms, column sums or reversal.
-inline bool irfft_plain(const IrfftArgs& a) {
-    return !a.cut && !a.base && !a.colsum && !a.reverse_out && a.a_mdc.h == 1.f && !a.a_mdc.d &&
-           a.a_prev.h == 0.f && !a.a_prev.d;
+    irfft4_kernel<N1, N2, PLAIN, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
 }
 
 template <int N1, int N2>
@@ -1022,8 +1075,14 @@ void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
-    if (irfft_plain(a)) irfft4_go<N1, N2, true>(p, a, s);
-    else irfft4_go<N1, N2, false>(p, a, s);
+    constexpr int PS = few_cols_p<N1, N2>();
+    const bool few = few_columns(a.C, FourStep<N1, N2>::CT) && PS < FourStep<N1, N2>::P;
+    if (irfft_plain(a)) {
+        if (few) irfft4_go<N1, N2, true, PS>(p, a, s);
+        else irfft4_go<N1, N2, true, 0>(p, a, s);
+    } else {
+        irfft4_go<N1, N2, false, 0>(p, a, s);
+    }
 }
 
 int tile_log_columns(int nt) {
