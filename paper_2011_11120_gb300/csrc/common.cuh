@@ -166,6 +166,14 @@ struct IrfftArgs {
     const float2* tw;
     const int* active;
     int vec4;              // set by the launcher: aligned 4-column output path
+    // An LSQR step applied with the previous output v = out (before it is overwritten), same layout:
+    //   xw_x <- xw_x + kx * xw_w,   xw_w <- ia * v + kw * xw_w     (kx, kw, ia: device doubles)
+    // xw_w null: no step.  Needs the previous-output term and no time reversal.
+    float* xw_x;
+    float* xw_w;
+    const double* xw_kx;
+    const double* xw_kw;
+    const double* xw_ia;
 };
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
 // The inverse transform; on a frequency shard with a reduction hook: the partial transform, the

@@ -475,10 +475,13 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     }
 }
 
-// PLAIN: the output is the transform alone (no window, base or previous-output terms, column sums
-// or time reversal, a_mdc = 1).  The inverse scale multiplies the spectrum as it is loaded.
-template <int N1, int N2, bool PLAIN, int PP>
-__global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
+// MODE 1 (plain): the output is the transform alone (no window, base or previous-output terms,
+// column sums or time reversal, a_mdc = 1); MODE 0: the general epilogue; MODE 2: the general
+// epilogue with the LSQR x/w step of IrfftArgs fused in.  The inverse scale multiplies the
+// spectrum as it is loaded.
+template <int N1, int N2, int MODE, int PP>
+__global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(IrfftArgs a) {
+    constexpr bool PLAIN = MODE == 1, XW = MODE == 2;
     using F = FourStep<N1, N2, PP>;
     constexpr int NT = F::NT, CT = F::CT, P = F::P;
     if (a.active && *a.active == 0) return;
@@ -578,9 +581,15 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
     }
     const float am = coef(a.a_mdc), ab = coef(a.a_base), ap = coef(a.a_prev);
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
+    float xkx = 0.f, xkw = 0.f, xia = 0.f;
+    if constexpr (XW) {
+        xkx = (float)*a.xw_kx;
+        xkw = (float)*a.xw_kw;
+        xia = (float)*a.xw_ia;
+    }
     if (a.vec4) {
         // four adjacent columns per thread: 16-byte loads and stores
-        constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, B = PER < 4 ? PER : 4;
+        constexpr int Q = CT / 4, TS = FFT_THREADS / Q, PER = NT / TS, BB = XW ? 2 : 4, B = PER < BB ? PER : BB;
         const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
         const bool want_ss = a.colsum != nullptr;
         float ss[4] = {0.f, 0.f, 0.f, 0.f};   // per-thread partial sums of squares (<= 16 terms)
@@ -591,13 +600,17 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
 #pragma unroll 1
             for (int b0 = 0; b0 < PER; b0 += B) {
                 // storage row rho holds time sample t = (rho % N2) * N1 + rho / N2
-                float4 bv[B], pv[B];
+                float4 bv[B], pv[B], wv[XW ? B : 1], xv[XW ? B : 1];
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     const int rho = t0 + (b0 + u) * TS;
                     const size_t o = (size_t)((rho % N2) * N1 + rho / N2) * a.C + cq;
                     bv[u] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
                     pv[u] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (XW) {
+                        wv[u] = *reinterpret_cast<const float4*>(a.xw_w + o);
+                        xv[u] = *reinterpret_cast<const float4*>(a.xw_x + o);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
@@ -615,7 +628,20 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                         v[i] = am * val + ab * bb[i] + ap * pp[i];
                         if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                     }
-                    *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
+                    const size_t o = (size_t)t * a.C + cq;
+                    *reinterpret_cast<float4*>(a.out + o) = make_float4(v[0], v[1], v[2], v[3]);
+                    if constexpr (XW) {
+                        const float ww[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
+                        const float xx[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+                        float nw[4], nx[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            nx[i] = fmaf(xkx, ww[i], xx[i]);
+                            nw[i] = fmaf(xkw, ww[i], xia * pp[i]);
+                        }
+                        *reinterpret_cast<float4*>(a.xw_x + o) = make_float4(nx[0], nx[1], nx[2], nx[3]);
+                        *reinterpret_cast<float4*>(a.xw_w + o) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+                    }
                 }
             }
         }
@@ -642,7 +668,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
         const int t0 = threadIdx.x / CT;
 #pragma unroll 1
         for (int b0 = 0; b0 < PER; b0 += B) {
-            float bv[B], pv[B];
+            float bv[B], pv[B], wv[XW ? B : 1], xv[XW ? B : 1];
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 const int rho = t0 + (b0 + u) * TS;
@@ -650,6 +676,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                 bv[u] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
                 pv[u] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
+                if constexpr (XW) {
+                    wv[u] = a.xw_w[(size_t)t * a.C + c];
+                    xv[u] = a.xw_x[(size_t)t * a.C + c];
+                }
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
@@ -663,6 +693,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) irfft4_kernel(IrfftArgs a) {
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                 a.out[(size_t)to * a.C + c] = r;
                 if (want_ss) ss = fmaf(r, r, ss);
+                if constexpr (XW) {
+                    a.xw_x[(size_t)t * a.C + c] = fmaf(xkx, wv[u], xv[u]);
+                    a.xw_w[(size_t)t * a.C + c] = fmaf(xkw, wv[u], xia * pv[u]);
+                }
             }
         }
     }
@@ -988,7 +1022,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
 // The transform alone: no window, base or previous-output terms, column sums or reversal.
 inline bool irfft_plain(const IrfftArgs& a) {
     return !a.cut && !a.base && !a.colsum && !a.reverse_out && a.a_mdc.h == 1.f && !a.a_mdc.d &&
-           a.a_prev.h == 0.f && !a.a_prev.d;
+           a.a_prev.h == 0.f && !a.a_prev.d && !a.xw_w;
 }
 
 template <int N1, int N2, bool WIN, bool X2>
@@ -1061,27 +1095,30 @@ void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     }
 }
 
-template <int N1, int N2, bool PLAIN, int PP>
+template <int N1, int N2, int MODE, int PP>
 void irfft4_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     using F = FourStep<N1, N2, PP>;
     static SmemLimit attr;
-    attr.ensure(irfft4_kernel<N1, N2, PLAIN, PP>, (int)F::smem);
+    attr.ensure(irfft4_kernel<N1, N2, MODE, PP>, (int)F::smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft4_kernel<N1, N2, PLAIN, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+    irfft4_kernel<N1, N2, MODE, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
 }
 
 template <int N1, int N2>
 void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
-             (!a.base || (uintptr_t)a.base % 16 == 0);
+             (!a.base || (uintptr_t)a.base % 16 == 0) &&
+             (!a.xw_w || ((uintptr_t)a.xw_w % 16 == 0 && (uintptr_t)a.xw_x % 16 == 0));
     constexpr int PS = few_cols_p<N1, N2>();
     const bool few = few_columns(a.C, FourStep<N1, N2>::CT) && PS < FourStep<N1, N2>::P;
     if (irfft_plain(a)) {
-        if (few) irfft4_go<N1, N2, true, PS>(p, a, s);
-        else irfft4_go<N1, N2, true, 0>(p, a, s);
+        if (few) irfft4_go<N1, N2, 1, PS>(p, a, s);
+        else irfft4_go<N1, N2, 1, 0>(p, a, s);
+    } else if (a.xw_w) {
+        irfft4_go<N1, N2, 2, 0>(p, a, s);
     } else {
-        irfft4_go<N1, N2, false, 0>(p, a, s);
+        irfft4_go<N1, N2, 0, 0>(p, a, s);
     }
 }
 
@@ -1160,7 +1197,34 @@ __global__ void __launch_bounds__(256) shard_epilogue(IrfftArgs a, const float* 
 
 }  // namespace
 
-void launch_irfft(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+namespace {
+// The LSQR x/w step of IrfftArgs on its own, for the transforms that do not fuse it: run before the
+// transform overwrites its previous output v.  Same rounding as the fused form.
+__global__ void xw_step(int64_t n, float* __restrict__ x, float* __restrict__ w, const float* __restrict__ v,
+                        const double* kx, const double* kw, const double* ia, const int* active) {
+    if (active && *active == 0) return;
+    const float fx = (float)*kx, fw = (float)*kw, fa = (float)*ia;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float wo = w[i];
+        x[i] = fmaf(fx, wo, x[i]);
+        w[i] = fmaf(fw, wo, fa * v[i]);
+    }
+}
+
+// The inverse transforms that fuse the LSQR x/w step: the four-step kernels (nt <= 1024).
+inline bool irfft_fuses_xw(const IrfftArgs& a) { return a.nt <= 1024 && !a.reverse_out; }
+}  // namespace
+
+void launch_irfft(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
+    IrfftArgs a = a0;
+    if (a.xw_w && (p->red_fn || !irfft_fuses_xw(a))) {
+        const int64_t n = (int64_t)a.nt * a.C;
+        int64_t g = (n + 255) / 256;
+        if (g > 152 * 16) g = 152 * 16;
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        xw_step<<<(unsigned)g, 256, 0, s>>>(n, a.xw_x, a.xw_w, a.out, a.xw_kx, a.xw_kw, a.xw_ia, a.active);
+        a.xw_x = a.xw_w = nullptr;
+    }
     if (!p->red_fn) {
         launch_irfft_local(p, a, s);
         return;

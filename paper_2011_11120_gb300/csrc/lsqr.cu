@@ -106,8 +106,13 @@ struct Solver {
         launch_rfft(q, a, s);
     }
     void irfft(mdc_plan* q, int voff, int conj_in, float* out, Coef a_mdc, const int* cutp, const float* base,
-               Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active) {
+               Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active, float* xw_x = nullptr,
+               float* xw_w = nullptr) {
         IrfftArgs a{};
+        if (xw_w) {                   // the pending LSQR x/w step, applied with the previous v-hat
+            a.xw_x = xw_x; a.xw_w = xw_w;
+            a.xw_kx = sc + S_KX; a.xw_kw = sc + S_KW; a.xw_ia = sc + S_INV_ALPHA;
+        }
         a.Y = q->specB; a.ldv = LD(); a.voff = voff0 + voff; a.C = C; a.S = n; a.nv = nv; a.nt = q->nt;
         a.logn = q->logn; a.nf = q->nf; a.k0 = q->k0; a.conj_in = conj_in;
         a.scale = (float)(q->dt * q->dr / (double)q->nt);
@@ -197,27 +202,23 @@ struct Solver {
         rfft(p, U1(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, a);
         rfft(p, U2(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, a);
     }
+    // The adjoint transforms also apply the previous rotation's x/w step (x += (phi/rho) w,
+    // w = v / alpha + kw w) with the v-hat they overwrite; the last rotation's x step is applied by
+    // xw_flush at the end of the solve.
     void iter_adj_post(int it, int niter, double tol, int* act0, double* resid0, int* itp, float* x1, float* x2) {
         const int* a = act0 + it;
         const Coef vprev = CD(1.f, sc + S_V_PREV);
-        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, a);
-        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, a);
-        {
-            LaunchScope ls(p, s, MDC_KC_SOLVER);
-            colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, 2 * C, part, a);
-            lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act0 + it + 1, resid0, itp, it,
-                                                        niter, tol);
-        }
+        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, a, x1, W1());
+        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, a, x2, W2());
         LaunchScope ls(p, s, MDC_KC_SOLVER);
-        const bool vec = (B % 4) == 0 && aligned16(x1) && aligned16(x2) && aligned16(W1()) && aligned16(W2()) &&
-                         aligned16(V1()) && aligned16(V2());
-        if (vec)
-            lsqr_xw4<<<elementwise_grid(B / 4), 256, 0, s>>>(
-                B / 4, reinterpret_cast<float4*>(x1), reinterpret_cast<float4*>(x2), reinterpret_cast<float4*>(W1()),
-                reinterpret_cast<float4*>(W2()), reinterpret_cast<const float4*>(V1()),
-                reinterpret_cast<const float4*>(V2()), sc, a);
-        else
-            lsqr_xw<<<elementwise_grid(B), 256, 0, s>>>(B, x1, x2, W1(), W2(), V1(), V2(), sc, a);
+        colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, 2 * C, part, a);
+        lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act0 + it + 1, resid0, itp, it,
+                                                    niter, tol);
+    }
+    // The last rotation's pending x step (once per solve, after its last iteration).
+    void xw_flush(float* x1, float* x2) {
+        LaunchScope ls(p, s, MDC_KC_SOLVER);
+        lsqr_x_flush<<<elementwise_grid(B), 256, 0, s>>>(B, x1, x2, W1(), W2(), sc);
     }
 
     // LSQR on u-hat (already holding the right-hand side and its column sums); x accumulates.
@@ -235,6 +236,7 @@ struct Solver {
             iter_adj_post(it, niter, tol, act0, resid0, itp, x1, x2);
             nvtxRangePop();
         }
+        xw_flush(x1, x2);
     }
 
     // Neumann series of Eq. 5 (forward passes only): x_k = d + N x_{k-1} from x_0 = 0, with
@@ -925,6 +927,7 @@ extern "C" int srv_step(mdc_server* v, int* completed) {
                 keep.push_back(j);
                 continue;
             }
+            j->S->xw_flush(j->x[0], j->x[1]);     // this solve's last x step
             if (j->solve < v->nref) {
                 const int niter = j->solve == 0 ? j->niter : v->niter_ref;
                 j->S->residual_pass(j->x[0], j->x[1]);

@@ -154,40 +154,16 @@ __global__ void __launch_bounds__(RED_THREADS) lsqr_alpha_rotate(double* sc, con
 __device__ __forceinline__ float xw_x(float x, float w, float kx) { return fmaf(kx, w, x); }
 __device__ __forceinline__ float xw_w(float v, float w, float ia, float kw) { return fmaf(kw, w, ia * v); }
 
-// x += (phi/rho) w ;  w = v-hat / alpha - (theta/rho) w, over both blocks; four elements per thread
-// and step (n4 = n / 4 16-byte vectors, every array 16-byte aligned: checked by the caller).
-__global__ void lsqr_xw4(int64_t n4, float4* __restrict__ x1, float4* __restrict__ x2,
-                         float4* __restrict__ w1, float4* __restrict__ w2,
-                         const float4* __restrict__ v1, const float4* __restrict__ v2,
-                         const double* sc, const int* act) {
-    if (*act == 0) return;
-    const float kx = (float)sc[S_KX], kw = (float)sc[S_KW], ia = (float)sc[S_INV_ALPHA];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 wa = w1[i], xa = x1[i], va = v1[i], wb = w2[i], xb = x2[i], vb = v2[i];
-        x1[i] = make_float4(xw_x(xa.x, wa.x, kx), xw_x(xa.y, wa.y, kx), xw_x(xa.z, wa.z, kx), xw_x(xa.w, wa.w, kx));
-        w1[i] = make_float4(xw_w(va.x, wa.x, ia, kw), xw_w(va.y, wa.y, ia, kw), xw_w(va.z, wa.z, ia, kw),
-                            xw_w(va.w, wa.w, ia, kw));
-        x2[i] = make_float4(xw_x(xb.x, wb.x, kx), xw_x(xb.y, wb.y, kx), xw_x(xb.z, wb.z, kx), xw_x(xb.w, wb.w, kx));
-        w2[i] = make_float4(xw_w(vb.x, wb.x, ia, kw), xw_w(vb.y, wb.y, ia, kw), xw_w(vb.z, wb.z, ia, kw),
-                            xw_w(vb.w, wb.w, ia, kw));
-    }
-}
-
-__global__ void lsqr_xw(int64_t n, float* __restrict__ x1, float* __restrict__ x2,
-                        float* __restrict__ w1, float* __restrict__ w2,
-                        const float* __restrict__ v1, const float* __restrict__ v2,
-                        const double* sc, const int* act) {
-    if (*act == 0) return;
-    const float kx = (float)sc[S_KX], kw = (float)sc[S_KW], ia = (float)sc[S_INV_ALPHA];
+// The pending x step of the last plane rotation, x += (phi/rho) w, over both blocks: the w step of a
+// rotation is applied with the next iteration's adjoint transform, which also applies the x step,
+// so the last rotation's x step is left for the end of the solve.
+__global__ void lsqr_x_flush(int64_t n, float* __restrict__ x1, float* __restrict__ x2, const float* __restrict__ w1,
+                             const float* __restrict__ w2, const double* sc) {
+    const float kx = (float)sc[S_KX];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float w = w1[i];
-        x1[i] = xw_x(x1[i], w, kx);
-        w1[i] = xw_w(v1[i], w, ia, kw);
-        w = w2[i];
-        x2[i] = xw_x(x2[i], w, kx);
-        w2[i] = xw_w(v2[i], w, ia, kw);
+        x1[i] = xw_x(x1[i], w1[i], kx);
+        x2[i] = xw_x(x2[i], w2[i], kx);
     }
 }
 

@@ -581,6 +581,7 @@ bool gemv_chunk_allowed() {
 
 // ------------------------------------------------------------------ SIMT complex GEMM
 constexpr int GBM = 64, GBN = 64, GBK = 8;
+constexpr int GCHUNK = 16;                 // reduction tiles per partial sum (128 terms)
 // Narrow tile for few columns: 128 rows x 32 columns (each thread still 4 x 4 outputs), so a
 // 20-column product leaves 38 % of the tile idle instead of 69 %.
 constexpr int GBM_N = 128, GBN_N = 32;
@@ -634,11 +635,14 @@ __global__ void __launch_bounds__(256) cgemm_simt(
     const float* sck = gscale + (size_t)k * nr;
     const float2* Bk = B + (size_t)k * K * ldb + voff_b;
     const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
-    float2 acc[4][4];
+    // Two-level sums: each chunk of GCHUNK reduction tiles accumulates in part, which is then added
+    // to acc, so a float32 sum over K terms carries about (GCHUNK * GBK + K / (GCHUNK * GBK)) roundings
+    // per output instead of K.
+    float2 acc[4][4], part[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) acc[i][j] = part[i][j] = make_float2(0.f, 0.f);
 
     for (int kt = 0; kt < K; kt += GBK) {
         // A tile: GBK x TBM complex values, 64 rows (forward) or 64 columns (adjoint) per round
@@ -687,9 +691,18 @@ __global__ void __launch_bounds__(256) cgemm_simt(
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < 4; ++j) cfma(part[i][j], a[i], b[j]);
         }
         __syncthreads();
+        if ((kt / GBK) % GCHUNK == GCHUNK - 1 || kt + GBK >= K) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j] = cadd(acc[i][j], part[i][j]);
+                    part[i][j] = make_float2(0.f, 0.f);
+                }
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

@@ -156,20 +156,24 @@ struct TcArgs {
 };
 
 // Pipeline depth: as many stages as fit 198 KB (at most 8); the split format carries two copies.
-// The E4M3 path (CVT) streams stages of [B slices | A byte tile] (at most 16) and widens A into a
-// separate ring of WBUF FP16 tiles.  Its byte tiles have 128-byte rows, as many bytes per TMA row
-// as the 16-bit tiles (adjoint: one box covers both 64-element halves of the 128 output rows), and
-// for narrow B tiles a stage spans KSUB = 2 reduction slices (the widened tile is two slices, each
-// laid out as a 16-bit TMA load of one slice would be), halving the hand-offs per kernel byte.
+// The E4M3 path (CVT) keeps three rings: stages of B slices (released when the MMAs that read them
+// complete), byte tiles of A (NBY slots, released as soon as they are widened, so the loads of the
+// kernel bytes run ahead of the MMAs by the whole byte ring), and WBUF widened FP16 tiles.  The
+// byte tiles have 128-byte rows, as many bytes per TMA row as the 16-bit tiles (adjoint: one box
+// covers both 64-element halves of the 128 output rows), and for narrow B tiles a stage spans
+// KSUB = 2 reduction slices (the widened tile is two slices, each laid out as a 16-bit TMA load of
+// one slice would be), halving the hand-offs per kernel byte.
 template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false> struct TcStages {
     static constexpr int KSUB = (CVT && BN <= 64) ? 2 : 1;
     static constexpr int WBUF = CVT ? (KSUB == 2 || BN >= 256 ? 2 : 3) : 0;
     static constexpr int WA = TC_BM * 128 * KSUB;                      // one widened A tile
-    static constexpr int bytes = CVT ? KSUB * (BN * 128 + (int)TC_STG_BYTES)
-                                     : (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
+    static constexpr int BYT = CVT ? KSUB * (int)TC_STG_BYTES : 0;     // one byte tile of A
+    static constexpr int bytes = CVT ? KSUB * BN * 128 : (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
     static constexpr int fit = (198 * 1024 - WBUF * WA) / bytes;
-    static constexpr int cap = CVT ? 16 : 8;
-    static constexpr int v = fit > cap ? cap : fit;
+    static constexpr int v = CVT ? (BN <= 64 ? 4 : 3) : (fit > 8 ? 8 : fit);
+    static constexpr int byfit = CVT ? (198 * 1024 - WBUF * WA - v * bytes) / BYT : 0;
+    static constexpr int NBY = byfit > 16 ? 16 : byfit;
+    static_assert(!CVT || NBY >= 2, "byte ring");
 };
 
 template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false>
@@ -177,7 +181,8 @@ constexpr size_t tc_smem_bytes() {
     // + alignment, barriers and TMEM slot, two 128-float column-scale buffers, and eight
     // 32 x 20-float output staging tiles
     using S = TcStages<BN, SPLIT, CVT, ADJ>;
-    return (size_t)S::v * S::bytes + (size_t)S::WBUF * S::WA + 1024 + 512 + 1024 + 8 * 32 * 20 * 4;
+    return (size_t)S::v * S::bytes + (size_t)S::NBY * S::BYT + (size_t)S::WBUF * S::WA + 1024 + 512 + 1024 +
+           8 * 32 * 20 * 4;
 }
 
 // Two E4M3 values (low byte first) to a packed pair of FP16 (exact: E4M3 is a subset of FP16).
@@ -226,11 +231,12 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     constexpr int STAGES = SC::v;
     constexpr int WBUF = SC::WBUF;
     constexpr int KSUB = SC::KSUB;
+    constexpr int NBY = SC::NBY;
+    constexpr uint32_t BYT = SC::BYT;
     constexpr uint32_t A_BYTES = TC_BM * 128;
     constexpr uint32_t B_BYTES = BN * 128;
     constexpr uint32_t WA_BYTES = SC::WA;
-    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo; or (CVT) KSUB B slices, then the
-    // byte tile of A (KSUB * 8 KB)
+    // stage layout: A_hi, B_hi, then (split format) A_lo, B_lo; or (CVT) KSUB B slices
     constexpr uint32_t STAGE_BYTES = SC::bytes;
     // KSUB divides the forward kstages; an adjoint tail slice reads rows past nr (zero filled)
     const int ksteps = (a.kstages + KSUB - 1) / KSUB;
@@ -238,18 +244,20 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     const uint32_t raw = su32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
-    const uint32_t wbase = base + STAGES * STAGE_BYTES;          // (CVT) widened A tiles
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES + WBUF * WA_BYTES);
+    const uint32_t bybase = base + STAGES * STAGE_BYTES;         // (CVT) byte tiles of A
+    const uint32_t wbase = bybase + NBY * BYT;                   // (CVT) widened A tiles
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + STAGES * STAGE_BYTES + NBY * BYT + WBUF * WA_BYTES);
     // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], tmem slot (two words), the MMA
-    // issuer's drain barrier, (CVT) conv[WBUF], wfree[WBUF], then the epilogue's double-buffered
-    // column scales of the current tile (16-byte aligned)
-    constexpr int SIG_OFF = 2 * STAGES + 6 + 2 * WBUF;
+    // issuer's drain barrier, (CVT) conv[WBUF], wfree[WBUF], bfull[NBY], bempty[NBY], then the
+    // epilogue's double-buffered column scales of the current tile (16-byte aligned)
+    constexpr int SIG_OFF = 2 * STAGES + 6 + 2 * WBUF + 2 * NBY;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
     float* sig_s = reinterpret_cast<float*>(bars + SIG_OFF);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
     const uint32_t accf0 = su32(bars + 2 * STAGES), acce0 = su32(bars + 2 * STAGES + 2);
     const uint32_t drain0 = su32(bars + 2 * STAGES + 5);
     const uint32_t conv0 = su32(bars + 2 * STAGES + 6), wfree0 = conv0 + 8 * WBUF;
+    const uint32_t bfull0 = wfree0 + 8 * WBUF, bempty0 = bfull0 + 8 * NBY;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t_first = (int)blockIdx.x;
     const int t_stride = (int)gridDim.x;
@@ -269,6 +277,10 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
         for (int i = 0; i < WBUF; ++i) {
             mbar_init(conv0 + 8 * i, TC_CVT_THREADS / 32);
             mbar_init(wfree0 + 8 * i, 1);
+        }
+        for (int i = 0; i < NBY; ++i) {
+            mbar_init(bfull0 + 8 * i, 1);
+            mbar_init(bempty0 + 8 * i, TC_CVT_THREADS / 32);
         }
         fence_mbar_init();
     }
@@ -302,13 +314,8 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     }
                     const uint32_t sa = base + s * STAGE_BYTES;
                     if constexpr (CVT) {
-                        // B as usual at the stage start, A as bytes after it
-                        // B slices at the stage start, A as bytes after them: forward one box of
-                        // 128 rows x KSUB * 64 bytes, adjoint one box of KSUB * 64 rows x 128 bytes
-                        const uint32_t st = sa + KSUB * B_BYTES;
-                        mbar_expect_tx(full0 + 8 * s, KSUB * (TC_STG_BYTES + B_BYTES));
-                        if (!ADJ) tma_load_3d(st, &tmA, full0 + 8 * s, kb * KSUB * TC_BK, m0, k);
-                        else tma_load_3d(st, &tmA, full0 + 8 * s, m0, kb * KSUB * TC_BK, k);
+                        // B slices only: the byte tiles of A come from lane 1
+                        mbar_expect_tx(full0 + 8 * s, KSUB * B_BYTES);
 #pragma unroll
                         for (int h = 0; h < KSUB; ++h) {
                             const uint32_t bt = sa + h * B_BYTES;
@@ -336,6 +343,28 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             // drain: every copy this thread issued must have landed before the CTA can exit
             for (long q = g > STAGES ? g - STAGES : 0; q < g; ++q)
                 mbar_wait(full0 + 8 * (int)(q % STAGES), (uint32_t)(q / STAGES) & 1, a.err, 2, TC_DRAIN_NS);
+        } else if (CVT && lane == 1) {
+            // the byte tiles of A: forward one box of 128 rows x KSUB * 64 bytes, adjoint one box of
+            // KSUB * 64 rows x 128 bytes, into slot g % NBY once the converters have released it
+            long g = 0;
+            bool ok = true;
+            for (int tile = t_first; tile < n_tiles && ok; tile += t_stride) {
+                int k, m0, n0;
+                coords(tile, k, m0, n0);
+                for (int kb = 0; kb < ksteps; ++kb, ++g) {
+                    const int y = (int)(g % NBY);
+                    if (g >= NBY && !mbar_wait(bempty0 + 8 * y, (uint32_t)(g / NBY - 1) & 1, a.err, 10, wl)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = bybase + y * BYT;
+                    mbar_expect_tx(bfull0 + 8 * y, BYT);
+                    if (!ADJ) tma_load_3d(st, &tmA, bfull0 + 8 * y, kb * KSUB * TC_BK, m0, k);
+                    else tma_load_3d(st, &tmA, bfull0 + 8 * y, m0, kb * KSUB * TC_BK, k);
+                }
+            }
+            for (long q = g > NBY ? g - NBY : 0; q < g; ++q)
+                mbar_wait(bfull0 + 8 * (int)(q % NBY), (uint32_t)(q / NBY) & 1, a.err, 11, TC_DRAIN_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -403,9 +432,9 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
         bool ok = true;
         for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
             for (int kb = 0; kb < ksteps; ++kb, ++g) {
-                const int s = (int)(g % STAGES);
+                const int y = (int)(g % (CVT ? NBY : 1));
                 const int w = (int)(g % (CVT ? WBUF : 1));
-                if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / STAGES) & 1, a.err, 6, wl)) {
+                if (!mbar_wait(bfull0 + 8 * y, (uint32_t)(g / (CVT ? NBY : 1)) & 1, a.err, 6, wl)) {
                     ok = false;
                     break;
                 }
@@ -414,7 +443,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     ok = false;
                     break;
                 }
-                const unsigned char* stg = gbase + (size_t)s * STAGE_BYTES + KSUB * B_BYTES;
+                const unsigned char* stg = gbase + (bybase - base) + (size_t)y * BYT;
                 unsigned char* at = gbase + (size_t)STAGES * STAGE_BYTES + (size_t)w * WA_BYTES;
                 // byte tile rows of RB bytes (64 forward with KSUB = 1, else 128).  Forward: chunk j of
                 // row R goes to slice j / 8, row R; adjoint: row R is reduction row R % 64 of slice
@@ -439,7 +468,10 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 // the tensor core reads the tile through the async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(conv0 + 8 * w);
+                if (lane == 0) {
+                    mbar_arrive(conv0 + 8 * w);
+                    mbar_arrive(bempty0 + 8 * y);      // this warp's reads of the byte tile are done
+                }
             }
     } else {
         const int q = warp & 3;                  // TMEM lane quarter of this warp
