@@ -76,10 +76,25 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity, uint32_t
         : "memory");
     return ok != 0;
 }
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Wait for the phase with the given parity to complete, for at most about limit_ns nanoseconds:
-// every try is bounded by a suspend hint no longer than the limit (1 ms at most), so the clock
-// is checked at least that often.
+// a short spin of non-blocking tests first (hand-offs that complete within a few hundred cycles
+// cost no suspension), then tries bounded by a suspend hint no longer than the limit (1 ms at
+// most), so the clock is checked at least that often.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, unsigned long long limit_ns) {
+    for (int i = 0; i < 64; ++i)
+        if (mbar_poll(bar, parity)) return true;
     const uint32_t hint = (uint32_t)(limit_ns < 1000000ull ? limit_ns : 1000000ull);
     if (mbar_try(bar, parity, hint)) return true;
     const unsigned long long t0 = gtime();
@@ -163,8 +178,12 @@ struct TcArgs {
 // covers both 64-element halves of the 128 output rows), and for narrow B tiles a stage spans
 // KSUB = 2 reduction slices (the widened tile is two slices, each laid out as a 16-bit TMA load of
 // one slice would be), halving the hand-offs per kernel byte.
+// Reduction slices per E4M3 step for a B tile of BN columns: two for narrow tiles (half the
+// hand-offs per kernel byte), one otherwise.
+constexpr int tc_cvt_ksub(int bn) { return bn <= 64 ? 2 : 1; }
+
 template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false> struct TcStages {
-    static constexpr int KSUB = (CVT && BN <= 64) ? 2 : 1;
+    static constexpr int KSUB = CVT ? tc_cvt_ksub(BN) : 1;
     static constexpr int WBUF = CVT ? (KSUB == 2 || BN >= 256 ? 2 : 3) : 0;
     static constexpr int WA = TC_BM * 128 * KSUB;                      // one widened A tile
     static constexpr int BYT = CVT ? KSUB * (int)TC_STG_BYTES : 0;     // one byte tile of A
@@ -428,6 +447,24 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
         // widen each stage's byte tile: item (row R, 8-byte chunk j) -> 16 bytes at row R, chunk
         // j ^ (R % 8) of the 128-byte-swizzled A tile
         const int ct = threadIdx.x - TC_THREADS;
+        // byte tile rows of RB bytes (64 forward with KSUB = 1, else 128).  Forward: 8-byte chunk j
+        // of row R goes to slice j / 8, row R; adjoint: row R is reduction row R % 64 of slice R / 64,
+        // and chunk j goes to output-row half j / 8 (8 KB apart); in both the widened 16-byte chunk
+        // lands swizzled at (j % 8) ^ (R % 8).  Each thread takes 16-byte source chunks (two 8-byte
+        // chunks j, j + 1 of one row and slice) whose offsets are the same at every step.
+        constexpr int RB = (!ADJ && KSUB == 1) ? 64 : 128;
+        constexpr int PER = (int)(KSUB * TC_STG_BYTES) / 16 / TC_CVT_THREADS;
+        uint32_t soff[PER], doff[PER][2];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int idx = ct + TC_CVT_THREADS * u;
+            const int R = idx / (RB / 16), j = 2 * (idx % (RB / 16));
+            const int off = ADJ ? (R >> 6) * (int)A_BYTES + (j >> 3) * (int)(A_BYTES / 2) + (R & 63) * 128
+                                : (j >> 3) * (int)A_BYTES + R * 128;
+            soff[u] = (uint32_t)(R * RB + j * 8);
+            doff[u][0] = (uint32_t)(off + (((j & 7) ^ (R & 7)) << 4));
+            doff[u][1] = (uint32_t)(off + ((((j + 1) & 7) ^ (R & 7)) << 4));
+        }
         long g = 0;
         bool ok = true;
         for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
@@ -444,26 +481,23 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     break;
                 }
                 const unsigned char* stg = gbase + (bybase - base) + (size_t)y * BYT;
-                unsigned char* at = gbase + (size_t)STAGES * STAGE_BYTES + (size_t)w * WA_BYTES;
-                // byte tile rows of RB bytes (64 forward with KSUB = 1, else 128).  Forward: chunk j of
-                // row R goes to slice j / 8, row R; adjoint: row R is reduction row R % 64 of slice
-                // R / 64, and chunk j goes to output-row half j / 8 (8 KB apart); in both the
-                // 16-byte chunk lands swizzled at (j % 8) ^ (R % 8)
-                constexpr int RB = (!ADJ && KSUB == 1) ? 64 : 128;
-                constexpr int ITEMS = (int)(KSUB * TC_STG_BYTES) / 8;
+                unsigned char* at = gbase + (wbase - base) + (size_t)w * WA_BYTES;
+                uint4 src[PER];
 #pragma unroll
-                for (int u = 0; u < ITEMS / TC_CVT_THREADS; ++u) {
-                    const int idx = ct + TC_CVT_THREADS * u;
-                    const int R = idx / (RB / 8), j = idx % (RB / 8);
-                    const int off = ADJ ? (R >> 6) * (int)A_BYTES + (j >> 3) * (int)(A_BYTES / 2) + (R & 63) * 128
-                                        : (j >> 3) * (int)A_BYTES + R * 128;
-                    const uint2 w = *reinterpret_cast<const uint2*>(stg + R * RB + j * 8);
-                    uint4 h;
-                    h.x = e4m3x2_to_h2(w.x);
-                    h.y = e4m3x2_to_h2(w.x >> 16);
-                    h.z = e4m3x2_to_h2(w.y);
-                    h.w = e4m3x2_to_h2(w.y >> 16);
-                    *reinterpret_cast<uint4*>(at + off + (((j & 7) ^ (R & 7)) << 4)) = h;
+                for (int u = 0; u < PER; ++u) src[u] = *reinterpret_cast<const uint4*>(stg + soff[u]);
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    uint4 h0, h1;
+                    h0.x = e4m3x2_to_h2(src[u].x);
+                    h0.y = e4m3x2_to_h2(src[u].x >> 16);
+                    h0.z = e4m3x2_to_h2(src[u].y);
+                    h0.w = e4m3x2_to_h2(src[u].y >> 16);
+                    h1.x = e4m3x2_to_h2(src[u].z);
+                    h1.y = e4m3x2_to_h2(src[u].z >> 16);
+                    h1.z = e4m3x2_to_h2(src[u].w);
+                    h1.w = e4m3x2_to_h2(src[u].w >> 16);
+                    *reinterpret_cast<uint4*>(at + doff[u][0]) = h0;
+                    *reinterpret_cast<uint4*>(at + doff[u][1]) = h1;
                 }
                 // the tensor core reads the tile through the async proxy
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -944,7 +978,8 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     // E4M3 byte tiles: forward 128 rows x 128 bytes for B tiles of <= 64 columns (two reduction
     // slices per stage), else 128 x 64; adjoint 128 (<= 64 columns) or 64 reduction rows x 128
     // bytes (both output-row halves)
-    const uint32_t fa0 = e4m3 && bn <= 64 ? 128 : 64, aa0 = e4m3 ? 128 : 64, aa1 = e4m3 && bn <= 64 ? 128 : 64;
+    const int ks = tc_cvt_ksub(bn);
+    const uint32_t fa0 = e4m3 ? 64 * ks : 64, aa0 = e4m3 ? 128 : 64, aa1 = e4m3 ? 64 * ks : 64;
     for (int h = 0; h < (split ? 2 : 1) && ok; ++h) {
         const void* ga = G + h * glo;
         const void* gb = Bp + h * blo;
