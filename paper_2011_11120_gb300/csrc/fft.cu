@@ -1072,10 +1072,12 @@ void rfft4_go(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     rfft4_kernel<N1, N2, WIN, X2, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem_full, s>>>(a);
 }
 
-// Few columns: the default tile would leave most SMs idle (fewer than two CTAs per SM).
+// Few columns: the default tile would leave most SMs idle (fewer CTAs than half the SMs); smaller
+// tiles then shorten each CTA's work.  (With one or more default CTAs per SM the smaller tiles only
+// add waves: measured slower at 3721 columns of 1024 samples.)
 template <int N1, int N2>
 constexpr int few_cols_p() { return 1024 / (N1 * N2) > 2 ? 1024 / (N1 * N2) : 2; }
-inline bool few_columns(int C, int ct) { return (C + ct - 1) / ct < 2 * 148; }
+inline bool few_columns(int C, int ct) { return (C + ct - 1) / ct < 148 / 2; }
 
 template <int N1, int N2>
 void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
