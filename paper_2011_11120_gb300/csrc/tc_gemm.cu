@@ -34,9 +34,11 @@ namespace {
 
 // warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: epilogue (two warps per TMEM lane
 // quarter, each taking half of the accumulator columns); for the E4M3 kernel copy warps
-// 10..17 widen each stage's A tile to FP16
+// 10..17 widen each stage's A tile to FP16 and warp 18 streams its bytes
 constexpr int TC_THREADS = 320;
 constexpr int TC_CVT_THREADS = 256;
+// (E4M3) the warp that streams the byte tiles of A, after the converter warps
+constexpr int TC_BYTE_WARP = (TC_THREADS + TC_CVT_THREADS) / 32;
 constexpr uint32_t TC_STG_BYTES = 128 * 64;     // E4M3 A tile: 128 rows x 64 one-byte reals
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // reduction elements per stage (128 bytes)
@@ -137,6 +139,24 @@ __device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// D(tmem) (+)= A(tmem) * B(smem desc), kind::f16: A's row m in TMEM lane m, its 16-bit K elements
+// packed two per 32-bit column (even element in the low half).
+__device__ __forceinline__ void umma_f16_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+        "r"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -184,12 +204,20 @@ constexpr int tc_cvt_ksub(int bn) { return bn <= 64 ? 2 : 1; }
 
 template <int BN, bool SPLIT, bool CVT = false, bool ADJ = false> struct TcStages {
     static constexpr int KSUB = CVT ? tc_cvt_ksub(BN) : 1;
-    static constexpr int WBUF = CVT ? (KSUB == 2 || BN >= 256 ? 2 : 3) : 0;
-    static constexpr int WA = TC_BM * 128 * KSUB;                      // one widened A tile
+    // TA: the forward E4M3 product with narrow B tiles widens A into tensor memory (four buffers of
+    // KSUB * 32 columns beside the accumulators) instead of shared memory, which leaves shared
+    // memory to the TMA byte tiles, their widening reads and B
+    static constexpr bool TA = CVT && !ADJ && KSUB == 2;
+    // (TA) two independent accumulation chains per tile (even and odd 16-element slices), so that
+    // consecutive narrow MMAs do not wait for each other's accumulation; the epilogue adds them
+    static constexpr int NCH = TA ? 2 : 1;
+    static constexpr int WBUF = TA ? 4 : (CVT ? (KSUB == 2 || BN >= 256 ? 2 : 3) : 0);
+    static constexpr int WA = TA ? 0 : TC_BM * 128 * KSUB;            // one widened A tile in shared memory
+    static constexpr int TCOLS = TA ? 512 : 2 * BN;                     // TMEM columns allocated
     static constexpr int BYT = CVT ? KSUB * (int)TC_STG_BYTES : 0;     // one byte tile of A
     static constexpr int bytes = CVT ? KSUB * BN * 128 : (SPLIT ? 2 : 1) * (TC_BM * 128 + BN * 128);
     static constexpr int fit = (198 * 1024 - WBUF * WA) / bytes;
-    static constexpr int v = CVT ? (BN <= 64 ? 4 : 3) : (fit > 8 ? 8 : fit);
+    static constexpr int v = TA ? (BN <= 32 ? 8 : 6) : (CVT ? (BN <= 64 ? 4 : 3) : (fit > 8 ? 8 : fit));
     static constexpr int byfit = CVT ? (198 * 1024 - WBUF * WA - v * bytes) / BYT : 0;
     static constexpr int NBY = byfit > 16 ? 16 : byfit;
     static_assert(!CVT || NBY >= 2, "byte ring");
@@ -240,7 +268,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // MMA issuer waits for the stage (B) and conv[w] (A), and its commit frees both.  The MMA is
 // the ordinary kind::f16 with FP16 operands.
 template <bool ADJ, int BN, bool SPLIT, bool CVT = false>
-__global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS, 1)
+__global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2, TcArgs a,
                    uint32_t idesc, const int* active, int n_tiles_n, int n_tiles_m, int n_tiles) {
@@ -282,7 +310,10 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     const int t_stride = (int)gridDim.x;
     const unsigned long long wl = a.wait_ns;
 
-    if (warp == 0) tmem_alloc(su32(tmem_slot), 2 * BN);
+    constexpr bool TA = SC::TA;
+    constexpr int NCH = SC::NCH;
+    constexpr uint32_t ACOL = 2 * NCH * BN;                      // (TA) first TMEM column of the A buffers
+    if (warp == 0) tmem_alloc(su32(tmem_slot), SC::TCOLS);
     if (threadIdx.x == 32) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(full0 + 8 * i, 1);
@@ -362,7 +393,10 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             // drain: every copy this thread issued must have landed before the CTA can exit
             for (long q = g > STAGES ? g - STAGES : 0; q < g; ++q)
                 mbar_wait(full0 + 8 * (int)(q % STAGES), (uint32_t)(q / STAGES) & 1, a.err, 2, TC_DRAIN_NS);
-        } else if (CVT && lane == 1) {
+        }
+    } else if (CVT && warp == TC_BYTE_WARP) {
+        // a warp of its own: a blocking wait of this loop never holds up the B producer
+        if (lane == 0) {
             // the byte tiles of A: forward one box of 128 rows x KSUB * 64 bytes, adjoint one box of
             // KSUB * 64 rows x 128 bytes, into slot g % NBY once the converters have released it
             long g = 0;
@@ -378,8 +412,9 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     }
                     const uint32_t st = bybase + y * BYT;
                     mbar_expect_tx(bfull0 + 8 * y, BYT);
-                    if (!ADJ) tma_load_3d(st, &tmA, bfull0 + 8 * y, kb * KSUB * TC_BK, m0, k);
-                    else tma_load_3d(st, &tmA, bfull0 + 8 * y, m0, kb * KSUB * TC_BK, k);
+                    // the byte map counts 4-byte elements along its inner dimension
+                    if (!ADJ) tma_load_3d(st, &tmA, bfull0 + 8 * y, kb * KSUB * TC_BK / 4, m0, k);
+                    else tma_load_3d(st, &tmA, bfull0 + 8 * y, m0 / 4, kb * KSUB * TC_BK, k);
                 }
             }
             for (long q = g > NBY ? g - NBY : 0; q < g; ++q)
@@ -399,7 +434,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                const uint32_t d = tmem + (uint32_t)(buf * NCH * BN);
                 const int kb1 = kb0 + kc < ksteps ? kb0 + kc : ksteps;
                 for (int kb = kb0; kb < kb1; ++kb, ++g) {
                     const int s = (int)(g % STAGES);
@@ -417,6 +452,19 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     const uint32_t sa = CVT ? wbase + w * WA_BYTES : base + s * STAGE_BYTES;
                     const uint32_t sb = CVT ? base + s * STAGE_BYTES : sa + A_BYTES;
                     const uint32_t sa2 = sb + B_BYTES, sb2 = sa2 + A_BYTES;
+                    if constexpr (TA) {
+                        // A in TMEM: 8 columns per 16 reduction elements, alternating chains
+#pragma unroll
+                        for (int kq = 0; kq < KSUB * (TC_BK / 16); ++kq) {
+                            const int kk = kq % (TC_BK / 16), ks = kq / (TC_BK / 16);
+                            const uint64_t bd = sdesc(sb + ks * B_BYTES + kk * 32, 16, 1024);
+                            umma_f16_ta(d + (uint32_t)((kq & 1) * BN), tmem + ACOL + (uint32_t)(w * KSUB * 32 + kq * 8),
+                                        bd, idesc, ((kb - kb0) | (kq >> 1)) != 0 ? 1u : 0u);
+                        }
+                        umma_commit(empty0 + 8 * s);
+                        umma_commit(wfree0 + 8 * w);                          // the A buffer is free
+                        continue;
+                    }
 #pragma unroll
                     for (int kq = 0; kq < KSUB * (TC_BK / 16); ++kq) {
                         // K-major: +32 bytes per 16 elements inside the swizzled row (next 64-element
@@ -443,7 +491,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             umma_commit(drain0);
             mbar_wait(drain0, 0, a.err, 9, TC_DRAIN_NS);
         }
-    } else if (CVT && warp >= TC_THREADS / 32) {
+    } else if (CVT && warp >= TC_THREADS / 32 && warp < TC_BYTE_WARP) {
         // widen each stage's byte tile: item (row R, 8-byte chunk j) -> 16 bytes at row R, chunk
         // j ^ (R % 8) of the 128-byte-swizzled A tile
         const int ct = threadIdx.x - TC_THREADS;
@@ -465,6 +513,9 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
             doff[u][0] = (uint32_t)(off + (((j & 7) ^ (R & 7)) << 4));
             doff[u][1] = (uint32_t)(off + ((((j + 1) & 7) ^ (R & 7)) << 4));
         }
+        // (TA) this thread widens row R of the byte tile (TMEM lane R: warps reach the lane quarter
+        // warp % 4), reduction half hh, into the TMEM A buffer of the step
+        const int tq = warp & 3, hh = (warp - TC_THREADS / 32) >> 2, R = 32 * tq + lane;
         long g = 0;
         bool ok = true;
         for (int tile = t_first; tile < n_tiles && ok; tile += t_stride)
@@ -481,6 +532,34 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     break;
                 }
                 const unsigned char* stg = gbase + (bybase - base) + (size_t)y * BYT;
+                if constexpr (TA) {
+                    // the byte tile arrives 128-byte swizzled: logical 16-byte chunk c of row R sits at
+                    // chunk c ^ (R % 8), so the lanes' row reads spread over all banks
+                    tc_fence_after();
+                    const unsigned char* row = stg + R * 128;
+#pragma unroll
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const int c = 4 * hh + 2 * pass;
+                        const uint4 c0 = *reinterpret_cast<const uint4*>(row + ((c ^ (R & 7)) << 4));
+                        const uint4 c1 = *reinterpret_cast<const uint4*>(row + (((c + 1) ^ (R & 7)) << 4));
+                        const uint32_t b[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                        uint32_t v[16];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            v[2 * i] = e4m3x2_to_h2(b[i]);
+                            v[2 * i + 1] = e4m3x2_to_h2(b[i] >> 16);
+                        }
+                        tmem_st16(tmem + ((uint32_t)(32 * tq) << 16) + ACOL + (uint32_t)(w * KSUB * 32 + 32 * hh + 16 * pass), v);
+                    }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(conv0 + 8 * w);
+                        mbar_arrive(bempty0 + 8 * y);
+                    }
+                    continue;
+                }
                 unsigned char* at = gbase + (wbase - base) + (size_t)w * WA_BYTES;
                 uint4 src[PER];
 #pragma unroll
@@ -614,7 +693,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                 const int buf = (int)(i & 1);
                 if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4, wl))) break;
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NCH * BN);
 #pragma unroll 1
                 for (int c0 = cbeg; c0 < cbeg + BH; c0 += 16) {
                     uint32_t v[16];
@@ -622,6 +701,11 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
                     float f[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
+                    if constexpr (NCH == 2) {
+                        tmem_ld16(taddr + BN + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) f[j] += __uint_as_float(v[j]);
+                    }
                     emit(c0, f);
                 }
                 tc_fence_before();
@@ -634,7 +718,7 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * BN);
+        tmem_dealloc(tmem, SC::TCOLS);
     }
 }
 
@@ -855,18 +939,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map_3d(CUtensorMap* m, const void* ptr, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
-                 uint64_t pitch1_bytes, uint64_t pitch2_bytes, uint32_t b0, uint32_t b1, bool bytes = false) {
+                 uint64_t pitch1_bytes, uint64_t pitch2_bytes, uint32_t b0, uint32_t b1, bool bytes = false,
+                 bool byte_swizzle = false) {
     auto enc = encode_fn();
     if (!enc) return false;
-    cuuint64_t dims[3] = {d0, d1, d2};
+    // E4M3 bytes move as 4-byte elements (four values each): d0 and b0 are given in bytes
+    cuuint64_t dims[3] = {bytes ? d0 / 4 : d0, d1, d2};
     cuuint64_t strides[2] = {pitch1_bytes, pitch2_bytes};
-    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t box[3] = {bytes ? b0 / 4 : b0, b1, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    // 16-bit operands land 128-byte swizzled for the MMA; E4M3 bytes land unswizzled for widening
-    const CUtensorMapDataType dt = bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+    // 16-bit operands land 128-byte swizzled for the MMA; E4M3 bytes land unswizzled for widening in
+    // shared memory, or 128-byte swizzled for the row-per-lane widening into tensor memory
+    const CUtensorMapDataType dt = bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT32
                                          : (bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
     CUresult r = enc(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     bytes ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                     (bytes && !byte_swizzle) ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -892,7 +979,7 @@ bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 gr
                const int* active) {
     static SmemLimit attr;
     const size_t smem = tc_smem_bytes<BN, SPLIT, CVT, ADJ>();
-    constexpr int THREADS = CVT ? TC_THREADS + TC_CVT_THREADS : TC_THREADS;
+    constexpr int THREADS = CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_THREADS;
     auto kern = tc_gemm_kernel<ADJ, BN, SPLIT, CVT>;
     attr.ensure(kern, (int)smem);
     const int n_tiles = (int)grid.x * (int)grid.y * (int)grid.z;
@@ -984,7 +1071,8 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         const void* ga = G + h * glo;
         const void* gb = Bp + h * blo;
         if (!adjoint)
-            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, fa0, 128, e4m3) &&
+            ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, fa0, 128, e4m3,
+                             e4m3 && ks == 2) &&
                  make_map_3d(&maps[2 * h + 1], gb, bf16, kp, rows_pad, p->nf, kp * 2, kp * 2 * rows_pad, 64, bbox);
         else
             ok = make_map_3d(&maps[2 * h], ga, bf16, kp, p->nr, p->nf, kp * ab, kp * ab * p->nr, aa0, aa1, e4m3) &&
