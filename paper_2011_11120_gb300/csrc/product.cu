@@ -635,14 +635,19 @@ __global__ void __launch_bounds__(256) cgemm_simt(
     const float* sck = gscale + (size_t)k * nr;
     const float2* Bk = B + (size_t)k * K * ldb + voff_b;
     const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
-    // Two-level sums: each chunk of GCHUNK reduction tiles accumulates in part, which is then added
-    // to acc, so a float32 sum over K terms carries about (GCHUNK * GBK + K / (GCHUNK * GBK)) roundings
-    // per output instead of K.
-    float2 acc[4][4], part[4][4];
+    // Two-level sums: each chunk of GCHUNK reduction tiles accumulates in part (registers), which is
+    // then added to the thread's running totals (shared memory, one slot per output and thread, so the
+    // registers stay at one accumulator set), so a float32 sum over K terms carries about
+    // (GCHUNK * GBK + K / (GCHUNK * GBK)) roundings per output instead of K.
+    __shared__ float2 tot[16][256];
+    float2 part[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = part[i][j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < 4; ++j) {
+            part[i][j] = make_float2(0.f, 0.f);
+            tot[4 * i + j][tid] = make_float2(0.f, 0.f);
+        }
 
     for (int kt = 0; kt < K; kt += GBK) {
         // A tile: GBK x TBM complex values, 64 rows (forward) or 64 columns (adjoint) per round
@@ -699,7 +704,7 @@ __global__ void __launch_bounds__(256) cgemm_simt(
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    acc[i][j] = cadd(acc[i][j], part[i][j]);
+                    tot[4 * i + j][tid] = cadd(tot[4 * i + j][tid], part[i][j]);
                     part[i][j] = make_float2(0.f, 0.f);
                 }
         }
@@ -713,7 +718,7 @@ __global__ void __launch_bounds__(256) cgemm_simt(
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + TXN * j;
             if (n < N)
-                Cm[((size_t)k * M + m) * ldc + voff_c + n] = make_float2(acc[i][j].x * sc, acc[i][j].y * sc);
+                Cm[((size_t)k * M + m) * ldc + voff_c + n] = make_float2(tot[4 * i + j][tid].x * sc, tot[4 * i + j][tid].y * sc);
         }
     }
 }
