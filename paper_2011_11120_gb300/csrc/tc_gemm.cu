@@ -139,6 +139,15 @@ __device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uin
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// D(tmem) (+)= A(smem desc) * B(smem desc), kind::f8f6f4 (K = 32 per instruction), FP32 accumulation.
+__device__ __forceinline__ void umma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
 // D(tmem) (+)= A(tmem) * B(smem desc), kind::f16: A's row m in TMEM lane m, its 16-bit K elements
 // packed two per 32-bit column (even element in the low half).
 __device__ __forceinline__ void umma_f16_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -722,17 +731,189 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
     }
 }
 
+// ------------------------------------------------------------------ E4M3 forward, operands swapped
+// With few columns the product above issues M = 128 x N = 2 ncol MMAs (N = 32 at 16 columns), and
+// their instruction rate, not the kernel's bytes, bounds it.  Here the kernel is the N = 256
+// operand, read as E4M3 bytes straight from its copy (kind::f8f6f4, no widening), and the spectra
+// are the M operand: each real row of the B operand above (row 2n: (Re, -Im), row 2n + 1: (Im, Re)
+// of column n along s) is split exactly into three E4M3 terms,
+//     sigma x = h0 + h1 / 16 + h2 / 256   (round to nearest even at each step),
+// stacked as rows t * R + row (R = 2 ncol, 3R <= 128) of one 128-row tile, so one MMA per 32
+// reduction elements forms all three partial products, in different TMEM lanes.  The epilogue adds
+// them with their weights (about 12 significant bits of the spectra, finer than the FP16 rounding
+// of the 16-bit path), applies the row scale of G and 1 / sigma, and writes Y[k][r][n].
+constexpr int F8_BN = 256;                          // kernel rows per tile (N of the MMA)
+constexpr int F8_STAGES = 4;
+constexpr uint32_t F8_A_BYTES = TC_BM * 128;        // stacked spectra terms: 128 rows x 128 bytes
+constexpr uint32_t F8_B_BYTES = F8_BN * 128;        // kernel bytes: 256 rows x 128 bytes
+constexpr uint32_t F8_STAGE = F8_A_BYTES + F8_B_BYTES;
+constexpr int F8_TERMS = 3;
+constexpr int F8_MAX_COLS = TC_BM / (2 * F8_TERMS);   // 21 columns: 3 terms x 42 rows fit 128
+constexpr int F8_LD = 17;                           // epilogue staging row pitch (floats)
+
+constexpr size_t f8_smem_bytes() {
+    // + alignment, barriers, and two 128 x 17-float staging tiles (one per column half)
+    return (size_t)F8_STAGES * F8_STAGE + 1024 + 256 + 2 * TC_BM * F8_LD * 4;
+}
+
+// Persistent CTA (one per SM) over tiles (frequency k, kernel rows n0 .. n0 + 255): warp 0 streams
+// each 128-byte reduction slice of the stacked spectra (128 rows) and of the kernel (256 rows) with
+// TMA, warp 1 issues four MMAs per slice into one of two TMEM accumulators, warps 2..9 read the
+// other back (4 lane quarters x 2 column halves), add the terms through shared memory and store.
+// Every wait is bounded as in tc_gemm_kernel.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_f8_fwd_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
+                     uint32_t idesc, const int* active, int n_tiles_n, int n_tiles) {
+    if (active && *active == 0) return;
+    const int ksteps = a.kstages;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = su32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - raw);
+    // full[S], empty[S], acc_full[2], acc_empty[2], tmem slot, drain; staging tiles 256 bytes on
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + F8_STAGES * F8_STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * F8_STAGES + 4);
+    float* stg = reinterpret_cast<float*>(bars + 32);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + F8_STAGES);
+    const uint32_t accf0 = su32(bars + 2 * F8_STAGES), acce0 = su32(bars + 2 * F8_STAGES + 2);
+    const uint32_t drain0 = su32(bars + 2 * F8_STAGES + 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t_first = (int)blockIdx.x, t_stride = (int)gridDim.x;
+    const unsigned long long wl = a.wait_ns;
+
+    if (warp == 0) tmem_alloc(su32(tmem_slot), 2 * F8_BN);
+    if (threadIdx.x == 32) {
+        for (int i = 0; i < F8_STAGES; ++i) {
+            mbar_init(full0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(accf0 + 8 * i, 1);
+            mbar_init(acce0 + 8 * i, 256);
+        }
+        mbar_init(drain0, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long g = 0;
+            bool ok = true;
+            for (int tile = t_first; tile < n_tiles && ok; tile += t_stride) {
+                const int k = tile / n_tiles_n, n0 = (tile - k * n_tiles_n) * F8_BN;
+                for (int kb = 0; kb < ksteps; ++kb, ++g) {
+                    const int s = (int)(g % F8_STAGES);
+                    if (g >= F8_STAGES &&
+                        !mbar_wait(empty0 + 8 * s, (uint32_t)(g / F8_STAGES - 1) & 1, a.err, 1, wl)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sa = base + s * F8_STAGE;
+                    mbar_expect_tx(full0 + 8 * s, F8_STAGE);
+                    // both maps count 4-byte elements along the reduction
+                    tma_load_3d(sa, &tmA, full0 + 8 * s, kb * 32, 0, k);
+                    tma_load_3d(sa + F8_A_BYTES, &tmB, full0 + 8 * s, kb * 32, n0, k);
+                }
+            }
+            // drain: every copy this thread issued must have landed before the CTA can exit
+            for (long q = g > F8_STAGES ? g - F8_STAGES : 0; q < g; ++q)
+                mbar_wait(full0 + 8 * (int)(q % F8_STAGES), (uint32_t)(q / F8_STAGES) & 1, a.err, 2, TC_DRAIN_NS);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            long g = 0, i = 0;
+            bool ok = true;
+            for (int tile = t_first; tile < n_tiles && ok; tile += t_stride, ++i) {
+                const int buf = (int)(i & 1);
+                if (i >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((i >> 1) - 1) & 1, a.err, 5, wl)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * F8_BN);
+                for (int kb = 0; kb < ksteps; ++kb, ++g) {
+                    const int s = (int)(g % F8_STAGES);
+                    if (!mbar_wait(full0 + 8 * s, (uint32_t)(g / F8_STAGES) & 1, a.err, 3, wl)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * F8_STAGE, sb = sa + F8_A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)      // 32 one-byte elements = 32 bytes per step
+                        umma_f8(d, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
+                                (kb | kk) != 0 ? 1u : 0u);
+                    umma_commit(empty0 + 8 * s);
+                }
+                umma_commit(accf0 + 8 * buf);
+            }
+            // drain: every MMA this thread issued has completed before TMEM is freed
+            umma_commit(drain0);
+            mbar_wait(drain0, 0, a.err, 9, TC_DRAIN_NS);
+        }
+    } else {
+        const int q = warp & 3, half = (warp - 2) >> 2;       // lane quarter, column half
+        const int ht = (warp - 2 - 4 * half) * 32 + lane;     // 0..127 within the half
+        const int R = 2 * a.ncol;
+        float* st = stg + half * (TC_BM * F8_LD);
+        float* rowp = st + (q * 32 + lane) * F8_LD;
+        long i = 0;
+        for (int tile = t_first; tile < n_tiles; tile += t_stride, ++i) {
+            const int k = tile / n_tiles_n, n0 = (tile - k * n_tiles_n) * F8_BN;
+            const int buf = (int)(i & 1);
+            if (!epilogue_all(mbar_wait(accf0 + 8 * buf, (uint32_t)(i >> 1) & 1, a.err, 4, wl))) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * F8_BN + half * 128);
+            const float* isg = a.inv_sigma + (size_t)k * a.ncol;
+            const float* gsk = a.gscale + (size_t)k * a.nr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(taddr + c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) rowp[j] = __uint_as_float(v[j]);
+                asm volatile("bar.sync %0, 128;" ::"r"(3 + half) : "memory");
+                for (int idx = ht; idx < a.ncol * 16; idx += 128) {
+                    const int n = idx % a.ncol, c = idx / a.ncol;
+                    const int r = n0 + half * 128 + c0 + c;
+                    const float* p0 = st + (2 * n) * F8_LD + c;           // term 0, real row 2n
+                    const float re = p0[0] + 0.0625f * p0[R * F8_LD] + 0.00390625f * p0[2 * R * F8_LD];
+                    const float im = p0[F8_LD] + 0.0625f * p0[(R + 1) * F8_LD] + 0.00390625f * p0[(2 * R + 1) * F8_LD];
+                    if (r < a.nout) {
+                        const float f = gsk[r] * isg[n];
+                        a.out[((size_t)k * a.nout + r) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
+                    }
+                }
+                asm volatile("bar.sync %0, 128;" ::"r"(3 + half) : "memory");
+            }
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * buf);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * F8_BN);
+    }
+}
+
 // ------------------------------------------------------------------ B-operand preparation
 template <typename T> __device__ __forceinline__ T cvt(float x);
 template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
-__device__ __forceinline__ float pow2_scale(float maxabs) {
+// Power of two with maxabs * scale < 2^emax (14 for the 16-bit operands, 8 for E4M3 terms).
+__device__ __forceinline__ float pow2_scale(float maxabs, int emax) {
     if (!(maxabs > 0.f) || !isfinite(maxabs)) return 1.f;
     int e;
     frexpf(maxabs, &e);           // maxabs < 2^e
     e = e < -100 ? -100 : e;      // scale and reciprocal stay normal floats
-    return ldexpf(1.f, 14 - e);   // maxabs * scale < 2^14
+    return ldexpf(1.f, emax - e);
 }
 
 // Packed pair of 16-bit values (lo element first in memory).
@@ -756,7 +937,7 @@ constexpr int PREP_ROWS = 256;    // spatial rows per staged block (one per thre
 // power-of-two scale of each column to sig[] and its reciprocal to inv_sigma.
 __device__ __forceinline__ void prep_scales(const float2* __restrict__ Xk, int ldi, int nrows, int n0, int ncol,
                                             const float* __restrict__ rw, float* red, float* sig,
-                                            float* __restrict__ inv_sigma_k) {
+                                            float* __restrict__ inv_sigma_k, int emax = 14) {
     const int j0 = threadIdx.x & 7;
     float m = 0.f;
     if (n0 + j0 < ncol) {
@@ -789,7 +970,7 @@ __device__ __forceinline__ void prep_scales(const float2* __restrict__ Xk, int l
     if (threadIdx.x < PREP_COLS) {
         float mm = 0.f;
         for (int i = threadIdx.x; i < 256; i += PREP_COLS) mm = fmaxf(mm, red[i]);
-        const float sc = pow2_scale(mm);
+        const float sc = pow2_scale(mm, emax);
         sig[threadIdx.x] = sc;
         if (n0 + (int)threadIdx.x < ncol) inv_sigma_k[n0 + threadIdx.x] = 1.f / sc;
     }
@@ -869,6 +1050,67 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
                     const T tlx = cvt<T>(lx), tly = cvt<T>(ly);
                     r0[plane2] = Pair2<T>::make(tlx, cvt<T>(-ly));
                     r0[plane2 + kp2] = Pair2<T>::make(tly, tlx);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Exact split of v (|v| < 2^8) into three E4M3 terms v = h0 + h1 / 16 + h2 / 256 + e, each term the
+// nearest E4M3 value of the scaled remainder (|e| <= 2^-12 |v| for normal values; the remainders are
+// exact in float32).
+__device__ __forceinline__ void e4m3_split3(float v, uint32_t (&h)[3]) {
+    float r = v;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3);
+        h[t] = q;
+        const float back = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+        r = (r - back) * 16.f;
+    }
+}
+
+// forward, E4M3 operands swapped: X[k][s][ldi] (voff, ncol columns) -> A[k][t * R + row][2 * ldg]
+// bytes (R = 2 ncol; row 2n: (Re, -Im), row 2n + 1: (Im, Re) of column n along s, split into the
+// three terms t of e4m3_split3 after the power-of-two column scale), inv_sigma[k][n].
+__global__ void __launch_bounds__(256) tc_prep_fwd_f8(const float2* __restrict__ X, int ldi, int voff, int ns,
+                                                      int ncol, int ldg, uint8_t* __restrict__ A,
+                                                      float* __restrict__ inv_sigma, const int* active) {
+    if (active && *active == 0) return;
+    const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
+    const float2* Xk = X + (size_t)k * ns * ldi + voff;
+    __shared__ float red[256];
+    __shared__ float sig[PREP_COLS];
+    __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    float2 pv[PREP_PER];
+    float pw[PREP_PER];
+    prep_load(Xk, ldi, ns, 0, n0, ncol, nullptr, pv, pw);
+    prep_scales(Xk, ldi, ns, n0, ncol, nullptr, red, sig, inv_sigma + (size_t)k * ncol, 8);
+    const int R = 2 * ncol;
+    const size_t kp = 2 * (size_t)ldg;
+    uint16_t* Ak = reinterpret_cast<uint16_t*>(A + (size_t)k * F8_TERMS * R * kp);   // two bytes per s
+    const size_t row2 = kp / 2;
+    for (int s0 = 0; s0 < ldg; s0 += PREP_ROWS) {
+        prep_put(pv, pw, sig, tile);
+        __syncthreads();
+        if (s0 + PREP_ROWS < ldg) prep_load(Xk, ldi, ns, s0 + PREP_ROWS, n0, ncol, nullptr, pv, pw);
+        const int s = s0 + threadIdx.x;
+        if (s < ldg) {
+#pragma unroll
+            for (int j = 0; j < PREP_COLS; ++j) {
+                const int n = n0 + j;
+                if (n >= ncol) break;
+                const float2 v = tile[threadIdx.x][j];
+                uint32_t hx[3], hy[3], hny[3];
+                e4m3_split3(v.x, hx);
+                e4m3_split3(v.y, hy);
+                e4m3_split3(-v.y, hny);
+#pragma unroll
+                for (int t = 0; t < F8_TERMS; ++t) {
+                    uint16_t* r0 = Ak + (size_t)(t * R + 2 * n) * row2 + s;
+                    r0[0] = (uint16_t)(hx[t] | (hny[t] << 8));          // (Re, -Im)
+                    r0[row2] = (uint16_t)(hy[t] | (hx[t] << 8));        // (Im, Re)
                 }
             }
         }
@@ -989,6 +1231,17 @@ bool launch_tc(const CUtensorMap* maps, const TcArgs& a, uint32_t idesc, dim3 gr
     return true;
 }
 
+// MDC_E4M3_SWAP=0 in the environment keeps narrow E4M3 forward products on the widening kernel
+// (for comparisons).
+bool f8_swap_allowed() {
+    static int env = -1;
+    if (env < 0) {
+        const char* e = getenv("MDC_E4M3_SWAP");
+        env = (e && e[0] == '0') ? 0 : 1;
+    }
+    return env == 1;
+}
+
 }  // namespace
 
 int tc_rows_pad(int ncol) {
@@ -998,7 +1251,10 @@ int tc_rows_pad(int ncol) {
 }
 
 size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
-    const size_t rows = (size_t)tc_rows_pad(ncol);
+    size_t rows = (size_t)tc_rows_pad(ncol);
+    // E4M3 forward products of few columns take three byte rows per real row (2 ncol real rows):
+    // 6 ncol bytes = 3 ncol 16-bit elements per reduction element
+    if (p->storage == MDC_CE4M3 && 3 * (size_t)ncol > rows) rows = 3 * (size_t)ncol;
     const size_t kfwd = 2 * (size_t)p->ldg;
     const size_t kadj = (size_t)round_up(p->nr, 8);
     return (size_t)p->nf * rows * (kfwd > kadj ? kfwd : kadj);
@@ -1026,6 +1282,42 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const size_t plane = (size_t)p->nf * rows_pad * (adjoint ? (size_t)kpitch : (size_t)kp);
     dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
     std::optional<LaunchScope> scope;
+    if (e4m3 && !adjoint && !bn_override && ncol <= F8_MAX_COLS && f8_swap_allowed()) {
+        // operands swapped: spectra split into three E4M3 terms, kernel bytes as the wide operand
+        if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
+        dim3 pf((unsigned)((ncol + PREP_COLS - 1) / PREP_COLS), (unsigned)p->nf);
+        tc_prep_fwd_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, (uint8_t*)p->tcB, p->tcSigma,
+                                          active);
+        scope.reset();
+        const int arows = F8_TERMS * 2 * ncol;
+        CUtensorMap mA, mB;
+        if (!make_map_3d(&mA, p->tcB, false, kp, (uint64_t)arows, p->nf, kp, kp * arows, 128, TC_BM, true, true) ||
+            !make_map_3d(&mB, p->G, false, kp, p->nr, p->nf, kp, kp * p->nr, 128, F8_BN, true, true))
+            return false;
+        TcArgs a{};
+        a.kstages = (int)(kp / 128);
+        a.nout = p->nr;
+        a.nr = p->nr;
+        a.ncol = ncol;
+        a.inv_sigma = p->tcSigma;
+        a.gscale = p->gscale;
+        a.out = out;
+        a.ldo = ldo;
+        a.voff_o = voff_o;
+        a.err = p->err_flag;
+        a.wait_ns = p->wait_ns;
+        // kind::f8f6f4: D float32, A and B E4M3 (format 0), both K-major, N = 256, M = 128
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(F8_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+        const int ntn = (p->nr + F8_BN - 1) / F8_BN;
+        const int n_tiles = ntn * p->nf;
+        const size_t smem = f8_smem_bytes();
+        static SmemLimit attr;
+        attr.ensure(tc_f8_fwd_kernel, (int)smem);
+        const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
+        if (scoped) scope.emplace(p, s, MDC_KC_PRODUCT_FWD);
+        tc_f8_fwd_kernel<<<ctas, TC_THREADS, smem, s>>>(mA, mB, a, idesc, active, ntn, n_tiles);
+        return true;
+    }
     if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
 #define MDC_PREP(KER, T, SP, ...) KER<T, SP><<<pg, 256, 0, s>>>(__VA_ARGS__, active, plane)
     if (!adjoint) {

@@ -71,10 +71,11 @@ U16 = 2.0 ** -11     # FP16 unit roundoff
 
 @pytest.mark.parametrize("nt,nr,ns,nf,nv", CASES)
 def test_tc_e4m3_widened_matches_oracle(nt, nr, ns, nf, nv):
-    """E4M3 kernel copy on tensor cores: TMA brings the kernel as bytes and the GEMM widens them to
-    FP16 in shared memory (exactly: E4M3 is a subset of FP16), so against the FP64 oracle on the
-    dequantised E4M3 kernel the only error is the FP16 rounding of the spectra (tolerance 4 u16),
-    like the FP16 copy's."""
+    """E4M3 kernel copy on tensor cores: TMA brings the kernel as bytes; the GEMM widens them to
+    FP16 (exactly: E4M3 is a subset of FP16), or, for forward products of at most 21 columns, feeds
+    them unwidened to E4M3 MMAs against a three-term E4M3 split of the spectra.  Against the FP64
+    oracle on the dequantised E4M3 kernel the only error is the rounding of the spectra (FP16, or
+    about 12 bits for the split: tolerance 4 u16 for both), like the FP16 copy's."""
     G, x, y, yg, xg = run("ce4m3", nt, nr, ns, nf, nv)
     Gq = dequantised(G, "ce4m3")
     ef = rel(yg, omdc.forward(Gq, x, 0.004, 400.0))
