@@ -731,17 +731,22 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
     }
 }
 
-// ------------------------------------------------------------------ E4M3 forward, operands swapped
+// ------------------------------------------------------------------ E4M3 products, operands swapped
 // With few columns the product above issues M = 128 x N = 2 ncol MMAs (N = 32 at 16 columns), and
 // their instruction rate, not the kernel's bytes, bounds it.  Here the kernel is the N = 256
 // operand, read as E4M3 bytes straight from its copy (kind::f8f6f4, no widening), and the spectra
-// are the M operand: each real row of the B operand above (row 2n: (Re, -Im), row 2n + 1: (Im, Re)
-// of column n along s) is split exactly into three E4M3 terms,
+// are the M operand: each real row of the B operand above is split exactly into three E4M3 terms,
 //     sigma x = h0 + h1 / 16 + h2 / 256   (round to nearest even at each step),
 // stacked as rows t * R + row (R = 2 ncol, 3R <= 128) of one 128-row tile, so one MMA per 32
 // reduction elements forms all three partial products, in different TMEM lanes.  The epilogue adds
 // them with their weights (about 12 significant bits of the spectra, finer than the FP16 rounding
-// of the 16-bit path), applies the row scale of G and 1 / sigma, and writes Y[k][r][n].
+// of the 16-bit path) and applies the scales.
+//   forward  D'[t R + 2n + c][r]  = sum_K' A[t R + 2n + c][K'] G^[r][K']   (G^ K-major, N = r)
+//            rows 2n: (Re, -Im), 2n + 1: (Im, Re) of X column n along s; Y[k][r][n] = D'[2n][r] +
+//            i D'[2n + 1][r] (term-weighted), times G's row scale and 1 / sigma.
+//   adjoint  D'[t R + 2n + c][m] = sum_r A[t R + 2n + c][r] G^[r][m]      (G^ MN-major, N = m = 2s + c')
+//            rows 2n: Re, 2n + 1: Im of Y column n times G's row scale, along r;
+//            X'[k][s][n] = (D'[2n][2s] + D'[2n+1][2s+1]) + i (D'[2n+1][2s] - D'[2n][2s+1]), times 1 / sigma.
 constexpr int F8_BN = 256;                          // kernel rows per tile (N of the MMA)
 constexpr int F8_STAGES = 4;
 constexpr uint32_t F8_A_BYTES = TC_BM * 128;        // stacked spectra terms: 128 rows x 128 bytes
@@ -756,14 +761,17 @@ constexpr size_t f8_smem_bytes() {
     return (size_t)F8_STAGES * F8_STAGE + 1024 + 256 + 2 * TC_BM * F8_LD * 4;
 }
 
-// Persistent CTA (one per SM) over tiles (frequency k, kernel rows n0 .. n0 + 255): warp 0 streams
-// each 128-byte reduction slice of the stacked spectra (128 rows) and of the kernel (256 rows) with
-// TMA, warp 1 issues four MMAs per slice into one of two TMEM accumulators, warps 2..9 read the
-// other back (4 lane quarters x 2 column halves), add the terms through shared memory and store.
-// Every wait is bounded as in tc_gemm_kernel.
+// Persistent CTA (one per SM) over tiles (frequency k, N columns n0 .. n0 + 255: kernel rows forward,
+// interleaved kernel columns adjoint): warp 0 streams each 128-element reduction slice of the stacked
+// spectra (128 rows x 128 bytes) and of the kernel (forward 256 rows x 128 bytes; adjoint 128 rows
+// x 2 x 128 bytes, the two 128-column halves 16 KB apart) with TMA, warp 1 issues four MMAs per
+// slice into one of two TMEM accumulators, warps 2..9 read the other back (4 lane quarters x 2
+// column halves), add the terms through shared memory and store.  Every wait is bounded as in
+// tc_gemm_kernel.
+template <bool ADJ>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_f8_fwd_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
-                     uint32_t idesc, const int* active, int n_tiles_n, int n_tiles) {
+    tc_f8_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a,
+                 uint32_t idesc, const int* active, int n_tiles_n, int n_tiles) {
     if (active && *active == 0) return;
     const int ksteps = a.kstages;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -814,9 +822,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t sa = base + s * F8_STAGE;
                     mbar_expect_tx(full0 + 8 * s, F8_STAGE);
-                    // both maps count 4-byte elements along the reduction
+                    // the maps count 4-byte elements along their inner (byte) dimension
                     tma_load_3d(sa, &tmA, full0 + 8 * s, kb * 32, 0, k);
-                    tma_load_3d(sa + F8_A_BYTES, &tmB, full0 + 8 * s, kb * 32, n0, k);
+                    if (!ADJ) {
+                        tma_load_3d(sa + F8_A_BYTES, &tmB, full0 + 8 * s, kb * 32, n0, k);
+                    } else {
+                        tma_load_3d(sa + F8_A_BYTES, &tmB, full0 + 8 * s, n0 / 4, kb * 128, k);
+                        tma_load_3d(sa + F8_A_BYTES + F8_B_BYTES / 2, &tmB, full0 + 8 * s, (n0 + 128) / 4, kb * 128, k);
+                    }
                 }
             }
             // drain: every copy this thread issued must have landed before the CTA can exit
@@ -844,9 +857,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const uint32_t sa = base + s * F8_STAGE, sb = sa + F8_A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)      // 32 one-byte elements = 32 bytes per step
-                        umma_f8(d, sdesc(sa + kk * 32, 16, 1024), sdesc(sb + kk * 32, 16, 1024), idesc,
-                                (kb | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        // 32 reduction elements per MMA: +32 bytes along a K-major row, or +32 rows of
+                        // the MN-major kernel tile (whose two 128-column halves are 16 KB apart)
+                        const uint64_t bd = ADJ ? sdesc(sb + kk * 4096, F8_B_BYTES / 2, 1024)
+                                                : sdesc(sb + kk * 32, 16, 1024);
+                        umma_f8(d, sdesc(sa + kk * 32, 16, 1024), bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                    }
                     umma_commit(empty0 + 8 * s);
                 }
                 umma_commit(accf0 + 8 * buf);
@@ -869,7 +886,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * F8_BN + half * 128);
             const float* isg = a.inv_sigma + (size_t)k * a.ncol;
-            const float* gsk = a.gscale + (size_t)k * a.nr;
+            const float* gsk = ADJ ? nullptr : a.gscale + (size_t)k * a.nr;
 #pragma unroll 1
             for (int c0 = 0; c0 < 128; c0 += 16) {
                 uint32_t v[16];
@@ -877,15 +894,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) rowp[j] = __uint_as_float(v[j]);
                 asm volatile("bar.sync %0, 128;" ::"r"(3 + half) : "memory");
-                for (int idx = ht; idx < a.ncol * 16; idx += 128) {
-                    const int n = idx % a.ncol, c = idx / a.ncol;
-                    const int r = n0 + half * 128 + c0 + c;
-                    const float* p0 = st + (2 * n) * F8_LD + c;           // term 0, real row 2n
-                    const float re = p0[0] + 0.0625f * p0[R * F8_LD] + 0.00390625f * p0[2 * R * F8_LD];
-                    const float im = p0[F8_LD] + 0.0625f * p0[(R + 1) * F8_LD] + 0.00390625f * p0[(2 * R + 1) * F8_LD];
-                    if (r < a.nout) {
-                        const float f = gsk[r] * isg[n];
-                        a.out[((size_t)k * a.nout + r) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
+                if (!ADJ) {
+                    for (int idx = ht; idx < a.ncol * 16; idx += 128) {
+                        const int n = idx % a.ncol, c = idx / a.ncol;
+                        const int r = n0 + half * 128 + c0 + c;
+                        const float* p0 = st + (2 * n) * F8_LD + c;           // term 0, real row 2n
+                        const float re = p0[0] + 0.0625f * p0[R * F8_LD] + 0.00390625f * p0[2 * R * F8_LD];
+                        const float im =
+                            p0[F8_LD] + 0.0625f * p0[(R + 1) * F8_LD] + 0.00390625f * p0[(2 * R + 1) * F8_LD];
+                        if (r < a.nout) {
+                            const float f = gsk[r] * isg[n];
+                            a.out[((size_t)k * a.nout + r) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
+                        }
+                    }
+                } else {
+                    // chunk columns 2j, 2j + 1 are the interleaved parts of output row s = (n0 + ...) / 2 + j
+                    for (int idx = ht; idx < a.ncol * 8; idx += 128) {
+                        const int n = idx % a.ncol, j = idx / a.ncol;
+                        const int so = (n0 + half * 128 + c0) / 2 + j;
+                        float re = 0.f, im = 0.f;
+#pragma unroll
+                        for (int t = F8_TERMS - 1; t >= 0; --t) {
+                            const float* p0 = st + (t * R + 2 * n) * F8_LD + 2 * j;
+                            const float w = t == 0 ? 1.f : (t == 1 ? 0.0625f : 0.00390625f);
+                            re += w * (p0[0] + p0[F8_LD + 1]);
+                            im += w * (p0[F8_LD] - p0[1]);
+                        }
+                        if (so < a.nout) {
+                            const float f = isg[n];
+                            a.out[((size_t)k * a.nout + so) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
+                        }
                     }
                 }
                 asm volatile("bar.sync %0, 128;" ::"r"(3 + half) : "memory");
@@ -1118,6 +1156,57 @@ __global__ void __launch_bounds__(256) tc_prep_fwd_f8(const float2* __restrict__
     }
 }
 
+// adjoint, E4M3 operands swapped: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] ->
+// A[k][t * R + row][kpitch] bytes (row 2n: Re, 2n + 1: Im of column n along r, split into the three
+// terms t of e4m3_split3 after the power-of-two column scale; zero for r >= nr), inv_sigma[k][n].
+__global__ void __launch_bounds__(256) tc_prep_adj_f8(const float2* __restrict__ Y, int ldi, int voff, int nr,
+                                                      int ncol, const float* __restrict__ gscale, int kpitch,
+                                                      uint8_t* __restrict__ A, float* __restrict__ inv_sigma,
+                                                      const int* active) {
+    if (active && *active == 0) return;
+    const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
+    const float2* Yk = Y + (size_t)k * nr * ldi + voff;
+    const float* gs = gscale + (size_t)k * nr;
+    __shared__ float red[256];
+    __shared__ float sig[PREP_COLS];
+    __shared__ float2 tile[PREP_ROWS][PREP_COLS + 1];
+    float2 pv[PREP_PER];
+    float pw[PREP_PER];
+    prep_load(Yk, ldi, nr, 0, n0, ncol, gs, pv, pw);
+    prep_scales(Yk, ldi, nr, n0, ncol, gs, red, sig, inv_sigma + (size_t)k * ncol, 8);
+    const int R = 2 * ncol;
+    uint16_t* Ak = reinterpret_cast<uint16_t*>(A + (size_t)k * F8_TERMS * R * kpitch);   // two bytes per r pair
+    const size_t kq = (size_t)kpitch / 2;
+    for (int r0 = 0; r0 < kpitch; r0 += PREP_ROWS) {
+        prep_put(pv, pw, sig, tile);
+        __syncthreads();
+        if (r0 + PREP_ROWS < kpitch) prep_load(Yk, ldi, nr, r0 + PREP_ROWS, n0, ncol, gs, pv, pw);
+        // threads 0..127 each take rows r0 + 2t, r0 + 2t + 1 for columns 0..3, threads 128..255 columns 4..7
+        const int t = threadIdx.x & 127, jb = (threadIdx.x >> 7) * (PREP_COLS / 2);
+        const int r = r0 + 2 * t;
+        if (r < kpitch) {
+#pragma unroll
+            for (int jj = 0; jj < PREP_COLS / 2; ++jj) {
+                const int j = jb + jj, n = n0 + j;
+                if (n >= ncol) continue;
+                const float2 va = tile[2 * t][j], vb = tile[2 * t + 1][j];
+                uint32_t ax[3], bx[3], ay[3], by[3];
+                e4m3_split3(va.x, ax);
+                e4m3_split3(vb.x, bx);
+                e4m3_split3(va.y, ay);
+                e4m3_split3(vb.y, by);
+#pragma unroll
+                for (int tt = 0; tt < F8_TERMS; ++tt) {
+                    uint16_t* q0 = Ak + (size_t)(tt * R + 2 * n) * kq + (r >> 1);
+                    q0[0] = (uint16_t)(ax[tt] | (bx[tt] << 8));           // Re at r, r + 1
+                    q0[kq] = (uint16_t)(ay[tt] | (by[tt] << 8));          // Im at r, r + 1
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // adjoint: Y[k][r][ldi] (voff, ncol columns) * gscale[k][r] -> BT[k][n''][kpitch], inv_sigma[k][n].
 // Real rows 2n and 2n + 1 hold Re and Im of column n along r; each thread writes two adjacent r.
 template <typename T, bool SPLIT>
@@ -1256,7 +1345,7 @@ size_t tc_scratch_elems(const mdc_plan* p, int ncol) {
     // 6 ncol bytes = 3 ncol 16-bit elements per reduction element
     if (p->storage == MDC_CE4M3 && 3 * (size_t)ncol > rows) rows = 3 * (size_t)ncol;
     const size_t kfwd = 2 * (size_t)p->ldg;
-    const size_t kadj = (size_t)round_up(p->nr, 8);
+    const size_t kadj = (size_t)round_up(p->nr, p->storage == MDC_CE4M3 ? 16 : 8);
     return (size_t)p->nf * rows * (kfwd > kadj ? kfwd : kadj);
 }
 
@@ -1282,21 +1371,27 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
     const size_t plane = (size_t)p->nf * rows_pad * (adjoint ? (size_t)kpitch : (size_t)kp);
     dim3 pg((unsigned)(rows_pad / 16), (unsigned)p->nf);
     std::optional<LaunchScope> scope;
-    if (e4m3 && !adjoint && !bn_override && ncol <= F8_MAX_COLS && f8_swap_allowed()) {
+    if (e4m3 && !bn_override && ncol <= F8_MAX_COLS && f8_swap_allowed()) {
         // operands swapped: spectra split into three E4M3 terms, kernel bytes as the wide operand
+        const int arows = F8_TERMS * 2 * ncol;
+        const uint64_t kpf = (uint64_t)round_up(p->nr, 16);     // adjoint reduction pitch (bytes)
         if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
         dim3 pf((unsigned)((ncol + PREP_COLS - 1) / PREP_COLS), (unsigned)p->nf);
-        tc_prep_fwd_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, (uint8_t*)p->tcB, p->tcSigma,
-                                          active);
+        if (!adjoint)
+            tc_prep_fwd_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, (uint8_t*)p->tcB,
+                                              p->tcSigma, active);
+        else
+            tc_prep_adj_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, (int)kpf, (uint8_t*)p->tcB,
+                                              p->tcSigma, active);
         scope.reset();
-        const int arows = F8_TERMS * 2 * ncol;
         CUtensorMap mA, mB;
-        if (!make_map_3d(&mA, p->tcB, false, kp, (uint64_t)arows, p->nf, kp, kp * arows, 128, TC_BM, true, true) ||
-            !make_map_3d(&mB, p->G, false, kp, p->nr, p->nf, kp, kp * p->nr, 128, F8_BN, true, true))
+        const uint64_t ka = adjoint ? kpf : kp;
+        if (!make_map_3d(&mA, p->tcB, false, ka, (uint64_t)arows, p->nf, ka, ka * arows, 128, TC_BM, true, true) ||
+            !make_map_3d(&mB, p->G, false, kp, p->nr, p->nf, kp, kp * p->nr, 128, adjoint ? 128 : F8_BN, true, true))
             return false;
         TcArgs a{};
-        a.kstages = (int)(kp / 128);
-        a.nout = p->nr;
+        a.kstages = adjoint ? (p->nr + 127) / 128 : (int)(kp / 128);
+        a.nout = adjoint ? p->ns : p->nr;
         a.nr = p->nr;
         a.ncol = ncol;
         a.inv_sigma = p->tcSigma;
@@ -1306,16 +1401,24 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         a.voff_o = voff_o;
         a.err = p->err_flag;
         a.wait_ns = p->wait_ns;
-        // kind::f8f6f4: D float32, A and B E4M3 (format 0), both K-major, N = 256, M = 128
-        const uint32_t idesc = (1u << 4) | ((uint32_t)(F8_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-        const int ntn = (p->nr + F8_BN - 1) / F8_BN;
+        // kind::f8f6f4: D float32, A and B E4M3 (format 0), A K-major, B K-major (forward) or
+        // MN-major (adjoint), N = 256, M = 128
+        const uint32_t idesc = (1u << 4) | ((adjoint ? 1u : 0u) << 16) | ((uint32_t)(F8_BN >> 3) << 17) |
+                               ((uint32_t)(TC_BM >> 4) << 24);
+        const int ntn = adjoint ? (int)((kp + F8_BN - 1) / F8_BN) : (p->nr + F8_BN - 1) / F8_BN;
         const int n_tiles = ntn * p->nf;
         const size_t smem = f8_smem_bytes();
-        static SmemLimit attr;
-        attr.ensure(tc_f8_fwd_kernel, (int)smem);
         const int ctas = n_tiles < sm_count() ? n_tiles : sm_count();
-        if (scoped) scope.emplace(p, s, MDC_KC_PRODUCT_FWD);
-        tc_f8_fwd_kernel<<<ctas, TC_THREADS, smem, s>>>(mA, mB, a, idesc, active, ntn, n_tiles);
+        if (scoped) scope.emplace(p, s, adjoint ? MDC_KC_PRODUCT_ADJ : MDC_KC_PRODUCT_FWD);
+        if (!adjoint) {
+            static SmemLimit attr;
+            attr.ensure(tc_f8_kernel<false>, (int)smem);
+            tc_f8_kernel<false><<<ctas, TC_THREADS, smem, s>>>(mA, mB, a, idesc, active, ntn, n_tiles);
+        } else {
+            static SmemLimit attr;
+            attr.ensure(tc_f8_kernel<true>, (int)smem);
+            tc_f8_kernel<true><<<ctas, TC_THREADS, smem, s>>>(mA, mB, a, idesc, active, ntn, n_tiles);
+        }
         return true;
     }
     if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
