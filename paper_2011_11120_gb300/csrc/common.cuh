@@ -174,6 +174,13 @@ struct IrfftArgs {
     const double* xw_kx;
     const double* xw_kw;
     const double* xw_ia;
+    // The forward transform of the final output (times the window fwd_cut if set, unscaled,
+    // conjugated if fwd_conj) into the spectrum fwd_X [nf][S][ldv] at column offset fwd_voff: fused
+    // into the kernel's epilogue where its tile holds the whole output, else launched after it.
+    // fwd_X null: none.
+    float2* fwd_X;
+    const int* fwd_cut;
+    int fwd_conj, fwd_voff;
 };
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
 // The inverse transform; on a frequency shard with a reduction hook: the partial transform, the

@@ -475,20 +475,83 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     }
 }
 
+// Forward transform of the tile the inverse kernel leaves behind: storage row rho = t1 * N2 + t2
+// holds time t = t1 + N1 t2 of P packed column pairs.  With k = k2 + N2 k1,
+//   X[k] = sum_t1 W_N1^(t1 k1) [ W_NT^(t1 k2) sum_t2 W_N2^(t2 k2) x[t1 + N1 t2] ],
+// so N2-point DFTs in each block t1, the twiddle, then N1-point DFTs over t1 leave bin k in row
+// k1 * N2 + k2 = k (natural order).  The two columns of each pair are then separated as in the
+// forward kernels (scale 1/2, optional conjugation) and bins [k0, k0 + nf) stored into fwd_X.
+// tw: the inverse transform's half-period table, conjugated here.
+template <int N1, int N2, int PP>
+__device__ __forceinline__ void fused_forward(const IrfftArgs& a, float2* z, const float2* tw, int c0) {
+    using F = FourStep<N1, N2, PP>;
+    constexpr int NT = F::NT, CT = F::CT, P = F::P;
+    for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
+        const int j = task % P, t1 = task / P;
+        float2 r[N2];
+#pragma unroll
+        for (int t2 = 0; t2 < N2; ++t2) r[t2] = z[F::zi(t1 * N2 + t2, j)];
+        reg_fft<N2, false>(r);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2)
+            z[F::zi(t1 * N2 + k2, j)] = k2 == 0 ? r[0] : cmul(r[k2], cconj(tw_full(tw, t1 * k2, NT)));
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
+        const int j = task % P, k2 = task / P;
+        float2 r[N1];
+#pragma unroll
+        for (int t1 = 0; t1 < N1; ++t1) r[t1] = z[F::zi(t1 * N2 + k2, j)];
+        reg_fft<N1, false>(r);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) z[F::zi(k1 * N2 + k2, j)] = r[k1];
+    }
+    __syncthreads();
+    constexpr int G = FFT_THREADS / CT;
+    const int cl = threadIdx.x % CT, g = threadIdx.x / CT, c = c0 + cl;
+    if (c >= a.C) return;
+    int s, v;
+    if ((a.nv % CT) == 0) {
+        s = c0 / a.nv;
+        v = c0 - s * a.nv + cl;
+    } else {
+        s = c / a.nv;
+        v = c - s * a.nv;
+    }
+    float2* dst = a.fwd_X + (size_t)s * a.ldv + a.fwd_voff + v;
+    const size_t kstride = (size_t)a.S * a.ldv;
+    const int j = cl >> 1;
+    const bool odd = (cl & 1) != 0;
+    for (int kk = g; kk < a.nf; kk += G) {
+        const int k = a.k0 + kk;
+        const float2 Z = z[F::zi(k, j)];
+        const float2 Zm = k == 0 ? Z : z[F::zi(NT - k, j)];
+        float2 r = odd ? make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x))
+                       : make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+        if (a.fwd_conj) r.y = -r.y;
+        dst[(size_t)kk * kstride] = r;
+    }
+}
+
 // MODE 1 (plain): the output is the transform alone (no window, base or previous-output terms,
 // column sums or time reversal, a_mdc = 1); MODE 0: the general epilogue; MODE 2: the general
 // epilogue with the LSQR x/w step of IrfftArgs fused in.  The inverse scale multiplies the
-// spectrum as it is loaded.
-template <int N1, int N2, int MODE, int PP>
+// spectrum as it is loaded.  FUSE (aligned path, MODES 0 and 2): the epilogue also keeps its
+// outputs (windowed by fwd_cut) in the tile, and the kernel ends with their forward transform into
+// fwd_X -- the transform the next product of an LSQR iteration needs, without reading the output
+// back from memory.
+template <int N1, int N2, int MODE, int PP, bool FUSE = false>
 __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(IrfftArgs a) {
     constexpr bool PLAIN = MODE == 1, XW = MODE == 2;
+    static_assert(!(FUSE && PLAIN), "the fused forward transform follows the general epilogue");
     using F = FourStep<N1, N2, PP>;
     constexpr int NT = F::NT, CT = F::CT, P = F::P;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 sm2[];
     float2* tw = sm2;
     float2* z = sm2 + NT / 2;
-    double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
+    // column-sum reduction: on the consumed tile, or (FUSE: the tile is transformed again) after it
+    double* red = reinterpret_cast<double*>(FUSE ? z + F::ZSIZE : z);
     const int c0 = blockIdx.x * CT;
     for (int i = threadIdx.x; i < NT / 2; i += FFT_THREADS) tw[i] = cconj(a.tw[i]);
     // rows no bin of the slab [k0, k0 + nf) reaches are zero (16-byte stores, P is even)
@@ -594,9 +657,12 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
         const bool want_ss = a.colsum != nullptr;
         float ss[4] = {0.f, 0.f, 0.f, 0.f};   // per-thread partial sums of squares (<= 16 terms)
         if (cq < a.C) {
-            int cut[4];
+            int cut[4], fcut[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+            for (int i = 0; i < 4; ++i) {
+                cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+                fcut[i] = (FUSE && a.fwd_cut) ? a.fwd_cut[cq + i] : 0x7fffffff;
+            }
 #pragma unroll 1
             for (int b0 = 0; b0 < PER; b0 += B) {
                 // storage row rho holds time sample t = (rho % N2) * N1 + rho / N2
@@ -630,6 +696,12 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                     }
                     const size_t o = (size_t)t * a.C + cq;
                     *reinterpret_cast<float4*>(a.out + o) = make_float4(v[0], v[1], v[2], v[3]);
+                    if constexpr (FUSE) {
+                        // the same tile slot, windowed for the forward transform
+                        *reinterpret_cast<float4*>(z + F::zi(rho, 2 * q)) =
+                            make_float4(tau >= fcut[0] ? 0.f : v[0], tau >= fcut[1] ? 0.f : v[1],
+                                        tau >= fcut[2] ? 0.f : v[2], tau >= fcut[3] ? 0.f : v[3]);
+                    }
                     if constexpr (XW) {
                         const float ww[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
                         const float xx[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
@@ -656,6 +728,10 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
                 a.colsum[c0 + threadIdx.x] = tot;
             }
+        }
+        if constexpr (FUSE) {
+            __syncthreads();                             // every output is in the tile
+            fused_forward<N1, N2, PP>(a, z, tw, c0);
         }
         return;
     }
@@ -1022,7 +1098,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
 // The transform alone: no window, base or previous-output terms, column sums or reversal.
 inline bool irfft_plain(const IrfftArgs& a) {
     return !a.cut && !a.base && !a.colsum && !a.reverse_out && a.a_mdc.h == 1.f && !a.a_mdc.d &&
-           a.a_prev.h == 0.f && !a.a_prev.d && !a.xw_w;
+           a.a_prev.h == 0.f && !a.a_prev.d && !a.xw_w && !a.fwd_X;
 }
 
 template <int N1, int N2, bool WIN, bool X2>
@@ -1097,31 +1173,38 @@ void rfft4_launch(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
     }
 }
 
-template <int N1, int N2, int MODE, int PP>
+template <int N1, int N2, int MODE, int PP, bool FUSE = false>
 void irfft4_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     using F = FourStep<N1, N2, PP>;
+    // FUSE: the column-sum reduction buffer follows the tile
+    constexpr size_t smem = F::smem + (FUSE ? (size_t)FFT_THREADS * 4 * sizeof(double) : 0);
     static SmemLimit attr;
-    attr.ensure(irfft4_kernel<N1, N2, MODE, PP>, (int)F::smem);
+    attr.ensure(irfft4_kernel<N1, N2, MODE, PP, FUSE>, (int)smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft4_kernel<N1, N2, MODE, PP><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, F::smem, s>>>(a);
+    irfft4_kernel<N1, N2, MODE, PP, FUSE><<<(a.C + F::CT - 1) / F::CT, FFT_THREADS, smem, s>>>(a);
 }
 
+// Returns true if the kernel also made the forward transform of IrfftArgs::fwd_X.
 template <int N1, int N2>
-void irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
+bool irfft4_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0) &&
              (!a.xw_w || ((uintptr_t)a.xw_w % 16 == 0 && (uintptr_t)a.xw_x % 16 == 0));
     constexpr int PS = few_cols_p<N1, N2>();
     const bool few = few_columns(a.C, FourStep<N1, N2>::CT) && PS < FourStep<N1, N2>::P;
+    const bool fuse = a.fwd_X && a.vec4 && !a.reverse_out;
     if (irfft_plain(a)) {
         if (few) irfft4_go<N1, N2, 1, PS>(p, a, s);
         else irfft4_go<N1, N2, 1, 0>(p, a, s);
     } else if (a.xw_w) {
-        irfft4_go<N1, N2, 2, 0>(p, a, s);
+        if (fuse) irfft4_go<N1, N2, 2, 0, true>(p, a, s);
+        else irfft4_go<N1, N2, 2, 0>(p, a, s);
     } else {
-        irfft4_go<N1, N2, 0, 0>(p, a, s);
+        if (fuse) irfft4_go<N1, N2, 0, 0, true>(p, a, s);
+        else irfft4_go<N1, N2, 0, 0>(p, a, s);
     }
+    return fuse;
 }
 
 int tile_log_columns(int nt) {
@@ -1158,7 +1241,18 @@ void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
 
 namespace {
 
-void launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
+bool launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s);
+
+// The forward transform IrfftArgs::fwd_X asks for, as its own launch on the finished output.
+void forward_of_output(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+    RfftArgs r{};
+    r.x = a.out;
+    r.C = a.C; r.S = a.S; r.nv = a.nv; r.nt = a.nt; r.logn = a.logn; r.nf = a.nf; r.k0 = a.k0;
+    r.cut = a.fwd_cut; r.scale = C1(1.f); r.conj = a.fwd_conj;
+    r.X = a.fwd_X; r.ldv = a.ldv; r.voff = a.fwd_voff;
+    r.tw = a.tw; r.active = a.active;
+    launch_rfft(p, r, s);
+}
 
 // Epilogue of a frequency shard's inverse transform, run on T = the partial transforms summed over
 // every shard (so the same signal on every shard): out = a_mdc Theta T + a_base base + a_prev out,
@@ -1228,7 +1322,7 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
         a.xw_x = a.xw_w = nullptr;
     }
     if (!p->red_fn) {
-        launch_irfft_local(p, a, s);
+        if (!launch_irfft_local(p, a, s) && a.fwd_X) forward_of_output(p, a, s);
         return;
     }
     const int64_t count = (int64_t)a.nt * a.C;
@@ -1255,23 +1349,27 @@ void launch_irfft(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     part.cut = nullptr;
     part.reverse_out = 0;
     part.colsum = nullptr;
+    part.fwd_X = nullptr;
     launch_irfft_local(p, part, s);
     const int st = p->red_fn(p->red_buf, count, (void*)s, p->red_ctx);
     if (st != MDC_OK && !p->host_error) p->host_error = st < 0 ? st : MDC_ERR_STATE;
-    LaunchScope ls(p, s, MDC_KC_IRFFT);
-    shard_epilogue<<<(unsigned)((a.C + 31) / 32), 256, 0, s>>>(a, p->red_buf);
+    {
+        LaunchScope ls(p, s, MDC_KC_IRFFT);
+        shard_epilogue<<<(unsigned)((a.C + 31) / 32), 256, 0, s>>>(a, p->red_buf);
+    }
+    if (a.fwd_X) forward_of_output(p, a, s);
 }
 
 namespace {
 
-void launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
+bool launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     switch (a.nt) {
-        case 64: irfft4_launch<8, 8>(p, a, s); return;
-        case 128: irfft4_launch<16, 8>(p, a, s); return;
-        case 256: irfft4_launch<16, 16>(p, a, s); return;
-        case 512: irfft4_launch<32, 16>(p, a, s); return;
-        case 1024: irfft4_launch<32, 32>(p, a, s); return;
-        case 2048: irfft_half_launch<32, 32>(p, a, s); return;
+        case 64: return irfft4_launch<8, 8>(p, a, s);
+        case 128: return irfft4_launch<16, 8>(p, a, s);
+        case 256: return irfft4_launch<16, 16>(p, a, s);
+        case 512: return irfft4_launch<32, 16>(p, a, s);
+        case 1024: return irfft4_launch<32, 32>(p, a, s);
+        case 2048: irfft_half_launch<32, 32>(p, a, s); return false;
         default: break;
     }
     const int logCT = tile_log_columns(a.nt);
@@ -1281,6 +1379,7 @@ void launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     const int grid = (a.C + (1 << logCT) - 1) >> logCT;
     LaunchScope ls(p, s, MDC_KC_IRFFT);
     irfft_kernel<<<grid, FFT_THREADS, smem, s>>>(a, logCT);
+    return false;
 }
 
 }  // namespace

@@ -49,6 +49,9 @@ struct Solver {
     int nresid = 0, nact = 0, nsolves = 0;
     int ldv = 0, voff0 = 0;    // spectrum layout: columns per point and this system's first column
     bool async_alloc = false;  // stream-ordered allocation (serving)
+    // The inverse transforms that produce v-hat also leave its spectra for the next forward product.
+    // Off for served jobs: the stacked spectrum layout changes between iterations.
+    bool fuse_v = true;
 
     void release(void* q) {
         if (!q) return;
@@ -105,10 +108,19 @@ struct Solver {
         a.tw = q->tw; a.active = active;
         launch_rfft(q, a, s);
     }
+    // fwd_voff >= 0: also the forward transform of the output (times the window fwd_cut if set,
+    // unscaled, conjugated if fwd_conj) into specA at column offset fwd_voff -- the next product's
+    // input, fused into the inverse kernel where it can be.
     void irfft(mdc_plan* q, int voff, int conj_in, float* out, Coef a_mdc, const int* cutp, const float* base,
                Coef a_base, Coef a_prev, double* colsum, int reverse, const int* active, float* xw_x = nullptr,
-               float* xw_w = nullptr) {
+               float* xw_w = nullptr, int fwd_voff = -1, const int* fwd_cut = nullptr, int fwd_conj = 0) {
         IrfftArgs a{};
+        if (fwd_voff >= 0) {
+            a.fwd_X = q->specA;
+            a.fwd_voff = voff0 + fwd_voff;
+            a.fwd_cut = fwd_cut;
+            a.fwd_conj = fwd_conj;
+        }
         if (xw_w) {                   // the pending LSQR x/w step, applied with the previous v-hat
             a.xw_x = xw_x; a.xw_w = xw_w;
             a.xw_kx = sc + S_KX; a.xw_kw = sc + S_KW; a.xw_ia = sc + S_INV_ALPHA;
@@ -153,13 +165,17 @@ struct Solver {
         irfft(pr, nv, 1, U2(), C1(1.f), cut, x2, C1(-1.f), C1(0.f), csU + C, 0, nullptr);
     }
 
-    // M^H u with u = u-hat / beta:  v-hat <- [a - (R*)^H Theta b ; b - R^H Theta a] + vprev * v-hat
+    // M^H u with u = u-hat / beta:  v-hat <- [a - (R*)^H Theta b ; b - R^H Theta a] + vprev * v-hat;
+    // the inverse transforms also leave the unscaled spectra of v-hat for the first forward product
+    // (1 / alpha is applied after that product).
     void apply_MH(const int* active, Coef vprev) {
         rfft(p, U1(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, active);
         rfft(p, U2(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, active);
         launch_product(p, true, p->specA, LD(), voff0, p->specB, LD(), voff0, 2 * nv, s, active);
-        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, active);
-        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, active);
+        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, active, nullptr,
+              nullptr, fuse_v ? nv : -1, nullptr, 1);
+        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, active, nullptr,
+              nullptr, fuse_v ? 0 : -1, nullptr, 0);
     }
 
     // LSQR start on u-hat (holding the right-hand side and its column sums): beta_1, then
@@ -184,32 +200,39 @@ struct Solver {
         else lsqr_w_init<<<eg, 256, 0, s>>>(B, W1(), W2(), V1(), V2(), sc);
     }
     // One LSQR iteration in four phases around the forward and adjoint products (so several
-    // systems can share one product over their stacked columns).
+    // systems can share one product over their stacked columns).  The adjoint product's input
+    // spectra come from the inverse transforms before it (the forward transform of their output,
+    // fused): the spectra of Theta u-hat without the 1 / beta that normalises u, which the inverse
+    // transform after the product applies instead.  With fuse_v the forward product's input is made
+    // the same way (spectra of v-hat, 1 / alpha applied after the product).
     //   u-hat <- M v - alpha u:  M [a; b] = [a - Theta R b ; b - Theta R* a]
     void iter_fwd_pre(const int* a) {
+        if (fuse_v) return;
         rfft(p, V2(), nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 0, 0, a);
         rfft(p, V1(), nullptr, nullptr, CD(1.f, sc + S_INV_ALPHA), 1, nv, a);
     }
     void iter_fwd_post(const int* a) {
-        irfft(p, 0, 0, U1(), C1(-1.f), cut, V1(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU, 0, a);
-        irfft(p, nv, 1, U2(), C1(-1.f), cut, V2(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU + C, 0, a);
+        const Coef am = fuse_v ? CD(-1.f, sc + S_INV_ALPHA) : C1(-1.f);
+        irfft(p, 0, 0, U1(), am, cut, V1(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU, 0, a, nullptr,
+              nullptr, 0, cut, 0);
+        irfft(p, nv, 1, U2(), am, cut, V2(), CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU + C, 0, a,
+              nullptr, nullptr, nv, cut, 1);
         LaunchScope ls(p, s, MDC_KC_SOLVER);
         colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, 2 * C, part, a);
         lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a);
     }
     //   v-hat <- M^H u - beta v
-    void iter_adj_pre(const int* a) {
-        rfft(p, U1(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 0, 0, a);
-        rfft(p, U2(), nullptr, cut, CD(1.f, sc + S_INV_BETA), 1, nv, a);
-    }
+    void iter_adj_pre(const int*) {}
     // The adjoint transforms also apply the previous rotation's x/w step (x += (phi/rho) w,
     // w = v / alpha + kw w) with the v-hat they overwrite; the last rotation's x step is applied by
     // xw_flush at the end of the solve.
     void iter_adj_post(int it, int niter, double tol, int* act0, double* resid0, int* itp, float* x1, float* x2) {
         const int* a = act0 + it;
         const Coef vprev = CD(1.f, sc + S_V_PREV);
-        irfft(p, nv, 1, V1(), C1(-1.f), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, a, x1, W1());
-        irfft(p, 0, 0, V2(), C1(-1.f), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0, a, x2, W2());
+        irfft(p, nv, 1, V1(), CD(-1.f, sc + S_INV_BETA), nullptr, U1(), CD(1.f, sc + S_INV_BETA), vprev, csV, 0, a,
+              x1, W1(), fuse_v ? nv : -1, nullptr, 1);
+        irfft(p, 0, 0, V2(), CD(-1.f, sc + S_INV_BETA), nullptr, U2(), CD(1.f, sc + S_INV_BETA), vprev, csV + C, 0,
+              a, x2, W2(), fuse_v ? 0 : -1, nullptr, 0);
         LaunchScope ls(p, s, MDC_KC_SOLVER);
         colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, 2 * C, part, a);
         lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act0 + it + 1, resid0, itp, it,
@@ -624,6 +647,7 @@ int start_job(mdc_server* v, ServeJob* j) {
     S->s = v->s;
     S->cut = j->cut_d;
     S->async_alloc = true;
+    S->fuse_v = false;
     S->nsolves = 1 + v->nref;
     S->nresid = (j->niter + 1) + v->nref * (v->niter_ref + 1);
     S->nact = (j->niter + 2) + v->nref * (v->niter_ref + 2);
@@ -728,6 +752,7 @@ int restore_job(mdc_server* v, ServeJob* j, const CkptJob& r, const unsigned cha
     S->s = v->s;
     S->cut = j->cut_d;
     S->async_alloc = true;
+    S->fuse_v = false;
     S->nsolves = r.nsolves;
     S->nresid = r.nresid;
     S->nact = r.nact;
