@@ -105,13 +105,16 @@ struct MddSolver {
         a.active = active;
         launch_rfft(p, a, s);
     }
-    // out = (operator result) + a_prev * out, with the column sums of squares of the new out
-    void irfft(float* out, int S, Coef a_prev, double* colsum, const int* active) {
+    // out = a_mdc (operator result) + a_prev * out, with the column sums of squares of the new out,
+    // and the unscaled spectrum of the new out into specA: the next product's input (the forward
+    // transform fused into the inverse kernel where it can be)
+    void irfft(float* out, int S, Coef a_mdc, Coef a_prev, double* colsum, const int* active) {
         IrfftArgs a{};
         a.Y = p->specB; a.ldv = nv; a.voff = 0; a.C = S * nv; a.S = S; a.nv = nv; a.nt = p->nt; a.logn = p->logn;
         a.nf = p->nf; a.k0 = p->k0; a.conj_in = 0; a.scale = (float)(p->dt * p->dr / (double)p->nt); a.out = out;
-        a.a_mdc = C1(1.f); a.a_base = C1(0.f); a.a_prev = a_prev; a.base = nullptr; a.cut = nullptr;
+        a.a_mdc = a_mdc; a.a_base = C1(0.f); a.a_prev = a_prev; a.base = nullptr; a.cut = nullptr;
         a.reverse_out = 0; a.colsum = colsum; a.tw = p->tw; a.active = active;
+        a.fwd_X = p->specA; a.fwd_voff = 0; a.fwd_cut = nullptr; a.fwd_conj = 0;
         launch_irfft(p, a, s);
     }
     void product(bool adjoint, const int* active) {
@@ -126,10 +129,12 @@ struct MddSolver {
             colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, Cu, part, nullptr);
             lsqr_init_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, resid, act + 1);
         }
-        // alpha_1 v_1 = G+^H u_1
+        // alpha_1 v_1 = G+^H u_1.  Each product's input is the unscaled spectrum the inverse
+        // transform before it leaves (of v-hat, of u-hat); 1 / alpha and 1 / beta, which normalise
+        // v and u, are applied by the inverse transform after the product.
         rfft(U, p->nr, CD(1.f, sc + S_INV_BETA), act + 1);
         product(true, act + 1);
-        irfft(V, p->ns, C1(0.f), csV, act + 1);
+        irfft(V, p->ns, C1(1.f), C1(0.f), csV, act + 1);
         {
             LaunchScope ls(p, s, MDC_KC_SOLVER);
             colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, Cv, part, act + 1);
@@ -139,18 +144,16 @@ struct MddSolver {
         for (int it = 1; it <= niter; ++it) {
             const int* a = act + it;
             // u-hat <- G+ v - alpha u
-            rfft(V, p->ns, CD(1.f, sc + S_INV_ALPHA), a);
             product(false, a);
-            irfft(U, p->nr, CD(1.f, sc + S_U_PREV), csU, a);
+            irfft(U, p->nr, CD(1.f, sc + S_INV_ALPHA), CD(1.f, sc + S_U_PREV), csU, a);
             {
                 LaunchScope ls(p, s, MDC_KC_SOLVER);
                 colsum_partials<<<PART_CTAS, 256, 0, s>>>(csU, Cu, part, a);
                 lsqr_beta<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a);
             }
             // v-hat <- G+^H u - beta v
-            rfft(U, p->nr, CD(1.f, sc + S_INV_BETA), a);
             product(true, a);
-            irfft(V, p->ns, CD(1.f, sc + S_V_PREV), csV, a);
+            irfft(V, p->ns, CD(1.f, sc + S_INV_BETA), CD(1.f, sc + S_V_PREV), csV, a);
             LaunchScope ls(p, s, MDC_KC_SOLVER);
             colsum_partials<<<PART_CTAS, 256, 0, s>>>(csV, Cv, part, a);
             lsqr_alpha_rotate<<<1, RED_THREADS, 0, s>>>(sc, part, PART_CTAS, a, act + it + 1, resid, iters, it, niter,
