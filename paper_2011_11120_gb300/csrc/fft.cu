@@ -888,14 +888,73 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     }
 }
 
-template <int N1, int N2, bool PLAIN>
+// Forward half-length transform of the tile the inverse kernel leaves behind: row rho = t1 * N2 + t2
+// holds z[n] = x[2n] + i x[2n+1], n = t1 + N1 t2, of column j.  The NC-point DFT in the order of
+// fused_forward (N2-point DFTs, twiddle W_NC^(t1 k2), N1-point DFTs) leaves Z[k] in row k; the
+// even/odd split then gives X[k] = E[k] + W_nt^k O[k] (k < NC), X[NC] = E[0] - O[0], as in
+// rfft_half_kernel (unscaled, optional conjugation), stored into fwd_X for bins [k0, k0 + nf).
+template <int N1, int N2>
+__device__ __forceinline__ void fused_forward_half(const IrfftArgs& a, float2* z, int c0) {
+    using H = HalfStep<N1, N2>;
+    using F = typename H::F;
+    constexpr int NC = H::NC, P = H::P;
+    const float2* __restrict__ twc = a.tw + NC;           // W_NC^m, m < NC
+    for (int task = threadIdx.x; task < P * N1; task += FFT_THREADS) {
+        const int j = task % P, t1 = task / P;
+        float2 r[N2];
+#pragma unroll
+        for (int t2 = 0; t2 < N2; ++t2) r[t2] = z[F::zi(t1 * N2 + t2, j)];
+        reg_fft<N2, false>(r);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) z[F::zi(t1 * N2 + k2, j)] = k2 == 0 ? r[0] : cmul(r[k2], twc[t1 * k2]);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
+        const int j = task % P, k2 = task / P;
+        float2 r[N1];
+#pragma unroll
+        for (int t1 = 0; t1 < N1; ++t1) r[t1] = z[F::zi(t1 * N2 + k2, j)];
+        reg_fft<N1, false>(r);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) z[F::zi(k1 * N2 + k2, j)] = r[k1];
+    }
+    __syncthreads();
+    constexpr int G = FFT_THREADS / P;
+    const int cl = threadIdx.x % P, g = threadIdx.x / P, c = c0 + cl;
+    if (c >= a.C) return;
+    const int s = c / a.nv, v = c - s * a.nv;
+    float2* dst = a.fwd_X + (size_t)s * a.ldv + a.fwd_voff + v;
+    const size_t kstride = (size_t)a.S * a.ldv;
+    for (int kk = g; kk < a.nf; kk += G) {
+        const int k = a.k0 + kk;
+        float2 X;
+        if (k >= NC) {                                        // Nyquist bin k = NC
+            const float2 Z0 = z[F::zi(0, cl)];
+            X = make_float2(Z0.x - Z0.y, 0.f);
+        } else {
+            const float2 Z = z[F::zi(k, cl)];
+            const float2 Zm = z[F::zi((NC - k) & (NC - 1), cl)];
+            const float2 E = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+            const float2 O = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
+            X = cadd(E, cmul(O, a.tw[k]));
+        }
+        if (a.fwd_conj) X.y = -X.y;
+        dst[(size_t)kk * kstride] = X;
+    }
+}
+
+// FUSE (aligned general path): the epilogue keeps its outputs (windowed by fwd_cut) in the tile as
+// z[n] = x[2n] + i x[2n+1], and the kernel ends with their forward half-length transform into fwd_X.
+template <int N1, int N2, bool PLAIN, bool FUSE = false>
 __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(IrfftArgs a) {
+    static_assert(!(FUSE && PLAIN), "the fused forward transform follows the general epilogue");
     using H = HalfStep<N1, N2>;
     using F = typename H::F;
     constexpr int NC = H::NC, NT = H::NT, P = H::P;
     if (a.active && *a.active == 0) return;
     extern __shared__ __align__(16) float2 z[];
-    double* red = reinterpret_cast<double*>(z);      // used after the tile is consumed
+    // column-sum reduction: on the consumed tile, or (FUSE: the tile is transformed again) after it
+    double* red = reinterpret_cast<double*>(FUSE ? z + F::ZSIZE : z);
     const float2* __restrict__ twc = a.tw + 2 * NC;   // conj W_NC^m, m < NC
     const int c0 = blockIdx.x * P;
     // Item (kk, j), kk <= NC / 2, reads X[kk] and X[NC - kk] of column c0 + j and writes Z[kk]
@@ -988,9 +1047,12 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
         const int q = threadIdx.x % Q, t0 = threadIdx.x / Q, cq = c0 + 4 * q;
         float ss[4] = {0.f, 0.f, 0.f, 0.f};
         if (cq < a.C) {
-            int cut[4];
+            int cut[4], fcut[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+            for (int i = 0; i < 4; ++i) {
+                cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
+                fcut[i] = (FUSE && a.fwd_cut) ? a.fwd_cut[cq + i] : 0x7fffffff;
+            }
 #pragma unroll 1
             for (int b0 = 0; b0 < PERQ; b0 += BQ) {
                 float4 bv[BQ][2], pv[BQ][2];
@@ -1012,6 +1074,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                     const float4 z01 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q));
                     const float4 z23 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q + 2));
                     const float re[4] = {z01.x, z01.z, z23.x, z23.z}, im[4] = {z01.y, z01.w, z23.y, z23.w};
+                    float vw[2][4];                  // (FUSE) the outputs, windowed for the forward transform
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int t = 2 * n + h;
@@ -1024,8 +1087,15 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                             const float val = tau >= cut[i] ? 0.f : (h ? im[i] : re[i]);
                             v[i] = am * val + ab * bb[i] + ap * pp[i];
                             if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
+                            vw[h][i] = tau >= fcut[i] ? 0.f : v[i];
                         }
                         *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                    if constexpr (FUSE) {
+                        *reinterpret_cast<float4*>(z + F::zi(rho, 4 * q)) =
+                            make_float4(vw[0][0], vw[1][0], vw[0][1], vw[1][1]);
+                        *reinterpret_cast<float4*>(z + F::zi(rho, 4 * q + 2)) =
+                            make_float4(vw[0][2], vw[1][2], vw[0][3], vw[1][3]);
                     }
                 }
             }
@@ -1041,6 +1111,10 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                 for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
                 a.colsum[c0 + threadIdx.x] = tot;
             }
+        }
+        if constexpr (FUSE) {
+            __syncthreads();                             // every output is in the tile
+            fused_forward_half<N1, N2>(a, z, c0);
         }
         return;
     }
@@ -1110,13 +1184,15 @@ void rfft_half_go(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     rfft_half_kernel<N1, N2, WIN, X2><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
 }
 
-template <int N1, int N2, bool PLAIN>
+template <int N1, int N2, bool PLAIN, bool FUSE = false>
 void irfft_half_go(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
     using H = HalfStep<N1, N2>;
+    // FUSE: the column-sum reduction buffer follows the tile
+    constexpr size_t smem = H::smem + (FUSE ? (size_t)FFT_THREADS * 4 * sizeof(double) : 0);
     static SmemLimit attr;
-    attr.ensure(irfft_half_kernel<N1, N2, PLAIN>, (int)H::smem);
+    attr.ensure(irfft_half_kernel<N1, N2, PLAIN, FUSE>, (int)smem);
     LaunchScope ls(p, s, MDC_KC_IRFFT);
-    irfft_half_kernel<N1, N2, PLAIN><<<(a.C + H::P - 1) / H::P, FFT_THREADS, H::smem, s>>>(a);
+    irfft_half_kernel<N1, N2, PLAIN, FUSE><<<(a.C + H::P - 1) / H::P, FFT_THREADS, smem, s>>>(a);
 }
 
 template <int N1, int N2>
@@ -1130,13 +1206,17 @@ void rfft_half_launch(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
     }
 }
 
+// Returns true if the kernel also made the forward transform of IrfftArgs::fwd_X.
 template <int N1, int N2>
-void irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
+bool irfft_half_launch(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
     a.vec4 = (a.C % 4 == 0) && !a.reverse_out && ((uintptr_t)a.out % 16 == 0) &&
              (!a.base || (uintptr_t)a.base % 16 == 0);
+    const bool fuse = a.fwd_X && a.vec4;
     if (irfft_plain(a)) irfft_half_go<N1, N2, true>(p, a, s);
+    else if (fuse) irfft_half_go<N1, N2, false, true>(p, a, s);
     else irfft_half_go<N1, N2, false>(p, a, s);
+    return fuse;
 }
 
 template <int N1, int N2, bool WIN, bool X2, int PP>
@@ -1369,7 +1449,7 @@ bool launch_irfft_local(mdc_plan* p, const IrfftArgs& a, cudaStream_t s) {
         case 256: return irfft4_launch<16, 16>(p, a, s);
         case 512: return irfft4_launch<32, 16>(p, a, s);
         case 1024: return irfft4_launch<32, 32>(p, a, s);
-        case 2048: irfft_half_launch<32, 32>(p, a, s); return false;
+        case 2048: return irfft_half_launch<32, 32>(p, a, s);
         default: break;
     }
     const int logCT = tile_log_columns(a.nt);
