@@ -48,6 +48,7 @@ def oracle_solve(cfg, G, cut, fd, niter, tol=0.0):
     (21, 512, 150, 2, 800.0, 20),   # redatuming shapes at reduced aperture
     (3, 2048, 300, 1, 600.0, 6),    # nt = 2048 (half-length real transforms), GEMV
     (5, 2048, 301, 2, 600.0, 6),    # nt = 2048, GEMM, odd nf
+    (3, 4096, 100, 2, 600.0, 4),    # nt = 4096 (radix-2 kernels: forward transforms as launches of their own)
 ])
 def test_marchenko_lsqr_matches_oracle(n_side, nt, nf, nvg, z, niter):
     import paper_2011_11120_gb300 as m

@@ -36,6 +36,7 @@ def problem(nt, nf, nS, nF, nv, seed):
     (64, 20, 30, 12, 1, 8),         # one virtual source (GEMV products)
     (128, 40, 100, 49, 20, 15),     # a batch of 20 virtual sources, as in the paper's MDD runs
     (256, 60, 70, 130, 3, 10),      # more focusing points than receivers (wide kernel)
+    (2048, 200, 40, 25, 4, 6),      # half-length transforms, the next product's spectra fused
 ])
 def test_mdd_lsqr_matches_oracle(nt, nf, nS, nF, nv, niter):
     import paper_2011_11120_gb300 as m
