@@ -1,5 +1,5 @@
-// Tensor-core (tcgen05) per-frequency products for the FP16/BF16 kernel copies:
-// K-hat and K-hat^H of Eq. 3 when many virtual points make each frequency slice a
+// Tensor-core (tcgen05) per-frequency products for the FP16/BF16, split-FP16 and E4M3 kernel
+// copies: K-hat and K-hat^H of Eq. 3 when many virtual points make each frequency slice a
 // dense GEMM (the batched products the paper uses for groups of focusing points).
 //
 // The complex product is one real GEMM on the interleaved (re, im) storage of G:
@@ -8,7 +8,7 @@
 //            BT[2n]   = ( Xr_s, -Xi_s )_s   (row of reals along K')
 //            BT[2n+1] = ( Xi_s,  Xr_s )_s
 //            -> D[r][2n] = Re Y[r][n], D[r][2n+1] = Im Y[r][n].
-//            A = G^ read K-major (rows r, 512-byte... contiguous along K').
+//            A = G^ read K-major (rows r contiguous along K').
 //   adjoint  D[m][n''] = sum_r G^[r][m] BT[n''][r],  m = 2s + c, n'' = 2n + c'',
 //            BT[2n] = (Yr_r)_r, BT[2n+1] = (Yi_r)_r (row scale of G folded in),
 //            Re X'[s][n] = D[2s][2n] + D[2s+1][2n+1], Im X'[s][n] = D[2s][2n+1] - D[2s+1][2n].
@@ -17,9 +17,10 @@
 // One CTA computes a 128 x BN tile of D for one frequency: warp 0 streams A and B
 // tiles with TMA into a ring of 128-byte-swizzled shared-memory stages, warp 1 (one
 // thread) issues tcgen05.mma (M=128, N=BN, K=16, FP32 accumulation in TMEM), warps
-// 2-5 read the accumulator back with tcgen05.ld and write complex64 results.  B is
+// 2-9 read the accumulator back with tcgen05.ld and write complex64 results.  B is
 // scaled per (frequency, column) by a power of two so FP16 neither overflows nor
 // underflows; the epilogue divides it out and applies G's row scale (forward).
+// E4M3 products of at most 21 columns run with the operands swapped (tc_f8_kernel below).
 // Every wait on an mbarrier is bounded in wall time: on expiry the thread records
 // an error code, the producer drains its own copies in flight, TMEM is freed and
 // the CTA exits.
@@ -271,11 +272,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // continuously across tiles and the accumulator is double-buffered in TMEM (2 x BN columns),
 // so the epilogue of one tile overlaps the main loop of the next.
 //
-// CVT (E4M3 kernel copy): TMA brings each stage's A tile as bytes (128 rows x 64 B, unswizzled)
-// beside its B tile; warps 10..17 widen it to FP16 into the next free tile w of a small ring,
-// laid out as a 16-bit TMA load would have put it (128-byte swizzle), and arrive on conv[w]; the
-// MMA issuer waits for the stage (B) and conv[w] (A), and its commit frees both.  The MMA is
-// the ordinary kind::f16 with FP16 operands.
+// CVT (E4M3 kernel copy): warp 18 streams each step's A tile as bytes into a byte ring; warps
+// 10..17 widen it to FP16 -- into tensor memory for forward products with narrow B tiles (TA: row
+// m in TMEM lane m, the MMA reads A from TMEM), else into the next free tile w of a small
+// shared-memory ring laid out as a 16-bit TMA load would have put it (128-byte swizzle) -- then
+// release the byte slot and arrive on conv[w]; the MMA issuer waits for the stage (B) and conv[w]
+// (A), and its commit frees both.  The MMA is the ordinary kind::f16 with FP16 operands.
 template <bool ADJ, int BN, bool SPLIT, bool CVT = false>
 __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -408,14 +410,15 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
         if (lane == 0) {
             // the byte tiles of A: forward one box of 128 rows x KSUB * 64 bytes, adjoint one box of
             // KSUB * 64 rows x 128 bytes, into slot g % NBY once the converters have released it
+            constexpr int NB = NBY > 0 ? NBY : 1;      // (the branch is dead without CVT)
             long g = 0;
             bool ok = true;
             for (int tile = t_first; tile < n_tiles && ok; tile += t_stride) {
                 int k, m0, n0;
                 coords(tile, k, m0, n0);
                 for (int kb = 0; kb < ksteps; ++kb, ++g) {
-                    const int y = (int)(g % NBY);
-                    if (g >= NBY && !mbar_wait(bempty0 + 8 * y, (uint32_t)(g / NBY - 1) & 1, a.err, 10, wl)) {
+                    const int y = (int)(g % NB);
+                    if (g >= NB && !mbar_wait(bempty0 + 8 * y, (uint32_t)(g / NB - 1) & 1, a.err, 10, wl)) {
                         ok = false;
                         break;
                     }
@@ -426,8 +429,8 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
                     else tma_load_3d(st, &tmA, bfull0 + 8 * y, m0 / 4, kb * KSUB * TC_BK, k);
                 }
             }
-            for (long q = g > NBY ? g - NBY : 0; q < g; ++q)
-                mbar_wait(bfull0 + 8 * (int)(q % NBY), (uint32_t)(q / NBY) & 1, a.err, 11, TC_DRAIN_NS);
+            for (long q = g > NB ? g - NB : 0; q < g; ++q)
+                mbar_wait(bfull0 + 8 * (int)(q % NB), (uint32_t)(q / NB) & 1, a.err, 11, TC_DRAIN_NS);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -472,26 +475,26 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
                         }
                         umma_commit(empty0 + 8 * s);
                         umma_commit(wfree0 + 8 * w);                          // the A buffer is free
-                        continue;
-                    }
+                    } else {
 #pragma unroll
-                    for (int kq = 0; kq < KSUB * (TC_BK / 16); ++kq) {
-                        // K-major: +32 bytes per 16 elements inside the swizzled row (next 64-element
-                        // slice: next A tile and B slice); MN-major: +16 rows
-                        const int kk = kq % (TC_BK / 16), ks = kq / (TC_BK / 16);
-                        const uint32_t ao = ks * A_BYTES + (ADJ ? kk * 2048 : kk * 32);
-                        const uint32_t lbo = ADJ ? A_BYTES / 2 : 16;
-                        const uint64_t ad = sdesc(sa + ao, lbo, 1024);
-                        const uint64_t bd = sdesc(sb + ks * B_BYTES + kk * 32, 16, 1024);
-                        umma_f16(d, ad, bd, idesc, ((kb - kb0) | kq) != 0 ? 1u : 0u);
-                        if (SPLIT) {
-                            // hi*lo + lo*hi: the dropped lo*lo term is below 2^-22 relative
-                            umma_f16(d, ad, sdesc(sb2 + kk * 32, 16, 1024), idesc, 1u);
-                            umma_f16(d, sdesc(sa2 + ao, lbo, 1024), bd, idesc, 1u);
+                        for (int kq = 0; kq < KSUB * (TC_BK / 16); ++kq) {
+                            // K-major: +32 bytes per 16 elements inside the swizzled row (next 64-element
+                            // slice: next A tile and B slice); MN-major: +16 rows
+                            const int kk = kq % (TC_BK / 16), ks = kq / (TC_BK / 16);
+                            const uint32_t ao = ks * A_BYTES + (ADJ ? kk * 2048 : kk * 32);
+                            const uint32_t lbo = ADJ ? A_BYTES / 2 : 16;
+                            const uint64_t ad = sdesc(sa + ao, lbo, 1024);
+                            const uint64_t bd = sdesc(sb + ks * B_BYTES + kk * 32, 16, 1024);
+                            umma_f16(d, ad, bd, idesc, ((kb - kb0) | kq) != 0 ? 1u : 0u);
+                            if (SPLIT) {
+                                // hi*lo + lo*hi: the dropped lo*lo term is below 2^-22 relative
+                                umma_f16(d, ad, sdesc(sb2 + kk * 32, 16, 1024), idesc, 1u);
+                                umma_f16(d, sdesc(sa2 + ao, lbo, 1024), bd, idesc, 1u);
+                            }
                         }
+                        umma_commit(empty0 + 8 * s);
+                        if (CVT) umma_commit(wfree0 + 8 * w);                 // the widened tile is free
                     }
-                    umma_commit(empty0 + 8 * s);
-                    if (CVT) umma_commit(wfree0 + 8 * w);                     // the widened tile is free
                 }
                 umma_commit(accf0 + 8 * buf);
               }
