@@ -48,7 +48,9 @@ typedef enum {
     MDC_C64 = 0,    /* complex float32 (the paper's complex64 kernel, Table 1) */
     MDC_C16F = 1,   /* complex float16, one float32 scale per (frequency, row) */
     MDC_CBF16 = 2,  /* complex bfloat16, one float32 scale per (frequency, row) */
-    MDC_CE4M3 = 3,  /* complex FP8 E4M3, one float32 scale per (frequency, row) */
+    MDC_CE4M3 = 3,  /* complex FP8 E4M3, one float32 scale per (frequency, row); tensor-core products
+                       of at most 21 columns take the spectra as three E4M3 terms (about 12
+                       significant bits), wider ones as FP16 */
     MDC_C32S = 4    /* complex as an FP16 pair hi + lo per component (about 22 significant bits,
                        float32-level accuracy), one float32 scale per (frequency, row); 8 bytes per
                        value like complex64, but products run on FP16 tensor cores */
@@ -64,8 +66,8 @@ typedef enum {
     MDC_KC_PRODUCT_ADJ = 2, /* K-hat^H of Eq. 3: per-frequency G(w)^H Y(w) */
     MDC_KC_IRFFT = 3,       /* I_wmax^H and F^H of Eq. 3 (plus fused epilogues) */
     MDC_KC_SOLVER = 4,      /* LSQR scalar recurrences and vector updates */
-    MDC_KC_TC_PREP = 5,     /* tensor-core products: spectra to the 16-bit B operand and column scales
-                               (the products' own time is in MDC_KC_PRODUCT_FWD / _ADJ) */
+    MDC_KC_TC_PREP = 5,     /* tensor-core products: spectra to the 16-bit (or E4M3 three-term) operand
+                               and column scales (the products' own time is in MDC_KC_PRODUCT_FWD / _ADJ) */
     MDC_KC_COUNT = 6
 } mdc_kernel_class;
 
