@@ -7,7 +7,8 @@ wall time by the handle's limit (MDC_OPT_WAIT_LIMIT_US, default 2 s).  Here the 
 every copy and MMA the kernel issues completes, the kernel drains them before it exits, and only
 the short limit makes the waits give up.  The test checks that the handle then reports
 MDC_ERR_TIMEOUT, that the flag clears, and that the same handle (limit restored) and a fresh one
-compute the product correctly afterwards.
+compute the product correctly afterwards.  FP16 storage runs the 16-bit GEMM; E4M3 storage at
+8 columns runs the swapped-operand E4M3 kernel, whose waits are bounded the same way.
 """
 import numpy as np
 import pytest
@@ -21,7 +22,8 @@ pytestmark = pytest.mark.gpu
 MDC_ERR_TIMEOUT = -4
 
 
-def test_short_wait_limit_reports_timeout_then_recovers():
+@pytest.mark.parametrize("storage", ["c16f", "ce4m3"])
+def test_short_wait_limit_reports_timeout_then_recovers(storage):
     import paper_2011_11120_gb300 as m
     nt, nr, ns, nf, nv = 64, 256, 32768, 2, 8
     rng = np.random.default_rng(77)
@@ -29,10 +31,10 @@ def test_short_wait_limit_reports_timeout_then_recovers():
     x = rng.standard_normal((nt, ns, nv)).astype(np.float32)
     Gd = torch.from_numpy(G.astype(np.complex64)).cuda()
     xd = torch.from_numpy(x).cuda()
-    u = FORMATS["c16f"][0]
-    y_ref = omdc.forward(dequantised(G, "c16f"), x, 0.004, 400.0)
+    u = FORMATS["c16f"][0]                 # spectra rounding of both tensor-core paths: within 4 u16
+    y_ref = omdc.forward(dequantised(G, storage), x, 0.004, 400.0)
 
-    op = m.MDC(Gd, nt, 0.004, 400.0, storage="c16f")
+    op = m.MDC(Gd, nt, 0.004, 400.0, storage=storage)
     try:
         m.mdc_reserve(op.h, nv)
         m.mdc_set_option(op.h, m.MDC_OPT_WAIT_LIMIT_US, 1)
@@ -51,7 +53,7 @@ def test_short_wait_limit_reports_timeout_then_recovers():
     finally:
         op.close()
 
-    op2 = m.MDC(Gd, nt, 0.004, 400.0, storage="c16f")
+    op2 = m.MDC(Gd, nt, 0.004, 400.0, storage=storage)
     try:
         y2 = op2.forward(xd)
         m.mdc_device_status(op2.h)
