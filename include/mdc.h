@@ -39,7 +39,9 @@ typedef enum {
     MDC_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
     MDC_ERR_NUMERIC = -5,   /* non-finite value met in a solver recurrence */
     MDC_ERR_BUDGET = -6,    /* request exceeds the configured memory budget */
-    MDC_ERR_STATE = -7      /* call not valid in the handle's current state */
+    MDC_ERR_STATE = -7,     /* call not valid in the handle's current state */
+    MDC_ERR_BOUNDS = -8     /* debug build only: a kernel index outside its buffer was caught (the
+                               access was skipped); reported by mdc_device_status */
 } mdc_status;
 
 /* Storage format of the library-owned kernel copy (Section "Implementing the batch

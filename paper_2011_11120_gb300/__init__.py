@@ -15,7 +15,9 @@ from typing import Optional
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmdc_gb300.so")
+# MDC_LIB_DEBUG=1: the bounds-checked build (python -m paper_2011_11120_gb300.build --debug)
+LIB_PATH = os.path.join(_HERE, "libmdc_gb300_debug.so" if os.environ.get("MDC_LIB_DEBUG") == "1"
+                        else "libmdc_gb300.so")
 
 MDC_OK = 0
 MDC_C64, MDC_C16F, MDC_CBF16, MDC_CE4M3, MDC_C32S = 0, 1, 2, 3, 4
@@ -288,7 +290,8 @@ def mdc_tc_fallback_count(h) -> int:
 
 
 def mdc_device_status(h, stream=None) -> None:
-    """Raise MDCError(MDC_ERR_TIMEOUT) if a bounded device wait of this handle gave up."""
+    """Raise MDCError(MDC_ERR_TIMEOUT) if a bounded device wait of this handle gave up (and, in the
+    bounds-checked build, MDCError(MDC_ERR_BOUNDS) if a kernel index fell outside its buffer)."""
     _check(lib().mdc_device_status(h, _stream(stream)), "mdc_device_status")
 
 

@@ -5,6 +5,13 @@
 Produces ``paper_2011_11120_gb300/libmdc_gb300.so`` (the product library behind
 ``include/mdc.h``) and ``synth/libsynth_gen.so`` (the synthetic-workload
 generator).  Translation units compile in parallel; each has one -gencode.
+
+    python -m paper_2011_11120_gb300.build --debug
+
+also builds ``libmdc_gb300_debug.so``: the same sources compiled with MDC_CHECK_BOUNDS, whose
+kernels check their global indices against the buffer extents (a miss is recorded in the handle's
+error flag and the access skipped; ``mdc_device_status`` reports MDC_ERR_BOUNDS).  Setting
+MDC_LIB_DEBUG=1 makes the Python binding load it instead of the release library.
 """
 from __future__ import annotations
 
@@ -19,6 +26,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmdc_gb300.so")
+DEBUG_LIB = os.path.join(PKG, "libmdc_gb300_debug.so")
 SYNTH_LIB = os.path.join(ROOT, "synth", "libsynth_gen.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,8 +43,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src: str, obj: str, log: str) -> None:
-    cmd = [nvcc(), "-c", src, "-o", obj] + NVFLAGS
+def _compile(src: str, obj: str, log: str, extra=()) -> None:
+    cmd = [nvcc(), "-c", src, "-o", obj] + NVFLAGS + list(extra)
     with open(log, "w") as fh:
         res = subprocess.run(cmd, stdout=fh, stderr=subprocess.STDOUT)
     if res.returncode != 0:
@@ -79,6 +87,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_debug(force: bool = False) -> str:
+    """The bounds-checked library (MDC_CHECK_BOUNDS), beside the release one."""
+    os.makedirs(BUILD, exist_ok=True)
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers.append(os.path.join(ROOT, "include", "mdc.h"))
+    jobs, objs = [], []
+    for s in SOURCES:
+        src = os.path.join(CSRC, s)
+        obj = os.path.join(BUILD, s.replace(".cu", ".debug.o"))
+        objs.append(obj)
+        if force or _stale(obj, [src] + headers):
+            jobs.append((src, obj, obj + ".log", ["-DMDC_CHECK_BOUNDS"]))
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs) or 1, os.cpu_count() or 4))) as ex:
+        list(ex.map(lambda j: _compile(*j), jobs))
+    if force or _stale(DEBUG_LIB, objs):
+        subprocess.run([nvcc(), "-shared", "-o", DEBUG_LIB] + objs + ARCH, check=True)
+    return DEBUG_LIB
+
+
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose="-v" in sys.argv)
     print(LIB)
+    if "--debug" in sys.argv:
+        print(build_debug(force="--force" in sys.argv))

@@ -73,6 +73,7 @@ extern "C" const char* mdc_strerror(int status) {
         case MDC_ERR_NUMERIC: return "non-finite value in solver recurrence";
         case MDC_ERR_BUDGET: return "request exceeds memory budget";
         case MDC_ERR_STATE: return "call not valid in current state";
+        case MDC_ERR_BOUNDS: return "kernel index outside its buffer (debug build)";
         default: return "unknown status";
     }
 }
@@ -421,7 +422,7 @@ extern "C" int mdc_device_status(mdc_handle h, void* stream) {
     if (v != 0) {
         MDC_CUDA_TRY(cudaMemsetAsync(h->err_flag, 0, sizeof(int), (cudaStream_t)stream));
         MDC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        return MDC_ERR_TIMEOUT;
+        return mdc::device_flag_status(v);
     }
     return MDC_OK;
 }

@@ -43,6 +43,41 @@ struct SmemLimit {
     }
 };
 
+// Bounds checks of the debug build (compiled with MDC_CHECK_BOUNDS into a library of its own):
+// every instrumented global access checks that elements [off, off + span) lie inside its buffer of
+// n elements.  A miss records MDC_BOUNDS_CODE + site in the handle's error flag (the first miss
+// wins; mdc_device_status then reports MDC_ERR_BOUNDS) and the access goes to a small dummy buffer
+// instead, so nothing outside any buffer is read or written.  Release builds expand MDC_AT to the
+// plain pointer arithmetic.
+constexpr int MDC_BOUNDS_CODE = 1000;
+#ifdef MDC_CHECK_BOUNDS
+static __device__ __align__(16) unsigned char mdc_bounds_dummy[64];
+template <typename T>
+__device__ __forceinline__ T* mdc_checked(T* p, long long off, long long span, long long n, int* err, int site) {
+    if (p != nullptr && off >= 0 && off + span <= n) return p + off;
+    if (err) atomicCAS(err, 0, MDC_BOUNDS_CODE + site);
+    return reinterpret_cast<T*>(mdc_bounds_dummy);
+}
+#define MDC_AT(p, off, span, n, err, site) \
+    mdc::mdc_checked((p), (long long)(off), (long long)(span), (long long)(n), (err), (site))
+// Guard form for accesses kept verbatim: `if (MDC_INB(...)) access;` (a miss is recorded and the
+// access skipped); release builds reduce the guard to the constant true.
+__device__ __forceinline__ bool mdc_ok(long long off, long long span, long long n, int* err, int site) {
+    if (off >= 0 && off + span <= n) return true;
+    if (err) atomicCAS(err, 0, MDC_BOUNDS_CODE + site);
+    return false;
+}
+#define MDC_INB(off, span, n, err, site) \
+    mdc::mdc_ok((long long)(off), (long long)(span), (long long)(n), (err), (site))
+#else
+#define MDC_AT(p, off, span, n, err, site) ((p) + (off))
+#define MDC_INB(off, span, n, err, site) true
+#endif
+// Status of a device error flag value: 0, a bounded wait that gave up, or a bounds miss.
+inline int device_flag_status(int v) {
+    return v == 0 ? MDC_OK : (v >= MDC_BOUNDS_CODE ? MDC_ERR_BOUNDS : MDC_ERR_TIMEOUT);
+}
+
 inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
@@ -148,6 +183,7 @@ struct RfftArgs {
     const float2* tw;
     const int* active;     // if non-null and *active == 0 the kernel does nothing
     int vec4;              // set by the launcher: x (and x2) 16-byte aligned rows, C % 4 == 0
+    int* err;              // set by the launcher: the plan's device error flag (bounds checks)
 };
 struct IrfftArgs {
     const float2* Y;       // [nf][S][ldv]
@@ -181,6 +217,7 @@ struct IrfftArgs {
     float2* fwd_X;
     const int* fwd_cut;
     int fwd_conj, fwd_voff;
+    int* err;              // set by the launcher: the plan's device error flag (bounds checks)
 };
 void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s);
 // The inverse transform; on a frequency shard with a reduction hook: the partial transform, the

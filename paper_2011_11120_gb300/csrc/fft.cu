@@ -66,11 +66,12 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft_kernel(RfftArgs a, int logCT
         float v = 0.f;
         if (c < a.C) {
             const size_t off = (size_t)t * a.C + c;
-            v = a.x[off];
-            if (a.x2) v += a.x2[off];
+            [[maybe_unused]] const long long nx = (long long)nt * a.C;
+            v = *MDC_AT(a.x, off, 1, nx, a.err, 1);
+            if (a.x2) v += *MDC_AT(a.x2, off, 1, nx, a.err, 2);
             if (a.cut) {
                 const int tau = t < (nt >> 1) ? t : nt - t;
-                if (tau >= a.cut[c]) v = 0.f;
+                if (tau >= *MDC_AT(a.cut, c, 1, a.C, a.err, 3)) v = 0.f;
             }
             v *= sc;
         }
@@ -90,13 +91,13 @@ __global__ void __launch_bounds__(FFT_THREADS) rfft_kernel(RfftArgs a, int logCT
         else               r = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
         if (a.conj) r.y = -r.y;
         const int s = c / a.nv, v = c - s * a.nv;
-        a.X[((size_t)k * a.S + s) * a.ldv + a.voff + v] = r;
+        *MDC_AT(a.X, ((size_t)k * a.S + s) * a.ldv + a.voff + v, 1, (long long)a.nf * a.S * a.ldv, a.err, 4) = r;
     }
 }
 
 __device__ __forceinline__ float2 load_bin(const IrfftArgs& a, int k, int c) {
     const int s = c / a.nv, v = c - s * a.nv;
-    return a.Y[((size_t)k * a.S + s) * a.ldv + a.voff + v];
+    return *MDC_AT(a.Y, ((size_t)k * a.S + s) * a.ldv + a.voff + v, 1, (long long)a.nf * a.S * a.ldv, a.err, 5);
 }
 
 __global__ void __launch_bounds__(FFT_THREADS) irfft_kernel(IrfftArgs a, int logCT) {
@@ -132,18 +133,19 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft_kernel(IrfftArgs a, int log
     const int cl = threadIdx.x & (CT - 1), c = c0 + cl;
     double ss = 0.0;
     if (c < a.C) {
-        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        const int cut = a.cut ? *MDC_AT(a.cut, c, 1, a.C, a.err, 6) : 0x7fffffff;
+        [[maybe_unused]] const long long nx = (long long)nt * a.C;
         for (int t = threadIdx.x >> logCT; t < nt; t += FFT_THREADS >> logCT) {
             const float2 zz = reinterpret_cast<const float2*>(zf + t * RS)[cl >> 1];
             float val = ((cl & 1) ? zz.y : zz.x) * a.scale;
             const int tau = t < (nt >> 1) ? t : nt - t;
             if (tau >= cut) val = 0.f;
             float r = am * val;
-            if (a.base) r += ab * a.base[(size_t)t * a.C + c];
+            if (a.base) r += ab * *MDC_AT(a.base, (size_t)t * a.C + c, 1, nx, a.err, 7);
             const int to = a.reverse_out ? ((nt - t) & (nt - 1)) : t;
             const size_t o = (size_t)to * a.C + c;
-            if (has_prev) r += ap * a.out[o];
-            a.out[o] = r;
+            if (has_prev) r += ap * *MDC_AT(a.out, o, 1, nx, a.err, 8);
+            *MDC_AT(a.out, o, 1, nx, a.err, 9) = r;
             ss += (double)r * (double)r;
         }
     }
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(FFT_THREADS) irfft_kernel(IrfftArgs a, int log
         if (threadIdx.x < CT && c < a.C) {
             double tot = 0.0;
             for (int i = threadIdx.x; i < FFT_THREADS; i += CT) tot += red[i];
-            a.colsum[c] = tot;
+            *MDC_AT(a.colsum, c, 1, a.C, a.err, 10) = tot;
         }
     }
 }
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
     auto put = [&](int t, int cl, float v) {
         if constexpr (WIN) {
             const int tau = t < (NT >> 1) ? t : NT - t;
-            if (tau >= a.cut[c0 + cl]) v = 0.f;
+            if (tau >= *MDC_AT(a.cut, c0 + cl, 1, a.C, a.err, 11)) v = 0.f;
         }
         reinterpret_cast<float*>(z + F::zi(t, cl >> 1))[cl & 1] = v;
     };
@@ -379,21 +381,21 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
         const size_t rstride = (size_t)N2 * a.C;          // floats between the rows n1 and n1 + 1
         for (int task = threadIdx.x; task < P * N2; task += FFT_THREADS) {
             const int j = task % P, n2 = task / P, c = c0 + 2 * j;
-            const float* xb = a.x + c + (size_t)n2 * a.C;
+            const size_t xo = c + (size_t)n2 * a.C;
             float2 r[N1];
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) r[n1] = *reinterpret_cast<const float2*>(xb + n1 * rstride);
+            for (int n1 = 0; n1 < N1; ++n1)
+                r[n1] = *reinterpret_cast<const float2*>(MDC_AT(a.x, xo + n1 * rstride, 2, (long long)NT * a.C, a.err, 12));
             if constexpr (X2) {
-                const float* x2b = a.x2 + c + (size_t)n2 * a.C;
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
-                    const float2 w = *reinterpret_cast<const float2*>(x2b + n1 * rstride);
+                    const float2 w = *reinterpret_cast<const float2*>(MDC_AT(a.x2, xo + n1 * rstride, 2, (long long)NT * a.C, a.err, 13));
                     r[n1].x += w.x;
                     r[n1].y += w.y;
                 }
             }
             if constexpr (WIN) {
-                const int cut0 = a.cut[c], cut1 = a.cut[c + 1];
+                const int cut0 = *MDC_AT(a.cut, c, 1, a.C, a.err, 14), cut1 = *MDC_AT(a.cut, c + 1, 1, a.C, a.err, 14);
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
                     const int t = n1 * N2 + n2;
@@ -421,8 +423,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 v[u] = 0.f;
                 if (c < a.C) {
                     const size_t off = (size_t)t * a.C + c;
-                    v[u] = a.x[off];
-                    if constexpr (X2) v[u] += a.x2[off];
+                    v[u] = *MDC_AT(a.x, off, 1, (long long)NT * a.C, a.err, 15);
+                    if constexpr (X2) v[u] += *MDC_AT(a.x2, off, 1, (long long)NT * a.C, a.err, 16);
                 }
             }
 #pragma unroll
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
             s = c / a.nv;
             v = c - s * a.nv;
         }
-        float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
+        const size_t dsto = (size_t)s * a.ldv + a.voff + v;
         const size_t kstride = (size_t)a.S * a.ldv;
         const int j = cl >> 1;
         const bool odd = (cl & 1) != 0;
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft4_kernel(RfftArgs a) {
                 float2 r = odd ? make_float2(hs * (Z.y + Zm.y), hs * (Zm.x - Z.x))
                                : make_float2(hs * (Z.x + Zm.x), hs * (Z.y - Zm.y));
                 if (a.conj) r.y = -r.y;
-                dst[(size_t)(k - a.k0) * kstride] = r;
+                *MDC_AT(a.X, dsto + (size_t)(k - a.k0) * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 17) = r;
             }
         }
     }
@@ -518,7 +520,7 @@ __device__ __forceinline__ void fused_forward(const IrfftArgs& a, float2* z, con
         s = c / a.nv;
         v = c - s * a.nv;
     }
-    float2* dst = a.fwd_X + (size_t)s * a.ldv + a.fwd_voff + v;
+    const size_t dsto = (size_t)s * a.ldv + a.fwd_voff + v;
     const size_t kstride = (size_t)a.S * a.ldv;
     const int j = cl >> 1;
     const bool odd = (cl & 1) != 0;
@@ -529,7 +531,7 @@ __device__ __forceinline__ void fused_forward(const IrfftArgs& a, float2* z, con
         float2 r = odd ? make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x))
                        : make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
         if (a.fwd_conj) r.y = -r.y;
-        dst[(size_t)kk * kstride] = r;
+        *MDC_AT(a.fwd_X, dsto + (size_t)kk * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 18) = r;
     }
 }
 
@@ -570,12 +572,15 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
         const size_t kstride = (size_t)a.S * a.ldv;
         const float2* pa = nullptr;
         const float2* pb = nullptr;
+        size_t paoff = 0, pboff = 0;
         if (ca < a.C) {
             const int sa = ca / a.nv, va = ca - sa * a.nv;
-            pa = a.Y + (size_t)sa * a.ldv + a.voff + va;
+            paoff = (size_t)sa * a.ldv + a.voff + va;
+            pa = a.Y + paoff;
             if (ca + 1 < a.C) {
                 const int sb = (ca + 1) / a.nv, vb = ca + 1 - sb * a.nv;
-                pb = a.Y + (size_t)sb * a.ldv + a.voff + vb;
+                pboff = (size_t)sb * a.ldv + a.voff + vb;
+                pb = a.Y + pboff;
             }
         }
         // both columns as one 16-byte load when they are adjacent and every row keeps the alignment
@@ -592,12 +597,12 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 if (kk < a.nf && pa) {
                     const size_t o = (size_t)kk * kstride;
                     if (pair16) {
-                        const float4 q = *reinterpret_cast<const float4*>(pa + o);
+                        const float4 q = *reinterpret_cast<const float4*>(MDC_AT(a.Y, paoff + o, 2, (long long)a.nf * a.S * a.ldv, a.err, 20));
                         A[u] = make_float2(q.x, q.y);
                         Bv[u] = make_float2(q.z, q.w);
                     } else {
-                        A[u] = pa[o];
-                        if (pb) Bv[u] = pb[o];
+                        A[u] = *MDC_AT(a.Y, paoff + o, 1, (long long)a.nf * a.S * a.ldv, a.err, 21);
+                        if (pb) Bv[u] = *MDC_AT(a.Y, pboff + o, 1, (long long)a.nf * a.S * a.ldv, a.err, 22);
                     }
                 }
             }
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
 #pragma unroll 4
                 for (int rho = threadIdx.x / Q; rho < NT; rho += TS) {
                     const int t = (rho % N2) * N1 + rho / N2;
-                    *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) =
+                    *reinterpret_cast<float4*>(MDC_AT(a.out, (size_t)t * a.C + cq, 4, (long long)NT * a.C, a.err, 23)) =
                         *reinterpret_cast<const float4*>(z + F::zi(rho, 2 * q));
                 }
             }
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 for (int rho = threadIdx.x / CT; rho < NT; rho += FFT_THREADS / CT) {
                     const int t = (rho % N2) * N1 + rho / N2;
                     const float2 zz = z[F::zi(rho, cl >> 1)];
-                    a.out[(size_t)t * a.C + c] = (cl & 1) ? zz.y : zz.x;
+                    *MDC_AT(a.out, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 24) = (cl & 1) ? zz.y : zz.x;
                 }
             }
         }
@@ -660,8 +665,8 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
             int cut[4], fcut[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
-                fcut[i] = (FUSE && a.fwd_cut) ? a.fwd_cut[cq + i] : 0x7fffffff;
+                cut[i] = a.cut ? *MDC_AT(a.cut, cq + i, 1, a.C, a.err, 25) : 0x7fffffff;
+                fcut[i] = (FUSE && a.fwd_cut) ? *MDC_AT(a.fwd_cut, cq + i, 1, a.C, a.err, 26) : 0x7fffffff;
             }
 #pragma unroll 1
             for (int b0 = 0; b0 < PER; b0 += B) {
@@ -671,11 +676,13 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 for (int u = 0; u < B; ++u) {
                     const int rho = t0 + (b0 + u) * TS;
                     const size_t o = (size_t)((rho % N2) * N1 + rho / N2) * a.C + cq;
-                    bv[u] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    pv[u] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    bv[u] = a.base ? *reinterpret_cast<const float4*>(MDC_AT(a.base, o, 4, (long long)NT * a.C, a.err, 27))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    pv[u] = has_prev ? *reinterpret_cast<const float4*>(MDC_AT(a.out, o, 4, (long long)NT * a.C, a.err, 28))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
                     if constexpr (XW) {
-                        wv[u] = *reinterpret_cast<const float4*>(a.xw_w + o);
-                        xv[u] = *reinterpret_cast<const float4*>(a.xw_x + o);
+                        wv[u] = *reinterpret_cast<const float4*>(MDC_AT(a.xw_w, o, 4, (long long)NT * a.C, a.err, 29));
+                        xv[u] = *reinterpret_cast<const float4*>(MDC_AT(a.xw_x, o, 4, (long long)NT * a.C, a.err, 30));
                     }
                 }
 #pragma unroll
@@ -695,7 +702,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                         if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                     }
                     const size_t o = (size_t)t * a.C + cq;
-                    *reinterpret_cast<float4*>(a.out + o) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4*>(MDC_AT(a.out, o, 4, (long long)NT * a.C, a.err, 31)) = make_float4(v[0], v[1], v[2], v[3]);
                     if constexpr (FUSE) {
                         // the same tile slot, windowed for the forward transform
                         *reinterpret_cast<float4*>(z + F::zi(rho, 2 * q)) =
@@ -711,8 +718,8 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                             nx[i] = fmaf(xkx, ww[i], xx[i]);
                             nw[i] = fmaf(xkw, ww[i], xia * pp[i]);
                         }
-                        *reinterpret_cast<float4*>(a.xw_x + o) = make_float4(nx[0], nx[1], nx[2], nx[3]);
-                        *reinterpret_cast<float4*>(a.xw_w + o) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+                        *reinterpret_cast<float4*>(MDC_AT(a.xw_x, o, 4, (long long)NT * a.C, a.err, 32)) = make_float4(nx[0], nx[1], nx[2], nx[3]);
+                        *reinterpret_cast<float4*>(MDC_AT(a.xw_w, o, 4, (long long)NT * a.C, a.err, 33)) = make_float4(nw[0], nw[1], nw[2], nw[3]);
                     }
                 }
             }
@@ -726,7 +733,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 const int qq = threadIdx.x / 4, ii = threadIdx.x % 4;
                 double tot = 0.0;
                 for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
-                a.colsum[c0 + threadIdx.x] = tot;
+                *MDC_AT(a.colsum, c0 + threadIdx.x, 1, a.C, a.err, 34) = tot;
             }
         }
         if constexpr (FUSE) {
@@ -739,7 +746,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
     const bool want_ss = a.colsum != nullptr;
     float ss = 0.f;   // per-thread partial sum of squares (<= 64 terms)
     if (c < a.C) {
-        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        const int cut = a.cut ? *MDC_AT(a.cut, c, 1, a.C, a.err, 35) : 0x7fffffff;
         constexpr int TS = FFT_THREADS / CT, PER = NT / TS, B = PER < 8 ? PER : 8;
         const int t0 = threadIdx.x / CT;
 #pragma unroll 1
@@ -750,11 +757,11 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 const int rho = t0 + (b0 + u) * TS;
                 const int t = (rho % N2) * N1 + rho / N2;
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
-                bv[u] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
-                pv[u] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
+                bv[u] = a.base ? *MDC_AT(a.base, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 36) : 0.f;
+                pv[u] = has_prev ? *MDC_AT(a.out, (size_t)to * a.C + c, 1, (long long)NT * a.C, a.err, 37) : 0.f;
                 if constexpr (XW) {
-                    wv[u] = a.xw_w[(size_t)t * a.C + c];
-                    xv[u] = a.xw_x[(size_t)t * a.C + c];
+                    wv[u] = *MDC_AT(a.xw_w, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 38);
+                    xv[u] = *MDC_AT(a.xw_x, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 39);
                 }
             }
 #pragma unroll
@@ -767,11 +774,11 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
                 if (tau >= cut) val = 0.f;
                 const float r = am * val + ab * bv[u] + ap * pv[u];
                 const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
-                a.out[(size_t)to * a.C + c] = r;
+                *MDC_AT(a.out, (size_t)to * a.C + c, 1, (long long)NT * a.C, a.err, 40) = r;
                 if (want_ss) ss = fmaf(r, r, ss);
                 if constexpr (XW) {
-                    a.xw_x[(size_t)t * a.C + c] = fmaf(xkx, wv[u], xv[u]);
-                    a.xw_w[(size_t)t * a.C + c] = fmaf(xkw, wv[u], xia * pv[u]);
+                    *MDC_AT(a.xw_x, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 41) = fmaf(xkx, wv[u], xv[u]);
+                    *MDC_AT(a.xw_w, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 42) = fmaf(xkw, wv[u], xia * pv[u]);
                 }
             }
         }
@@ -783,7 +790,7 @@ __global__ void __launch_bounds__(FFT_THREADS, MODE == 2 ? 2 : 3) irfft4_kernel(
         if (threadIdx.x < CT && c < a.C) {
             double tot = 0.0;
             for (int i = threadIdx.x; i < FFT_THREADS; i += CT) tot += red[i];
-            a.colsum[c] = tot;
+            *MDC_AT(a.colsum, c, 1, a.C, a.err, 10) = tot;
         }
     }
 }
@@ -826,19 +833,20 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
         float2 r[N1];
         if (c < a.C) {
             const size_t rstride = (size_t)2 * N2 * a.C;       // floats between n1 and n1 + 1
-            const float* xb = a.x + c + (size_t)2 * n2 * a.C;
+            const size_t xo = c + (size_t)2 * n2 * a.C;
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) r[n1] = make_float2(xb[n1 * rstride], xb[n1 * rstride + a.C]);
+            for (int n1 = 0; n1 < N1; ++n1)
+                r[n1] = make_float2(*MDC_AT(a.x, xo + n1 * rstride, 1, (long long)NT * a.C, a.err, 50),
+                                    *MDC_AT(a.x, xo + n1 * rstride + a.C, 1, (long long)NT * a.C, a.err, 50));
             if constexpr (X2) {
-                const float* x2b = a.x2 + c + (size_t)2 * n2 * a.C;
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
-                    r[n1].x += x2b[n1 * rstride];
-                    r[n1].y += x2b[n1 * rstride + a.C];
+                    r[n1].x += *MDC_AT(a.x2, xo + n1 * rstride, 1, (long long)NT * a.C, a.err, 51);
+                    r[n1].y += *MDC_AT(a.x2, xo + n1 * rstride + a.C, 1, (long long)NT * a.C, a.err, 51);
                 }
             }
             if constexpr (WIN) {
-                const int cut = a.cut[c];
+                const int cut = *MDC_AT(a.cut, c, 1, a.C, a.err, 52);
 #pragma unroll
                 for (int n1 = 0; n1 < N1; ++n1) {
                     const int t = 2 * (n1 * N2 + n2);
@@ -863,7 +871,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
     const int cl = threadIdx.x % P, g = threadIdx.x / P, c = c0 + cl;
     if (c >= a.C) return;
     const int s = c / a.nv, v = c - s * a.nv;
-    float2* dst = a.X + (size_t)s * a.ldv + a.voff + v;
+    const size_t dsto = (size_t)s * a.ldv + a.voff + v;
     const size_t kstride = (size_t)a.S * a.ldv;
     const float sc = coef(a.scale), hs = 0.5f * sc;
     const int kend = a.k0 + a.nf;                                  // bins [k0, kend) are written
@@ -883,7 +891,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) rfft_half_kernel(RfftArgs a) {
                 X = cadd(E, cmul(O, a.tw[k]));
             }
             if (a.conj) X.y = -X.y;
-            dst[(size_t)(k - a.k0) * kstride] = X;
+            *MDC_AT(a.X, dsto + (size_t)(k - a.k0) * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 53) = X;
         }
     }
 }
@@ -923,7 +931,7 @@ __device__ __forceinline__ void fused_forward_half(const IrfftArgs& a, float2* z
     const int cl = threadIdx.x % P, g = threadIdx.x / P, c = c0 + cl;
     if (c >= a.C) return;
     const int s = c / a.nv, v = c - s * a.nv;
-    float2* dst = a.fwd_X + (size_t)s * a.ldv + a.fwd_voff + v;
+    const size_t dsto = (size_t)s * a.ldv + a.fwd_voff + v;
     const size_t kstride = (size_t)a.S * a.ldv;
     for (int kk = g; kk < a.nf; kk += G) {
         const int k = a.k0 + kk;
@@ -939,7 +947,7 @@ __device__ __forceinline__ void fused_forward_half(const IrfftArgs& a, float2* z
             X = cadd(E, cmul(O, a.tw[k]));
         }
         if (a.fwd_conj) X.y = -X.y;
-        dst[(size_t)kk * kstride] = X;
+        *MDC_AT(a.fwd_X, dsto + (size_t)kk * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 54) = X;
     }
 }
 
@@ -965,9 +973,11 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
         const size_t kstride = (size_t)a.S * a.ldv;
         const int j = threadIdx.x % P, c = c0 + j, kend = a.k0 + a.nf;
         const float2* col = nullptr;
+        size_t colo = 0;
         if (c < a.C) {
             const int sp = c / a.nv, vp = c - sp * a.nv;
-            col = a.Y + (size_t)sp * a.ldv + a.voff + vp;
+            colo = (size_t)sp * a.ldv + a.voff + vp;
+            col = a.Y + colo;
         }
 #pragma unroll 1
         for (int kk0 = threadIdx.x / P; kk0 < KK; kk0 += BL * STEP) {
@@ -978,8 +988,9 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
             Al[u] = make_float2(0.f, 0.f);
             Bl[u] = Al[u];
             if (kk < KK && col) {
-                if (kk >= a.k0 && kk < kend) Al[u] = col[(size_t)(kk - a.k0) * kstride];
-                if (NC - kk >= a.k0 && NC - kk < kend) Bl[u] = col[(size_t)(NC - kk - a.k0) * kstride];
+                if (kk >= a.k0 && kk < kend) Al[u] = *MDC_AT(a.Y, colo + (size_t)(kk - a.k0) * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 55);
+                if (NC - kk >= a.k0 && NC - kk < kend)
+                    Bl[u] = *MDC_AT(a.Y, colo + (size_t)(NC - kk - a.k0) * kstride, 1, (long long)a.nf * a.S * a.ldv, a.err, 56);
             }
           }
 #pragma unroll
@@ -1019,9 +1030,9 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                     const int n = (rho % N2) * N1 + rho / N2;
                     const float4 z01 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q));
                     const float4 z23 = *reinterpret_cast<const float4*>(z + F::zi(rho, 4 * q + 2));
-                    *reinterpret_cast<float4*>(a.out + (size_t)(2 * n) * a.C + cq) =
+                    *reinterpret_cast<float4*>(MDC_AT(a.out, (size_t)(2 * n) * a.C + cq, 4, (long long)NT * a.C, a.err, 57)) =
                         make_float4(z01.x, z01.z, z23.x, z23.z);
-                    *reinterpret_cast<float4*>(a.out + (size_t)(2 * n + 1) * a.C + cq) =
+                    *reinterpret_cast<float4*>(MDC_AT(a.out, (size_t)(2 * n + 1) * a.C + cq, 4, (long long)NT * a.C, a.err, 57)) =
                         make_float4(z01.y, z01.w, z23.y, z23.w);
                 }
             }
@@ -1031,8 +1042,8 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                 for (int rho = threadIdx.x / P; rho < NC; rho += FFT_THREADS / P) {
                     const int n = (rho % N2) * N1 + rho / N2;
                     const float2 zz = z[F::zi(rho, cl)];
-                    a.out[(size_t)(2 * n) * a.C + c] = zz.x;
-                    a.out[(size_t)(2 * n + 1) * a.C + c] = zz.y;
+                    *MDC_AT(a.out, (size_t)(2 * n) * a.C + c, 1, (long long)NT * a.C, a.err, 58) = zz.x;
+                    *MDC_AT(a.out, (size_t)(2 * n + 1) * a.C + c, 1, (long long)NT * a.C, a.err, 58) = zz.y;
                 }
             }
         }
@@ -1050,8 +1061,8 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
             int cut[4], fcut[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                cut[i] = a.cut ? a.cut[cq + i] : 0x7fffffff;
-                fcut[i] = (FUSE && a.fwd_cut) ? a.fwd_cut[cq + i] : 0x7fffffff;
+                cut[i] = a.cut ? *MDC_AT(a.cut, cq + i, 1, a.C, a.err, 25) : 0x7fffffff;
+                fcut[i] = (FUSE && a.fwd_cut) ? *MDC_AT(a.fwd_cut, cq + i, 1, a.C, a.err, 26) : 0x7fffffff;
             }
 #pragma unroll 1
             for (int b0 = 0; b0 < PERQ; b0 += BQ) {
@@ -1063,8 +1074,10 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const size_t o = (size_t)(2 * n + h) * a.C + cq;
-                        bv[u][h] = a.base ? *reinterpret_cast<const float4*>(a.base + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        pv[u][h] = has_prev ? *reinterpret_cast<const float4*>(a.out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        bv[u][h] = a.base ? *reinterpret_cast<const float4*>(MDC_AT(a.base, o, 4, (long long)NT * a.C, a.err, 59))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                        pv[u][h] = has_prev ? *reinterpret_cast<const float4*>(MDC_AT(a.out, o, 4, (long long)NT * a.C, a.err, 60))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
 #pragma unroll
@@ -1089,7 +1102,8 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                             if (want_ss) ss[i] = fmaf(v[i], v[i], ss[i]);
                             vw[h][i] = tau >= fcut[i] ? 0.f : v[i];
                         }
-                        *reinterpret_cast<float4*>(a.out + (size_t)t * a.C + cq) = make_float4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<float4*>(MDC_AT(a.out, (size_t)t * a.C + cq, 4, (long long)NT * a.C, a.err, 61)) =
+                            make_float4(v[0], v[1], v[2], v[3]);
                     }
                     if constexpr (FUSE) {
                         *reinterpret_cast<float4*>(z + F::zi(rho, 4 * q)) =
@@ -1109,7 +1123,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                 const int qq = threadIdx.x / 4, ii = threadIdx.x % 4;
                 double tot = 0.0;
                 for (int tt = qq; tt < FFT_THREADS; tt += Q) tot += red[4 * tt + ii];
-                a.colsum[c0 + threadIdx.x] = tot;
+                *MDC_AT(a.colsum, c0 + threadIdx.x, 1, a.C, a.err, 34) = tot;
             }
         }
         if constexpr (FUSE) {
@@ -1122,7 +1136,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
     const int cl = threadIdx.x % P, t0 = threadIdx.x / P, c = c0 + cl;
     float ss = 0.f;
     if (c < a.C) {
-        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        const int cut = a.cut ? *MDC_AT(a.cut, c, 1, a.C, a.err, 62) : 0x7fffffff;
 #pragma unroll 1
         for (int b0 = 0; b0 < PER; b0 += BS) {
             float bv[BS][2], pv[BS][2];
@@ -1134,8 +1148,8 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                 for (int h = 0; h < 2; ++h) {
                     const int t = 2 * n + h;
                     const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
-                    bv[u][h] = a.base ? a.base[(size_t)t * a.C + c] : 0.f;
-                    pv[u][h] = has_prev ? a.out[(size_t)to * a.C + c] : 0.f;
+                    bv[u][h] = a.base ? *MDC_AT(a.base, (size_t)t * a.C + c, 1, (long long)NT * a.C, a.err, 63) : 0.f;
+                    pv[u][h] = has_prev ? *MDC_AT(a.out, (size_t)to * a.C + c, 1, (long long)NT * a.C, a.err, 64) : 0.f;
                 }
             }
 #pragma unroll
@@ -1151,7 +1165,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
                     if (tau >= cut) val = 0.f;
                     const int to = a.reverse_out ? ((NT - t) & (NT - 1)) : t;
                     const float r = am * val + ab * bv[u][h] + ap * pv[u][h];
-                    a.out[(size_t)to * a.C + c] = r;
+                    *MDC_AT(a.out, (size_t)to * a.C + c, 1, (long long)NT * a.C, a.err, 65) = r;
                     if (want_ss) ss = fmaf(r, r, ss);
                 }
             }
@@ -1164,7 +1178,7 @@ __global__ void __launch_bounds__(FFT_THREADS, PLAIN ? 3 : 2) irfft_half_kernel(
         if (threadIdx.x < P && c < a.C) {
             double tot = 0.0;
             for (int i = threadIdx.x; i < FFT_THREADS; i += P) tot += red[i];
-            a.colsum[c] = tot;
+            *MDC_AT(a.colsum, c, 1, a.C, a.err, 66) = tot;
         }
     }
 }
@@ -1300,7 +1314,9 @@ size_t irfft_smem(int nt, int logCT) { return rfft_smem(nt, logCT) + FFT_THREADS
 
 }  // namespace
 
-void launch_rfft(mdc_plan* p, const RfftArgs& a, cudaStream_t s) {
+void launch_rfft(mdc_plan* p, const RfftArgs& a0, cudaStream_t s) {
+    RfftArgs a = a0;
+    a.err = p->err_flag;
     switch (a.nt) {
         case 64: rfft4_launch<8, 8>(p, a, s); return;
         case 128: rfft4_launch<16, 8>(p, a, s); return;
@@ -1346,16 +1362,17 @@ __global__ void __launch_bounds__(256) shard_epilogue(IrfftArgs a, const float* 
     const bool has_prev = (a.a_prev.h != 0.f) || (a.a_prev.d != nullptr);
     double ss = 0.0;
     if (c < a.C) {
-        const int cut = a.cut ? a.cut[c] : 0x7fffffff;
+        const int cut = a.cut ? *MDC_AT(a.cut, c, 1, a.C, a.err, 70) : 0x7fffffff;
+        [[maybe_unused]] const long long nx = (long long)a.nt * a.C;
         for (int t = ty; t < a.nt; t += 8) {
             const int tau = t < (a.nt >> 1) ? t : a.nt - t;
-            const float val = tau >= cut ? 0.f : T[(size_t)t * a.C + c];
+            const float val = tau >= cut ? 0.f : *MDC_AT(T, (size_t)t * a.C + c, 1, nx, a.err, 71);
             float r = am * val;
-            if (a.base) r += ab * a.base[(size_t)t * a.C + c];
+            if (a.base) r += ab * *MDC_AT(a.base, (size_t)t * a.C + c, 1, nx, a.err, 72);
             const int to = a.reverse_out ? ((a.nt - t) & (a.nt - 1)) : t;
             const size_t o = (size_t)to * a.C + c;
-            if (has_prev) r += ap * a.out[o];
-            a.out[o] = r;
+            if (has_prev) r += ap * *MDC_AT(a.out, o, 1, nx, a.err, 73);
+            *MDC_AT(a.out, o, 1, nx, a.err, 74) = r;
             ss += (double)r * (double)r;
         }
     }
@@ -1366,7 +1383,7 @@ __global__ void __launch_bounds__(256) shard_epilogue(IrfftArgs a, const float* 
         if (ty == 0 && c < a.C) {
             double tot = 0.0;
             for (int i = 0; i < 8; ++i) tot += red[32 * i + tx];
-            a.colsum[c] = tot;
+            *MDC_AT(a.colsum, c, 1, a.C, a.err, 75) = tot;
         }
     }
 }
@@ -1393,6 +1410,7 @@ inline bool irfft_fuses_xw(const IrfftArgs& a) { return a.nt <= 1024 && !a.rever
 
 void launch_irfft(mdc_plan* p, const IrfftArgs& a0, cudaStream_t s) {
     IrfftArgs a = a0;
+    a.err = p->err_flag;
     if (a.xw_w && (p->red_fn || !irfft_fuses_xw(a))) {
         const int64_t n = (int64_t)a.nt * a.C;
         int64_t g = (n + 255) / 256;

@@ -468,7 +468,7 @@ int run_marchenko(mdc_plan* p, mdc_plan* pr, const int* cut, const float* fd, in
     }
     int err = 0;
     cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) return MDC_ERR_TIMEOUT;
+    if (err) return mdc::device_flag_status(err);
     const int he = take_host_error(p), her = pr != p ? take_host_error(pr) : MDC_OK;
     if (he != MDC_OK) return he;
     if (her != MDC_OK) return her;
@@ -524,7 +524,7 @@ extern "C" int marchenko_neumann(mdc_handle R, const int* window, const float* f
     }
     int err = 0;
     cudaMemcpy(&err, R->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) return MDC_ERR_TIMEOUT;
+    if (err) return mdc::device_flag_status(err);
     return mdc::take_host_error(R);
 }
 

@@ -203,7 +203,7 @@ extern "C" int mdd_lsqr(mdc_handle Gplus, const float* g_minus, int nv, int nite
     if (iters_done) *iters_done = it;
     int err = 0;
     cudaMemcpy(&err, p->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
-    if (err) return MDC_ERR_TIMEOUT;
+    if (err) return mdc::device_flag_status(err);
     const int he = take_host_error(p);
     if (he != MDC_OK) return he;
     return sch[S_STATUS] != 0.0 ? MDC_ERR_NUMERIC : MDC_OK;

@@ -105,14 +105,15 @@ template <int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_c64(
     const float4* __restrict__ G, int ldg, int nr, int ns,
     const float2* __restrict__ X, int ldi, int voff_i,
-    float2* __restrict__ Y, int ldo, int voff_o, const int* active) {
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int* err) {
     if (active && *active == 0) return;
     extern __shared__ __align__(16) float2 xs[];   // [ldg][NVC]
     const int k = blockIdx.y;
     const float2* Xk = X + (size_t)k * ns * ldi + voff_i;
     for (int i = threadIdx.x; i < ldg * NVC; i += GEMV_THREADS) {
         const int s = i / NVC, v = i - s * NVC;
-        xs[i] = s < ns ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
+        xs[i] = s < ns && MDC_INB((size_t)k * ns * ldi + voff_i + (size_t)s * ldi + v, 1, (long long)gridDim.y * ns * ldi, err, 100)
+                    ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_c64(
     const int r0 = blockIdx.x * FWD_ROWS_PER_CTA;
     const int r1 = min(r0 + FWD_ROWS_PER_CTA, nr);
     for (int r = r0 + warp; r < r1; r += GEMV_THREADS / 32) {
+        if (!MDC_INB(((size_t)k * nr + r) * nvec, nvec, (long long)gridDim.y * nr * nvec, err, 101)) continue;
         const float4* g = G + ((size_t)k * nr + r) * nvec;
         float2 acc[NVC];
 #pragma unroll
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_c64(
                 acc[v].y += __shfl_xor_sync(0xffffffffu, acc[v].y, off);
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && MDC_INB(((size_t)k * nr + r) * ldo + voff_o, NVC, (long long)gridDim.y * nr * ldo, err, 102)) {
             float2* y = Y + ((size_t)k * nr + r) * ldo + voff_o;
 #pragma unroll
             for (int v = 0; v < NVC; ++v) y[v] = acc[v];
@@ -170,7 +172,7 @@ template <int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
     const float4* __restrict__ G, int ldg, int nr, int ns,
     const float2* __restrict__ Yin, int ldi, int voff_i,
-    float2* __restrict__ Xout, int ldo, int voff_o, const int* active) {
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int* err) {
     if (active && *active == 0) return;
     extern __shared__ __align__(16) float2 ys[];   // [nr][NVC], then reduction space
     const int k = blockIdx.y;
@@ -178,7 +180,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
     const float2* Yk = Yin + (size_t)k * nr * ldi + voff_i;
     for (int i = threadIdx.x; i < nr * NVC; i += GEMV_THREADS) {
         const int r = i / NVC, v = i - r * NVC;
-        ys[i] = Yk[(size_t)r * ldi + v];
+        ys[i] = MDC_INB((size_t)k * nr * ldi + voff_i + (size_t)r * ldi + v, 1, (long long)gridDim.y * nr * ldi, err, 103)
+                    ? Yk[(size_t)r * ldi + v] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,7 +191,10 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
 #pragma unroll
     for (int v = 0; v < NVC; ++v) { a0[v] = make_float2(0.f, 0.f); a1[v] = make_float2(0.f, 0.f); }
     constexpr int W = GEMV_THREADS / 32;
-    int r = warp;
+    // this lane's column of vectors: rows 0 .. nr - 1, nvec apart
+    const bool gok = MDC_INB((size_t)k * nr * nvec + (s0 >> 1) + lane, (size_t)(nr - 1) * nvec + 1,
+                             (long long)gridDim.y * nr * nvec, err, 104);
+    int r = gok ? warp : nr;
     for (; r + 3 * W < nr; r += 4 * W) {
         float4 gv[4];
 #pragma unroll
@@ -227,7 +233,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_c64(
         float2 tot = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < W; ++w) tot = cadd(tot, red[(w * ADJ_TILE + sl) * NVC + v]);
-        if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
+        if (s < ns && MDC_INB(((size_t)k * ns + s) * ldo + voff_o + v, 1, (long long)gridDim.y * ns * ldo, err, 105))
+            Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
     }
 }
 
@@ -240,7 +247,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ X, int ldi, int voff_i,
-    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo) {
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo, int* err) {
     constexpr int CPV = Fmt<FMT>::CPV;
     if (active && *active == 0) return;
     extern __shared__ __align__(16) float2 xs[];
@@ -250,13 +257,16 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
     for (int e = threadIdx.x; e < ldg * NVC; e += GEMV_THREADS) {
         const int s = e / NVC, v = e - s * NVC;
         const int i = s / CPV, j = s - i * CPV;
-        xs[(j * nvec + i) * NVC + v] = s < ns ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
+        xs[(j * nvec + i) * NVC + v] =
+            s < ns && MDC_INB((size_t)k * ns * ldi + voff_i + (size_t)s * ldi + v, 1, (long long)gridDim.y * ns * ldi, err, 106)
+                ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = blockIdx.x * FWD_ROWS_PER_CTA;
     const int r1 = min(r0 + FWD_ROWS_PER_CTA, nr);
     for (int r = r0 + warp; r < r1; r += GEMV_THREADS / 32) {
+        if (!MDC_INB(((size_t)k * nr + r) * nvec, nvec, (long long)gridDim.y * nr * nvec, err, 107)) continue;
         const uint4* g = G + ((size_t)k * nr + r) * nvec;
         float2 acc[NVC];
 #pragma unroll
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd(
                 acc[v].y += __shfl_xor_sync(0xffffffffu, acc[v].y, off);
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && MDC_INB(((size_t)k * nr + r) * ldo + voff_o, NVC, (long long)gridDim.y * nr * ldo, err, 109)) {
             const float sc = (FMT == MDC_C64) ? 1.f : gscale[(size_t)k * nr + r];
             float2* y = Y + ((size_t)k * nr + r) * ldo + voff_o;
 #pragma unroll
@@ -305,7 +315,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ Yin, int ldi, int voff_i,
-    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo) {
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo, int* err) {
     constexpr int CPV = Fmt<FMT>::CPV;
     constexpr int TILE = 32 * CPV;
     constexpr int W = GEMV_THREADS / 32;
@@ -316,7 +326,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     const float2* Yk = Yin + (size_t)k * nr * ldi + voff_i;
     for (int e = threadIdx.x; e < nr * NVC; e += GEMV_THREADS) {
         const int r = e / NVC, v = e - r * NVC;
-        float2 y = Yk[(size_t)r * ldi + v];
+        float2 y = MDC_INB((size_t)k * nr * ldi + voff_i + (size_t)r * ldi + v, 1, (long long)gridDim.y * nr * ldi, err, 110)
+                       ? Yk[(size_t)r * ldi + v] : make_float2(0.f, 0.f);
         if (FMT != MDC_C64) {
             const float sc = gscale[(size_t)k * nr + r];
             y.x *= sc;
@@ -327,7 +338,10 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nvec = ldg / CPV;
-    const bool live = s0 + CPV * lane < ldg;
+    // live lanes walk their column of vectors: rows 0 .. nr - 1, nvec apart
+    const bool live = s0 + CPV * lane < ldg &&
+                      MDC_INB((size_t)k * nr * nvec + (s0 / CPV) + lane, (size_t)(nr - 1) * nvec + 1,
+                              (long long)gridDim.y * nr * nvec, err, 112);
     const uint4* g = G + (size_t)k * nr * nvec + (s0 / CPV) + lane;
     float2 acc[CPV][NVC];
 #pragma unroll
@@ -374,7 +388,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj(
         float2 tot = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < W; ++w) tot = cadd(tot, red[(w * TILE + sl) * NVC + v]);
-        if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
+        if (s < ns && MDC_INB(((size_t)k * ns + s) * ldo + voff_o + v, 1, (long long)gridDim.y * ns * ldo, err, 113))
+            Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
     }
 }
 
@@ -407,7 +422,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_chunked(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ X, int ldi, int voff_i,
-    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo) {
+    float2* __restrict__ Y, int ldo, int voff_o, const int* active, int64_t lo, int* err) {
     constexpr int CPV = Fmt<FMT>::CPV;
     constexpr int CHV = FwdChunk<FMT, NVC>::CHV;
     constexpr int W = GEMV_THREADS / 32;
@@ -431,13 +446,16 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_chunked(
             const int sl = e / NVC, v = e - sl * NVC;
             const int i = sl / CPV, j = sl - i * CPV;
             const int s = c0 * CPV + sl;
-            xs[(j * CHV + i) * NVC + v] = s < ns ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
+            xs[(j * CHV + i) * NVC + v] =
+                s < ns && MDC_INB((size_t)k * ns * ldi + voff_i + (size_t)s * ldi + v, 1, (long long)gridDim.y * ns * ldi, err, 114)
+                    ? Xk[(size_t)s * ldi + v] : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
             const int r = rw + W * q;
             if (r >= nr) break;                        // warp-uniform
+            if (!MDC_INB(((size_t)k * nr + r) * nvec, nvec, (long long)gridDim.y * nr * nvec, err, 115)) continue;
             const uint4* g = G + ((size_t)k * nr + r) * nvec;
             int i = c0 + lane;
             for (; i + 96 < c1; i += 128) {
@@ -475,7 +493,7 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_fwd_chunked(
                 acc[q][v].y += __shfl_xor_sync(0xffffffffu, acc[q][v].y, off);
             }
         }
-        if (lane == 0) {
+        if (lane == 0 && MDC_INB(((size_t)k * nr + r) * ldo + voff_o, NVC, (long long)gridDim.y * nr * ldo, err, 117)) {
             const float sc = (FMT == MDC_C64) ? 1.f : gscale[(size_t)k * nr + r];
             float2* y = Y + ((size_t)k * nr + r) * ldo + voff_o;
 #pragma unroll
@@ -490,7 +508,7 @@ template <int FMT, int NVC>
 __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_chunked(
     const uint4* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ Yin, int ldi, int voff_i,
-    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo) {
+    float2* __restrict__ Xout, int ldo, int voff_o, const int* active, int64_t lo, int* err) {
     constexpr int CPV = Fmt<FMT>::CPV;
     constexpr int TILE = 32 * CPV;
     constexpr int W = GEMV_THREADS / 32;
@@ -502,7 +520,10 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_chunked(
     const float2* Yk = Yin + (size_t)k * nr * ldi + voff_i;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nvec = ldg / CPV;
-    const bool live = s0 + CPV * lane < ldg;
+    // live lanes walk their column of vectors: rows 0 .. nr - 1, nvec apart
+    const bool live = s0 + CPV * lane < ldg &&
+                      MDC_INB((size_t)k * nr * nvec + (s0 / CPV) + lane, (size_t)(nr - 1) * nvec + 1,
+                              (long long)gridDim.y * nr * nvec, err, 112);
     const uint4* g = G + (size_t)k * nr * nvec + (s0 / CPV) + lane;
     float2 acc[CPV][NVC];
 #pragma unroll
@@ -515,7 +536,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_chunked(
         for (int e = threadIdx.x; e < (c1 - c0) * NVC; e += GEMV_THREADS) {
             const int rl = e / NVC, v = e - rl * NVC;
             const int r = c0 + rl;
-            float2 y = Yk[(size_t)r * ldi + v];
+            float2 y = MDC_INB((size_t)k * nr * ldi + voff_i + (size_t)r * ldi + v, 1, (long long)gridDim.y * nr * ldi, err, 118)
+                           ? Yk[(size_t)r * ldi + v] : make_float2(0.f, 0.f);
             if (FMT != MDC_C64) {
                 const float sc = gscale[(size_t)k * nr + r];
                 y.x *= sc;
@@ -565,7 +587,8 @@ __global__ void __launch_bounds__(GEMV_THREADS) gemv_adj_chunked(
         float2 tot = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < W; ++w) tot = cadd(tot, red[(w * TILE + sl) * NVC + v]);
-        if (s < ns) Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
+        if (s < ns && MDC_INB(((size_t)k * ns + s) * ldo + voff_o + v, 1, (long long)gridDim.y * ns * ldo, err, 113))
+            Xout[((size_t)k * ns + s) * ldo + voff_o + v] = tot;
     }
 }
 
@@ -620,7 +643,7 @@ template <int FMT, bool ADJ, bool NARROW = false>
 __global__ void __launch_bounds__(256) cgemm_simt(
     const unsigned char* __restrict__ G, int ldg, int nr, int ns, const float* __restrict__ gscale,
     const float2* __restrict__ B, int ldb, int voff_b,
-    float2* __restrict__ Cm, int ldc, int voff_c, int N, const int* active, size_t lo) {
+    float2* __restrict__ Cm, int ldc, int voff_c, int N, const int* active, size_t lo, int* err) {
     if (active && *active == 0) return;
     constexpr int BPC = Bytes<FMT>::v;
     constexpr int TBM = NARROW ? GBM_N : GBM, TBN = NARROW ? GBN_N : GBN;
@@ -656,14 +679,18 @@ __global__ void __launch_bounds__(256) cgemm_simt(
             if (!ADJ) {
                 const int m = (tid >> 2) + 64 * r, kq = (tid & 3) * 2;
                 float2 c0 = make_float2(0.f, 0.f), c1 = c0;
-                if (m0 + m < M) load2<FMT>(Gk + (size_t)(m0 + m) * ldg * BPC, kt + kq, c0, c1, lo);
+                if (m0 + m < M && MDC_INB(((size_t)k * nr + m0 + m) * ldg * BPC + (size_t)(kt + kq) * BPC, 2 * BPC,
+                                          (long long)gridDim.z * nr * ldg * BPC, err, 120))
+                    load2<FMT>(Gk + (size_t)(m0 + m) * ldg * BPC, kt + kq, c0, c1, lo);
                 As[kq][m] = c0;
                 As[kq + 1][m] = c1;
             } else {
                 const int kk = tid >> 5, mq = (tid & 31) * 2 + 64 * r;
                 float2 c0 = make_float2(0.f, 0.f), c1 = c0;
                 // a 128-column tile may reach past the padded row (ldg is a multiple of 64 only)
-                if (kt + kk < K && m0 + mq < ldg) {
+                if (kt + kk < K && m0 + mq < ldg &&
+                    MDC_INB(((size_t)k * nr + kt + kk) * ldg * BPC + (size_t)(m0 + mq) * BPC, 2 * BPC,
+                            (long long)gridDim.z * nr * ldg * BPC, err, 121)) {
                     load2<FMT>(Gk + (size_t)(kt + kk) * ldg * BPC, m0 + mq, c0, c1, lo);
                     const float sc = (FMT == MDC_C64) ? 1.f : sck[kt + kk];
                     c0 = make_float2(c0.x * sc, -c0.y * sc);
@@ -679,8 +706,9 @@ __global__ void __launch_bounds__(256) cgemm_simt(
             float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
             if (kt + kk < K) {
                 const float2* row = Bk + (size_t)(kt + kk) * ldb + n0 + nq;
-                if (n0 + nq < N) b0 = row[0];
-                if (n0 + nq + 1 < N) b1 = row[1];
+                [[maybe_unused]] const size_t ro = (size_t)k * K * ldb + voff_b + (size_t)(kt + kk) * ldb + n0 + nq;
+                if (n0 + nq < N && MDC_INB(ro, 1, (long long)gridDim.z * K * ldb, err, 123)) b0 = row[0];
+                if (n0 + nq + 1 < N && MDC_INB(ro + 1, 1, (long long)gridDim.z * K * ldb, err, 123)) b1 = row[1];
             }
             Bs[kk][nq] = b0;
             Bs[kk][nq + 1] = b1;
@@ -717,7 +745,7 @@ __global__ void __launch_bounds__(256) cgemm_simt(
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx + TXN * j;
-            if (n < N)
+            if (n < N && MDC_INB(((size_t)k * M + m) * ldc + voff_c + n, 1, (long long)gridDim.z * M * ldc, err, 125))
                 Cm[((size_t)k * M + m) * ldc + voff_c + n] = make_float2(tot[4 * i + j][tid].x * sc, tot[4 * i + j][tid].y * sc);
         }
     }
@@ -738,7 +766,7 @@ void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         dim3 grid((p->nr + FWD_CHUNK_ROWS - 1) / FWD_CHUNK_ROWS, p->nf);
         gemv_fwd_chunked<FMT, NVC><<<grid, GEMV_THREADS, csmem, s>>>(
             reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-            ldo, voff_o, active, lo_plane_vec(p));
+            ldo, voff_o, active, lo_plane_vec(p), p->err_flag);
         return;
     }
     static SmemLimit attr;
@@ -749,12 +777,12 @@ void gemv_fwd_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         attr64.ensure(gemv_fwd_c64<NVC>, 220 * 1024);
         gemv_fwd_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
             reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-            voff_o, active);
+            voff_o, active, p->err_flag);
         return;
     }
     gemv_fwd<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
         reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-        ldo, voff_o, active, lo_plane_vec(p));
+        ldo, voff_o, active, lo_plane_vec(p), p->err_flag);
 }
 
 template <int FMT, int NVC>
@@ -771,7 +799,7 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         dim3 grid((unsigned)((p->ldg + TILE - 1) / TILE), p->nf);
         gemv_adj_chunked<FMT, NVC><<<grid, GEMV_THREADS, csmem, s>>>(
             reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-            ldo, voff_o, active, lo_plane_vec(p));
+            ldo, voff_o, active, lo_plane_vec(p), p->err_flag);
         return;
     }
     if (smem < red) smem = red;
@@ -783,12 +811,12 @@ void gemv_adj_launch(mdc_plan* p, const float2* in, int ldi, int voff_i, float2*
         attr64.ensure(gemv_adj_c64<NVC>, 220 * 1024);
         gemv_adj_c64<NVC><<<grid, GEMV_THREADS, smem, s>>>(
             reinterpret_cast<const float4*>(p->G), (int)p->ldg, p->nr, p->ns, in, ldi, voff_i, out, ldo,
-            voff_o, active);
+            voff_o, active, p->err_flag);
         return;
     }
     gemv_adj<FMT, NVC><<<grid, GEMV_THREADS, smem, s>>>(
         reinterpret_cast<const uint4*>(p->G), (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i, out,
-        ldo, voff_o, active, lo_plane_vec(p));
+        ldo, voff_o, active, lo_plane_vec(p), p->err_flag);
 }
 
 bool gemv_fits(const mdc_plan* p, bool adjoint, int ncol, int cpv) {
@@ -843,19 +871,19 @@ bool product_fmt(mdc_plan* p, bool adjoint, const float2* in, int ldi, int voff_
         dim3 grid((ncol + GBN_N - 1) / GBN_N, (M + GBM_N - 1) / GBM_N, p->nf);
         if (adjoint)
             cgemm_simt<FMT, true, true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi,
-                                                             voff_i, out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
+                                                             voff_i, out, ldo, voff_o, ncol, active, lo_plane_bytes(p), p->err_flag);
         else
             cgemm_simt<FMT, false, true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi,
-                                                              voff_i, out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
+                                                              voff_i, out, ldo, voff_o, ncol, active, lo_plane_bytes(p), p->err_flag);
         return true;
     }
     dim3 grid((ncol + GBN - 1) / GBN, (M + GBM - 1) / GBM, p->nf);
     if (adjoint)
         cgemm_simt<FMT, true><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
-                                                   out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
+                                                   out, ldo, voff_o, ncol, active, lo_plane_bytes(p), p->err_flag);
     else
         cgemm_simt<FMT, false><<<grid, 256, 0, s>>>(G, (int)p->ldg, p->nr, p->ns, p->gscale, in, ldi, voff_i,
-                                                    out, ldo, voff_o, ncol, active, lo_plane_bytes(p));
+                                                    out, ldo, voff_o, ncol, active, lo_plane_bytes(p), p->err_flag);
     return true;
 }
 

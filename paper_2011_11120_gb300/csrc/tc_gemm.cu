@@ -188,6 +188,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 struct TcArgs {
+    int nf;             // frequencies (output extent of the bounds checks)
     int kstages;        // reduction slices of TC_BK elements
     int nout;           // output rows: nr (forward) or ns (adjoint)
     int nr;             // kernel rows (row-scale stride)
@@ -615,11 +616,14 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
             {
                 const int e = threadIdx.x - 64;
                 const int n = (n0 >> 1) + e;
-                if (e < BN / 2) sgs[e] = n < a.ncol ? a.inv_sigma[(size_t)k * a.ncol + n] : 0.f;
+                if (e < BN / 2)
+                    sgs[e] = n < a.ncol && MDC_INB((size_t)k * a.ncol + n, 1, (long long)a.nf * a.ncol, a.err, 131)
+                                 ? a.inv_sigma[(size_t)k * a.ncol + n] : 0.f;
                 asm volatile("bar.sync 1, 256;" ::: "memory");
             }
             const int r = m0 + row;
-            const float gs = (!ADJ && r < a.nout) ? a.gscale[(size_t)k * a.nr + r] : 1.f;
+            const float gs = (!ADJ && r < a.nout && MDC_INB((size_t)k * a.nr + r, 1, (long long)a.nf * a.nr, a.err, 132))
+                                 ? a.gscale[(size_t)k * a.nr + r] : 1.f;
             // Store 16 accumulator columns c0.. (8 complex output columns) of this warp's 32 rows:
             // scaled values go through a per-warp staging tile (rows padded to 20 floats, so both
             // the row-wise writes and the column-wise reads are conflict-free), then each store
@@ -662,7 +666,9 @@ __global__ void __launch_bounds__(CVT ? TC_THREADS + TC_CVT_THREADS + 32 : TC_TH
                 for (int it = 0; it < NROWS / 8; ++it) {
                     const int rr = (lane & 7) + 8 * it, orow = orow0 + rr;
                     const float4 val = *reinterpret_cast<const float4*>(stg + rr * 20 + 4 * cc);
-                    if (orow < a.nout && n < a.ncol) {
+                    if (orow < a.nout && n < a.ncol &&
+                        MDC_INB(((size_t)k * a.nout + orow) * a.ldo + a.voff_o + n, n + 1 < a.ncol ? 2 : 1,
+                                (long long)a.nf * a.nout * a.ldo, a.err, 130)) {
                         float2* dst = a.out + ((size_t)k * a.nout + orow) * a.ldo + a.voff_o + n;
                         if (n + 1 < a.ncol && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
                             *reinterpret_cast<float4*>(dst) = val;
@@ -905,7 +911,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float re = p0[0] + 0.0625f * p0[R * F8_LD] + 0.00390625f * p0[2 * R * F8_LD];
                         const float im =
                             p0[F8_LD] + 0.0625f * p0[(R + 1) * F8_LD] + 0.00390625f * p0[(2 * R + 1) * F8_LD];
-                        if (r < a.nout) {
+                        if (r < a.nout && MDC_INB(((size_t)k * a.nout + r) * a.ldo + a.voff_o + n, 1,
+                                                  (long long)a.nf * a.nout * a.ldo, a.err, 134)) {
                             const float f = gsk[r] * isg[n];
                             a.out[((size_t)k * a.nout + r) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
                         }
@@ -923,7 +930,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             re += w * (p0[0] + p0[F8_LD + 1]);
                             im += w * (p0[F8_LD] - p0[1]);
                         }
-                        if (so < a.nout) {
+                        if (so < a.nout && MDC_INB(((size_t)k * a.nout + so) * a.ldo + a.voff_o + n, 1,
+                                                   (long long)a.nf * a.nout * a.ldo, a.err, 135)) {
                             const float f = isg[n];
                             a.out[((size_t)k * a.nout + so) * a.ldo + a.voff_o + n] = make_float2(re * f, im * f);
                         }
@@ -1056,7 +1064,8 @@ __device__ __forceinline__ void prep_put(const float2 (&v)[PREP_PER], const floa
 template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X, int ldi, int voff, int ns,
                                                    int ncol, int ldg, int rows_pad, T* __restrict__ BT,
-                                                   float* __restrict__ inv_sigma, const int* active, size_t plane) {
+                                                   float* __restrict__ inv_sigma, const int* active, size_t plane,
+                                                   int* err) {
     if (active && *active == 0) return;
     using P2 = typename Pair2<T>::type;
     const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
@@ -1083,6 +1092,7 @@ __global__ void __launch_bounds__(256) tc_prep_fwd(const float2* __restrict__ X,
                 if (2 * n >= rows_pad) break;
                 const float2 v = tile[threadIdx.x][j];
                 const T hx = cvt<T>(v.x), hy = cvt<T>(v.y);
+                if (!MDC_INB((size_t)k * rows_pad * kp2 + (size_t)(2 * n) * kp2 + s, kp2 + 1, plane2, err, 136)) break;
                 P2* r0 = Bk + (size_t)(2 * n) * kp2 + s;
                 r0[0] = Pair2<T>::make(hx, cvt<T>(-v.y));
                 r0[kp2] = Pair2<T>::make(hy, hx);
@@ -1117,7 +1127,7 @@ __device__ __forceinline__ void e4m3_split3(float v, uint32_t (&h)[3]) {
 // three terms t of e4m3_split3 after the power-of-two column scale), inv_sigma[k][n].
 __global__ void __launch_bounds__(256) tc_prep_fwd_f8(const float2* __restrict__ X, int ldi, int voff, int ns,
                                                       int ncol, int ldg, uint8_t* __restrict__ A,
-                                                      float* __restrict__ inv_sigma, const int* active) {
+                                                      float* __restrict__ inv_sigma, const int* active, int* err) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
     const float2* Xk = X + (size_t)k * ns * ldi + voff;
@@ -1149,6 +1159,9 @@ __global__ void __launch_bounds__(256) tc_prep_fwd_f8(const float2* __restrict__
                 e4m3_split3(-v.y, hny);
 #pragma unroll
                 for (int t = 0; t < F8_TERMS; ++t) {
+                    if (!MDC_INB((size_t)k * F8_TERMS * R * row2 + (size_t)(t * R + 2 * n) * row2 + s, row2 + 1,
+                                 (long long)gridDim.y * F8_TERMS * R * row2, err, 138))
+                        continue;
                     uint16_t* r0 = Ak + (size_t)(t * R + 2 * n) * row2 + s;
                     r0[0] = (uint16_t)(hx[t] | (hny[t] << 8));          // (Re, -Im)
                     r0[row2] = (uint16_t)(hy[t] | (hx[t] << 8));        // (Im, Re)
@@ -1165,7 +1178,7 @@ __global__ void __launch_bounds__(256) tc_prep_fwd_f8(const float2* __restrict__
 __global__ void __launch_bounds__(256) tc_prep_adj_f8(const float2* __restrict__ Y, int ldi, int voff, int nr,
                                                       int ncol, const float* __restrict__ gscale, int kpitch,
                                                       uint8_t* __restrict__ A, float* __restrict__ inv_sigma,
-                                                      const int* active) {
+                                                      const int* active, int* err) {
     if (active && *active == 0) return;
     const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
     const float2* Yk = Y + (size_t)k * nr * ldi + voff;
@@ -1200,6 +1213,9 @@ __global__ void __launch_bounds__(256) tc_prep_adj_f8(const float2* __restrict__
                 e4m3_split3(vb.y, by);
 #pragma unroll
                 for (int tt = 0; tt < F8_TERMS; ++tt) {
+                    if (!MDC_INB((size_t)k * F8_TERMS * R * kq + (size_t)(tt * R + 2 * n) * kq + (r >> 1), kq + 1,
+                                 (long long)gridDim.y * F8_TERMS * R * kq, err, 139))
+                        continue;
                     uint16_t* q0 = Ak + (size_t)(tt * R + 2 * n) * kq + (r >> 1);
                     q0[0] = (uint16_t)(ax[tt] | (bx[tt] << 8));           // Re at r, r + 1
                     q0[kq] = (uint16_t)(ay[tt] | (by[tt] << 8));          // Im at r, r + 1
@@ -1216,7 +1232,7 @@ template <typename T, bool SPLIT>
 __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y, int ldi, int voff, int nr,
                                                    int ncol, const float* __restrict__ gscale, int kpitch,
                                                    int rows_pad, T* __restrict__ BT, float* __restrict__ inv_sigma,
-                                                   const int* active, size_t plane) {
+                                                   const int* active, size_t plane, int* err) {
     if (active && *active == 0) return;
     using P2 = typename Pair2<T>::type;
     const int k = blockIdx.y, n0 = blockIdx.x * PREP_COLS;
@@ -1245,6 +1261,7 @@ __global__ void __launch_bounds__(256) tc_prep_adj(const float2* __restrict__ Y,
                 if (2 * n >= rows_pad) continue;
                 const float2 a = tile[2 * t][j], b = tile[2 * t + 1][j];
                 const T ax = cvt<T>(a.x), bx = cvt<T>(b.x), ay = cvt<T>(a.y), by = cvt<T>(b.y);
+                if (!MDC_INB((size_t)k * rows_pad * kq + (size_t)(2 * n) * kq + (r >> 1), kq + 1, plane2, err, 137)) continue;
                 P2* q0 = Bk + (size_t)(2 * n) * kq + (r >> 1);
                 q0[0] = Pair2<T>::make(ax, bx);
                 q0[kq] = Pair2<T>::make(ay, by);
@@ -1382,10 +1399,10 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         dim3 pf((unsigned)((ncol + PREP_COLS - 1) / PREP_COLS), (unsigned)p->nf);
         if (!adjoint)
             tc_prep_fwd_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->ns, ncol, (int)p->ldg, (uint8_t*)p->tcB,
-                                              p->tcSigma, active);
+                                              p->tcSigma, active, p->err_flag);
         else
             tc_prep_adj_f8<<<pf, 256, 0, s>>>(in, ldi, voff_i, p->nr, ncol, p->gscale, (int)kpf, (uint8_t*)p->tcB,
-                                              p->tcSigma, active);
+                                              p->tcSigma, active, p->err_flag);
         scope.reset();
         CUtensorMap mA, mB;
         const uint64_t ka = adjoint ? kpf : kp;
@@ -1393,6 +1410,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
             !make_map_3d(&mB, p->G, false, kp, p->nr, p->nf, kp, kp * p->nr, 128, adjoint ? 128 : F8_BN, true, true))
             return false;
         TcArgs a{};
+        a.nf = p->nf;
         a.kstages = adjoint ? (p->nr + 127) / 128 : (int)(kp / 128);
         a.nout = adjoint ? p->ns : p->nr;
         a.nr = p->nr;
@@ -1425,7 +1443,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         return true;
     }
     if (scoped) scope.emplace(p, s, MDC_KC_TC_PREP);
-#define MDC_PREP(KER, T, SP, ...) KER<T, SP><<<pg, 256, 0, s>>>(__VA_ARGS__, active, plane)
+#define MDC_PREP(KER, T, SP, ...) KER<T, SP><<<pg, 256, 0, s>>>(__VA_ARGS__, active, plane, p->err_flag)
     if (!adjoint) {
         if (bf16)
             MDC_PREP(tc_prep_fwd, __nv_bfloat16, false, in, ldi, voff_i, p->ns, ncol, (int)p->ldg, rows_pad,
@@ -1483,6 +1501,7 @@ bool launch_tc_product(mdc_plan* p, bool adjoint, const float2* in, int ldi, int
         maps[3] = maps[1];
     }
     TcArgs a{};
+    a.nf = p->nf;
     a.kstages = adjoint ? (p->nr + TC_BK - 1) / TC_BK : (int)(kp / TC_BK);
     a.nout = adjoint ? p->ns : p->nr;
     a.nr = p->nr;
