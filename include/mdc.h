@@ -454,7 +454,8 @@ int mdc_set_option(mdc_handle h, int option, int value);
  * path.  -1 for a NULL handle.  Host-only. */
 int64_t mdc_tc_fallback_count(mdc_handle h);
 /* mdc_device_status -- synchronise `stream` and report MDC_ERR_TIMEOUT if a kernel of this
- * handle gave up a bounded device-side wait since the last check (the flag is then cleared). */
+ * handle gave up a bounded device-side wait since the last check, or (bounds-checked build only)
+ * MDC_ERR_BOUNDS if a kernel index fell outside its buffer; the flag is then cleared. */
 int mdc_device_status(mdc_handle h, void* stream);
 int mdc_timing_read(mdc_handle h, int kernel_class, double* total_ms, int64_t* launches);
 int64_t mdc_launch_count(mdc_handle h);
